@@ -1,0 +1,363 @@
+#!/usr/bin/env python3
+"""Benchmark of the descent hot path: feasible packings per second (largest overlap <= 1e-9).
+
+One step = one pass of the whole path over one batch of synthetic instances: random initial
+layouts drawn on the device (Philox), sector partition, cell-list neighbor lists with ANM and
+the Verlet rule, geometric-batch L-BFGS descent (FP32 bulk + FP64 polish, or plain FP64), and
+the FP64 feasibility check.  Workloads:
+  c3      4096 instances, n ~ U{300..1000}, R = sqrt(n / u), u ~ U[0.80, 0.84]; FP32 + FP64 polish (default)
+  c3-fp64 the same instances, plain FP64 descent
+  c2      one instance n = 1000, u = 0.83; FP32 + FP64 polish
+  c2-fp64 the same, plain FP64
+  c1      one instance n = 50, u = 0.80; plain FP64
+Prints one JSON line.  --impl reference times the FP64 CPU oracle on the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2303_02650_gb300 import synth  # noqa: E402
+
+METRIC = "feasible packings/s (overlap≤1e-9) and neighbor-pair grad evals/s vs plain FP64"
+UNIT = "feasible packings/s"
+
+
+def workload(name: str):
+    if name in ("c3", "c3-fp64"):
+        n, R = synth.batch_manifest(4096, seed=2303)
+        desc = "batching form: 4096 instances, n~U{300..1000}, R=sqrt(n/u), u~U[0.80,0.84], disk init"
+    elif name in ("c2", "c2-fp64"):
+        n, R = np.array([1000], dtype=np.int32), np.array([synth.radius(1000, 0.83)])
+        desc = "precision form: 1 instance n=1000, R=sqrt(n/0.83), disk init"
+    elif name == "c1":
+        n, R = np.array([50], dtype=np.int32), np.array([synth.radius(50, 0.80)])
+        desc = "plain method: 1 instance n=50, R=sqrt(n/0.80), disk init"
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    prec = 0 if (name.endswith("fp64") or name == "c1") else 2
+    return n, R, prec, desc
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.out, _ = self.p.communicate(timeout=5)
+            except Exception:
+                self.p.kill()
+                self.out = ""
+        else:
+            self.out = ""
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").splitlines():
+            f = [t.strip() for t in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def algorithmic_bytes_descent(n, k, iters, trials, m, vec_bytes=8):
+    """Algorithmic DRAM bytes of the first-phase descent kernel (per launch).
+    Per circle and sweep: one fused energy + gradient pass (read x 8 B, row pointer 4 B, about 6
+    neighbor indices 24 B, write g 8 B = 44 B), the quasi-Newton direction over the m stored
+    pairs (read 4 m vectors of vec_bytes), the new pair (write s, y: 2 vec_bytes).  Per line-search
+    trial: one fused pass over the batch's n/k circles (44 B each)."""
+    n = n.astype(np.float64)
+    per_sweep = 44.0 + 4 * m * vec_bytes + 2 * vec_bytes
+    return float(np.sum(n * iters * per_sweep) + np.sum(n / k * trials * 44.0))
+
+
+def run_ours(args, rank, world, local):
+    import torch
+
+    from paper_2303_02650_gb300 import pecc
+
+    torch.cuda.set_device(local)
+    n, R, prec, desc = workload(args.workload)
+    if args.instances:
+        n, R = n[:args.instances], R[:args.instances]
+        desc += f" (first {n.size} instances only: profiling case)"
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    ctx = pecc.Context(n, precision=prec)
+    ctx.set_radius(R)
+    kvec = np.array([1 if v < 300 else (3 if v < 500 else 5) for v in n], dtype=np.float64)
+    kvec = np.minimum(kvec, np.maximum(n, 1))
+    seed0 = args.seed + 1_000_003 * rank
+
+    def step(s):
+        ctx.init_random(seed0 + s)
+        ctx.descend()
+        feas, mo = ctx.check_feasible(1e-9)
+        return feas
+
+    for w in range(args.warmup):
+        step(10_000 + w)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    feas_sum = torch.zeros((), dtype=torch.int64, device="cuda")
+    phase_ms, phase_bytes, phase2_ms = [], [], []
+    it_all, st_all = [], []
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        torch.cuda.synchronize()
+        e0.record()
+        for s in range(args.steps):
+            feas = step(s)
+            feas_sum += feas.to(torch.int64).sum()
+            # device time of the descent kernels of this step (events inside the graph)
+            ms = ctx.phase_times()
+            st = ctx.get_stats().cpu().numpy()
+            phase_ms.append(ms[0])
+            phase2_ms.append(ms[1])
+            phase_bytes.append(algorithmic_bytes_descent(n, kvec, st[:, 8], st[:, 9], 10,
+                                                         16 if prec == 0 else 8))
+            it_all.append(st[:, 0])
+            st_all.append(st[:, 1])
+        e1.record()
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms_total = e0.elapsed_time(e1)
+    feasible = int(feas_sum.item())
+    if dist:
+        t = torch.tensor([ms_total], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+        f = torch.tensor([feasible], device="cuda", dtype=torch.int64)
+        dist.all_reduce(f)
+        feasible = int(f.item())
+    value = feasible / (ms_total / 1e3)
+    solved = sum(int(n.size) for _ in range(args.steps)) * world
+
+    # neighbor-pair gradient evaluations per second inside the descent (first phase)
+    # and the standalone fused energy + gradient kernel against the HBM roofline
+    eg = energy_grad_roofline(ctx, torch, n)
+
+    # end to end through the host-buffer entry point (copies inside the timed region)
+    e2e_ms, e2e_feas = 0.0, 0
+    h2d = n.size * 8
+    d2h = int(n.sum()) * 16 + n.size * (4 + 4 + 1 + 8)
+    for s in range(args.steps):
+        t0 = time.perf_counter()
+        out = ctx.solve_host(R, seed0 + 50_000 + s, want_xy=True)
+        e2e_ms += (time.perf_counter() - t0) * 1e3
+        e2e_feas += int(out["feasible"].sum())
+
+    hbm, peak_kind = peaks()
+    dom_ms = float(np.mean(phase_ms))
+    dom_bytes = float(np.mean(phase_bytes))
+    achieved = dom_bytes / (dom_ms / 1e3) / 1e9
+    its = np.concatenate(it_all)
+    sts = np.concatenate(st_all)
+    line = {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_total / args.steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if prec == 0 else "f32+f64",
+        "data": "synthetic (Philox-drawn layouts; instance manifest from a seeded generator)",
+        "config": {"workload": f"{args.workload}: {desc}",
+                   "precision": "plain FP64" if prec == 0 else "FP32 bulk + FP64 polish",
+                   "instances_per_step": int(n.size), "circles_per_step": int(n.sum()),
+                   "l_cut": 2.5, "rebuild_disp": 0.25, "lbfgs_m": 10, "max_iter": 2000,
+                   "k_batches": "1 (n<300), 3 (n<500), 5", "partition": "sector",
+                   "l2": "working set per step > 129 MB L2 (histories and lists of all instances); no flush",
+                   "launch": dict(zip(["block_threads", "blocks_per_sm", "grid"], ctx.launch_shape())),
+                   "parallelism": f"instances sharded over {world} GPU(s), no collective on the data path"},
+        "success_rate": round(feasible / solved, 4),
+        "iters_mean": round(float(its.mean()), 1),
+        "status_counts": np.bincount(sts, minlength=7).tolist(),
+        "pair_grad_evals_per_s": eg.get("pair_evals_per_s_descent"),
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                     "frac": round(achieved / hbm, 4), "traffic": None,
+                     "kernel": "descend_kernel<Arith64>" if prec == 0 else "descend_kernel<Arith32> (FP32 bulk phase)",
+                     "peak_kind": peak_kind, "avg_launch_ms": round(dom_ms, 3),
+                     "algorithmic_bytes_per_launch": dom_bytes,
+                     "polish_kernel_ms": round(float(np.mean(phase2_ms)), 3)},
+        "energy_grad_roofline": eg,
+        "e2e": {"value": round(e2e_feas / (e2e_ms / 1e3), 3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": (4 if prec == 0 else 5) * args.steps,
+        "clocks": clk.summary(),
+    }
+    ctx.close()
+    if rank == 0:
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(args, n, R, prec)
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def energy_grad_roofline(ctx, torch, n):
+    """The standalone fused energy + gradient kernel over every circle of the batch, after a
+    forced FP32 (or FP64) list build at the final layouts; L2 flushed between launches."""
+    prec = ctx.precision
+    ev = 0 if prec == 0 else 1
+    ctx.rebuild_neighbors(force=True, eval=ev)
+    nnz = ctx.neighbor_count()
+    N, I = int(n.sum()), int(n.size)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    times = []
+    for r in range(6):
+        flush.fill_(float(r))
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        ctx.energy_grad(eval=ev)
+        b.record()
+        torch.cuda.synchronize()
+        times.append(a.elapsed_time(b))
+    ms = float(np.median(times[1:]))
+    pos = 16 if ev == 0 else 8
+    acc = 8 if ev == 0 else 4
+    # algorithmic bytes: read x, instance id, row pointers, column indices; write g and the
+    # per-circle energy; the per-instance energy reduction reads them back once
+    bytes_ = N * (pos + 4 + 4 + pos + acc) + 4 * I + 4 * nnz + N * acc
+    hbm, kind = peaks()
+    gbs = bytes_ / (ms / 1e3) / 1e9
+    return {"kernel": "energy_grad_kernel + energy_reduce_kernel", "achieved": round(gbs, 1), "peak": hbm,
+            "unit": "GB/s", "frac": round(gbs / hbm, 4), "peak_kind": kind, "avg_launch_ms": round(ms, 4),
+            "algorithmic_bytes_per_launch": int(bytes_), "circles": N, "neighbor_entries": int(nnz),
+            "pair_evals_per_s_standalone": round((nnz / 2) / (ms / 1e3), 1)}
+
+
+def cpu_baseline(args, n, R, prec, budget_s=15.0):
+    """The FP64 oracle, as it stands, on a bounded sample of the same workload (host cores)."""
+    import oracle
+
+    oracle.build()
+    cores = os.cpu_count() or 1
+    rng_order = np.arange(n.size)
+    # time one instance first, then size the sample to about budget_s of wall time
+    t1, _ = oracle.solve_batch(n[:1], R[:1], args.seed, nthreads=1)
+    per = max(t1, 1e-3)
+    count = int(max(1, min(n.size, budget_s * cores / per)))
+    if n.size == 1:
+        count = max(1, min(int(budget_s / per), 64))
+        nn = np.repeat(n, count)
+        RR = np.repeat(R, count)
+        t, out = oracle.solve_batch(nn, RR, args.seed, nthreads=cores)
+        sample = f"{count} runs of the single instance (different seeds), {cores} threads"
+    else:
+        idx = rng_order[:count]
+        t, out = oracle.solve_batch(n[idx], R[idx], args.seed, nthreads=cores)
+        sample = f"first {count} of the {n.size} instances, {cores} threads"
+    feas = int(out["feasible"].sum())
+    return {"value": round(feas / t, 3), "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+            "seconds": round(t, 2), "success_rate": round(feas / len(out["feasible"]), 4),
+            "arithmetic": "FP64 (plain descent; the oracle has no FP32 phase)"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import oracle
+
+    oracle.build()
+    n, R, prec, desc = workload(args.workload)
+    cores = os.cpu_count() or 1
+    per_step = max(1, min(n.size, 2 * cores))
+    for w in range(args.warmup):
+        oracle.solve_batch(n[:1], R[:1], args.seed + w, nthreads=1)
+    tot_t, tot_f = 0.0, 0
+    for s in range(args.steps):
+        lo = (s * per_step) % n.size
+        idx = np.arange(lo, lo + per_step) % n.size
+        t, out = oracle.solve_batch(n[idx], R[idx], args.seed + s, inst_base=int(lo), nthreads=cores)
+        tot_t += t
+        tot_f += int(out["feasible"].sum())
+    value = tot_f / tot_t
+    sample = f"{per_step} instances per step of the workload, {cores} threads"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(tot_t * 1e3 / args.steps, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": f"{args.workload}: {desc}", "precision": "FP64 oracle"},
+        "cpu_baseline": {"value": round(value, 3), "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": round(value, 3), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c3", choices=["c3", "c3-fp64", "c2", "c2-fp64", "c1"])
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--instances", type=int, default=0, help="use only the first N instances (small profiling case)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

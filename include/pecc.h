@@ -1,0 +1,224 @@
+/*
+ * pecc.h -- C ABI of the GB300 descent library for the elastic model of
+ * packing equal circles in a circle (arXiv 2303.02650).
+ *
+ * The library evaluates and minimises the overlap energy of Sec. 3.2
+ *
+ *   d_ij = max(0, 2 - |c_i - c_j|)           (Eq. 3, pair overlap depth)
+ *   d_i0 = max(0, |c_i| + 1 - R)             (Eq. 3, container overlap depth)
+ *   E(x) = sum_{i<j} d_ij^2 + sum_i d_i0^2   (Eq. 5)
+ *
+ * over neighbor lists Gamma(i) = {j != i : l_ij < l_cut} (Sec. 4.3) that are
+ * rebuilt adaptively (Algorithm ANM, Sec. 4.3, plus a Verlet displacement
+ * rule), by geometric batch optimisation (Algorithm GBO, Sec. 4.1): circles
+ * are split into k sector batches and each batch takes quasi-Newton steps
+ * (Eq. 8, with the inverse Hessian of Eq. 10 / Eq. 11 kept as m secant pairs)
+ * in Gauss-Seidel order.
+ *
+ * Conventions for every call:
+ *  - A context holds num_instances independent instances; instance q has n[q]
+ *    unit circles in a container of radius R[q] centred at the origin.
+ *  - Positions are interleaved (x, y) pairs, instances concatenated in n[]
+ *    order: circle i of instance q is at element 2 * (off[q] + i), where
+ *    off[q] = n[0] + ... + n[q-1].
+ *  - Pointers named *_dev are DEVICE pointers owned by the caller (for
+ *    example a torch CUDA tensor's data_ptr()); *_host are host pointers.
+ *  - Every call is asynchronous and ordered on the context's CUDA stream, and
+ *    returns after enqueueing; only pecc_destroy, pecc_neighbor_count,
+ *    pecc_solve_host and pecc_last_error synchronise.
+ *  - Argument errors are returned synchronously.  Errors found on the device
+ *    (non-finite coordinates, a neighbor list over capacity, a time budget
+ *    exceeded) are written to the per-instance status outputs of the call
+ *    that found them; nothing aborts, traps or spins without a bound.
+ *  - A context is not thread safe; use one context per host thread.
+ */
+#ifndef PECC_H
+#define PECC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pecc_ctx pecc_ctx;
+
+typedef enum {
+    PECC_OK = 0,
+    PECC_ERR_ARG = 1,          /* invalid argument (message in pecc_last_error) */
+    PECC_ERR_CUDA = 2,         /* a CUDA runtime call failed */
+    PECC_ERR_OOM = 3,          /* device allocation failed */
+    PECC_ERR_NBR_OVERFLOW = 4, /* a neighbor list exceeded its capacity */
+    PECC_ERR_NONFINITE = 5,    /* NaN or Inf coordinates or energy */
+    PECC_ERR_TIMEOUT = 6       /* the time budget ran out */
+} pecc_status;
+
+/* Per-instance outcome of pecc_descend (status_dev values). */
+enum {
+    PECC_DESC_CONVERGED = 0,   /* E <= e_tol */
+    PECC_DESC_STATIONARY = 1,  /* sum over batches of |g_p|_2 <= gsum_tol (Algorithm GBO) */
+    PECC_DESC_STALLED = 2,     /* no batch could lower its energy in a sweep */
+    PECC_DESC_MAX_ITER = 3,    /* max_iter sweeps done */
+    PECC_DESC_NBR_OVERFLOW = 4,
+    PECC_DESC_NONFINITE = 5,
+    PECC_DESC_TIMEOUT = 6
+};
+
+/* Arithmetic of the context. */
+enum {
+    PECC_FP64 = 0,          /* plain FP64 everywhere */
+    PECC_FP32 = 1,          /* FP32 coordinates, energy, gradient and accumulation */
+    PECC_FP32_POLISH64 = 2  /* FP32 bulk descent, then an FP64 polish descent */
+};
+
+/* Geometric partitions of Sec. 4.1. */
+enum { PECC_PART_SECTOR = 0, PECC_PART_ANNULUS = 1, PECC_PART_FENCE = 2 };
+
+/* Initial layout of Sec. 5.1. */
+enum { PECC_INIT_DISK = 0, PECC_INIT_SQUARE = 1 };
+
+typedef struct {
+    int32_t num_instances;
+    const int32_t *n;       /* host array [num_instances], each n >= 0; copied at create */
+    int32_t precision;      /* PECC_FP64 | PECC_FP32 | PECC_FP32_POLISH64 */
+    double l_cut;           /* neighbor cutoff; 2.5 (the paper uses 4), must exceed 2 */
+    double rebuild_disp;    /* Verlet half-skin: a rebuild happens before a batch step when
+                               2 * max displacement since the last build + step_max exceeds
+                               2 * rebuild_disp; 0.25 = (l_cut - 2) / 2 */
+    double step_max;        /* cap on any circle's move in one batch step; 0.1 */
+    int32_t lbfgs_m;        /* secant pairs kept per batch, 1..10; 10 */
+    int32_t max_iter;       /* sweeps of the main descent; 2000 */
+    int32_t polish_max_iter;/* sweeps of the FP64 polish (PECC_FP32_POLISH64); 1000 */
+    int32_t k_batches;      /* batches per instance; 0 = 1 (n < 300), 3 (n < 500), 5 */
+    int32_t partition;      /* PECC_PART_*; sector */
+    int32_t max_trials;     /* backtracking trials per line search; 30 */
+    int32_t anm;            /* 1: ANM deferred rebuilds on (Algorithm ANM); 1 */
+    int32_t init_mode;      /* PECC_INIT_*; disk of radius R - 1 */
+    double e_tol;           /* stop when E <= e_tol; 1e-20 */
+    double gsum_tol;        /* stop when sum_p |g_p|_2 <= gsum_tol; 1e-12 */
+    double c1;              /* Armijo constant; 1e-4 */
+    double curv_eps;        /* keep a pair only if s'y > curv_eps |s| |y|; 1e-10 */
+    double polish_gate;     /* polish only instances whose FP32 energy is <= this; 1e-4 */
+    double feas_tol;        /* feasible when the largest overlap depth <= feas_tol; 1e-9 */
+    double nbr_capacity;    /* neighbor entries reserved per circle; 16 */
+    int64_t time_budget_ns; /* per pecc_descend call, measured on the device; 0 = none */
+    int32_t block_threads;  /* threads per instance block; 0 = autotuned */
+    int32_t blocks_per_sm;  /* resident instance blocks per SM; 0 = autotuned */
+    double stall_rel;       /* FP32 phase of PECC_FP32_POLISH64 / PECC_FP32 ends (status STALLED) when
+                               E fell by less than stall_rel (relative) over stall_window sweeps:
+                               binary32 has reached its resolution; 1e-3 */
+    int32_t stall_window;   /* sweeps per stagnation check of the FP32 phase; 10 (0 = off) */
+} pecc_config;
+
+/* Fill *cfg with the defaults listed above (num_instances = 0, n = NULL). */
+void pecc_config_default(pecc_config *cfg);
+
+/* Create a context on the current CUDA device.  stream: a cudaStream_t (NULL =
+ * the legacy default stream).  Allocates every device buffer the context needs
+ * (sized from n[] and the config); *out receives the context or NULL. */
+pecc_status pecc_create(const pecc_config *cfg, void *stream, pecc_ctx **out);
+
+/* Synchronise the stream and free the context and its device memory. */
+pecc_status pecc_destroy(pecc_ctx *ctx);
+
+/* Container radii: R_dev = device double[num_instances], each R > 0 (read on the stream). */
+pecc_status pecc_set_radius(pecc_ctx *ctx, const double *R_dev);
+
+/* Coordinates: xy_dev = device double[2 * sum n].  FP32 contexts round them to binary32. */
+pecc_status pecc_set_positions(pecc_ctx *ctx, const double *xy_dev);
+
+/* Random initial layout of Sec. 5.1 on the device (init_mode of the config): circle i of
+ * instance q uses Philox4x32-10 with key (seed lo, seed hi) and counter (i, attempt, q, 0);
+ * two 53-bit uniforms give a candidate in [-(R-1), R-1]^2, accepted inside the disk. */
+pecc_status pecc_init_random(pecc_ctx *ctx, uint64_t seed);
+
+/* Current coordinates as doubles: xy_dev = device double[2 * sum n].  For
+ * PECC_FP32_POLISH64 these are the polished FP64 coordinates after pecc_descend. */
+pecc_status pecc_get_positions(pecc_ctx *ctx, double *xy_dev);
+
+/* (Re)build the neighbor lists Gamma of every instance (Sec. 4.3) by cell binning and a
+ * key sort.  force = 0 rebuilds only instances whose largest displacement since their
+ * last build exceeds rebuild_disp; rebuilt_dev (device int32[num_instances], may be NULL)
+ * receives 1 where a list was rebuilt. */
+pecc_status pecc_rebuild_neighbors(pecc_ctx *ctx, int32_t force, int32_t *rebuilt_dev);
+
+/* Number of stored neighbor entries (sum over instances of sum_i |Gamma(i)|); synchronises. */
+pecc_status pecc_neighbor_count(pecc_ctx *ctx, int64_t *nnz_host);
+
+/* Export the neighbor lists as one CSR over all circles: row_ptr_dev = device
+ * int32[sum n + 1], col_dev = device int32[cap] of global circle indices, each row
+ * ascending.  PECC_ERR_ARG if cap is below the count of pecc_neighbor_count. */
+pecc_status pecc_export_neighbors(pecc_ctx *ctx, int32_t *row_ptr_dev, int32_t *col_dev, int64_t cap);
+
+/* Export the cell binning of the last build: key_dev = device uint32[sum n] (cell index
+ * cy * ncx + cx with cell side l_cut (1 + 2^-20)), order_dev = device int32[sum n], the
+ * circles of each instance stably sorted by key (local indices). */
+pecc_status pecc_export_cells(pecc_ctx *ctx, uint32_t *key_dev, int32_t *order_dev);
+
+/* Energy (Eq. 5, neighbor-list form of Sec. 4.3) and gradient of every instance at the
+ * current coordinates over the current lists: E_dev = device double[num_instances];
+ * grad_dev = device float2[sum n] (FP32 contexts) or double2[sum n] (PECC_FP64).
+ * One launch over all circles; the gradient is gathered (no atomics). */
+pecc_status pecc_energy_grad(pecc_ctx *ctx, double *E_dev, void *grad_dev);
+
+/* Same, with an explicit arithmetic: eval = PECC_FP64 (double2 gradient), PECC_FP32
+ * (float2) or PECC_FP32_POLISH64 (the mixed arithmetic of the polish: FP64 coordinates,
+ * pair differences and 4 - l^2, FP32 elsewhere; float2 gradient).  The lists must have
+ * been built in the matching precision (FP32 for PECC_FP32, FP64 otherwise):
+ * pecc_rebuild_neighbors_ex. */
+pecc_status pecc_energy_grad_ex(pecc_ctx *ctx, int32_t eval, double *E_dev, void *grad_dev);
+pecc_status pecc_rebuild_neighbors_ex(pecc_ctx *ctx, int32_t eval, int32_t force, int32_t *rebuilt_dev);
+
+/* Descend every instance from its current coordinates (Algorithm GBO with ANM, Sec. 4.1 /
+ * Sec. 4.3) as one persistent, graph-captured launch: one thread block per instance, a
+ * device work queue over instances (largest first).  PECC_FP32_POLISH64 runs the FP32
+ * descent and then the FP64 polish on instances whose FP32 energy is <= polish_gate.
+ * iters_dev (device int32[num_instances], may be NULL): sweeps done (both phases);
+ * status_dev (device int32[num_instances], may be NULL): PECC_DESC_* of the last phase. */
+pecc_status pecc_descend(pecc_ctx *ctx, int32_t *iters_dev, int32_t *status_dev);
+
+/* Per-instance energies after the last pecc_descend: device double[num_instances]. */
+pecc_status pecc_get_energy(pecc_ctx *ctx, double *E_dev);
+
+/* Feasibility (Eq. 1, Eq. 2): largest pair overlap depth over ALL pairs (a fresh FP64 cell
+ * list with cutoff l_cut > 2 holds every overlapping pair) and largest container overlap
+ * depth, in FP64 with correctly rounded operations; feasible_dev (device uint8[num]) is 1
+ * where the larger of the two is <= tol, max_overlap_dev (device double[num]) receives it. */
+pecc_status pecc_check_feasible(pecc_ctx *ctx, double tol, uint8_t *feasible_dev, double *max_overlap_dev);
+
+/* The whole path from host memory: copy R_host (double[num]) to the device, draw the
+ * initial layout from seed, descend, check feasibility with feas_tol, and copy back
+ * xy_host (double[2 sum n], may be NULL), iters_host / status_host (int32[num], may be
+ * NULL), feasible_host (uint8[num], may be NULL) and max_overlap_host (double[num], may
+ * be NULL).  Synchronises. */
+pecc_status pecc_solve_host(pecc_ctx *ctx, const double *R_host, uint64_t seed, double *xy_host,
+                            int32_t *iters_host, int32_t *status_host, uint8_t *feasible_host,
+                            double *max_overlap_host);
+
+/* Counters of the last pecc_descend, device int32[num_instances] each (may be NULL):
+ * neighbor builds, builds that changed Gamma, line-search trials. */
+pecc_status pecc_get_counters(pecc_ctx *ctx, int32_t *builds_dev, int32_t *changes_dev, int32_t *trials_dev);
+
+/* Per-instance statistics of the last pecc_descend: stats_dev = device int32[num_instances][10]:
+ * iters (both phases), status, neighbor builds, builds that changed Gamma, line-search trials,
+ * memory resets, stalled batch steps, polished (0/1), sweeps of the first phase, trials of the
+ * first phase. */
+pecc_status pecc_get_stats(pecc_ctx *ctx, int32_t *stats_dev);
+
+/* Device time of the kernels of the last pecc_descend, from events recorded on the context's
+ * stream inside the descent graph: ms_host[0] = first phase (FP64 or FP32 descent kernel),
+ * ms_host[1] = FP64 polish kernel (0 when there is none), ms_host[2] = the whole descent.
+ * Synchronises on the last event. */
+pecc_status pecc_phase_times(pecc_ctx *ctx, float *ms_host);
+
+/* The launch shape the context uses for its descent kernels. */
+pecc_status pecc_get_launch(pecc_ctx *ctx, int32_t *block_threads, int32_t *blocks_per_sm, int32_t *grid);
+
+/* Text of the last error on this context (or of the last failed pecc_create when ctx is NULL). */
+const char *pecc_last_error(pecc_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PECC_H */

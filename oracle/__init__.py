@@ -70,7 +70,7 @@ def lib():
         sig = {
             "orc_philox4x32_10": (None, [u32, u32, u32]),
             "orc_init_positions": (None, [C.c_int, C.c_double, C.c_uint64, C.c_int, C.c_int, d]),
-            "orc_cell_grid": (None, [C.c_double, C.c_double, d, _P(C.c_int)]),
+            "orc_cell_grid": (None, [C.c_double, C.c_double, C.c_int, d, _P(C.c_int)]),
             "orc_cell_keys": (None, [C.c_int, d, C.c_double, C.c_double, u32]),
             "orc_cell_sort": (None, [C.c_int, u32, C.c_int, i32, i32]),
             "orc_neighbors_brute": (C.c_int64, [C.c_int, d, C.c_double, C.c_int, i32, i32, C.c_int64]),
@@ -126,10 +126,11 @@ def init_positions(n: int, R: float, seed: int, inst: int = 0, mode: int = 0) ->
 
 
 # --------------------------------------------------------------------------- cells / neighbors
-def cell_grid(R: float, l_cut: float):
+def cell_grid(R: float, l_cut: float, n: int):
+    """Cell grid of an instance: (1 / cell side, cells per side)."""
     inv = C.c_double()
     nc = C.c_int()
-    lib().orc_cell_grid(R, l_cut, C.byref(inv), C.byref(nc))
+    lib().orc_cell_grid(R, l_cut, n, C.byref(inv), C.byref(nc))
     return inv.value, nc.value
 
 

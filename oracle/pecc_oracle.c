@@ -120,14 +120,21 @@ void orc_init_positions(int n, double R, uint64_t seed, int inst, int mode, doub
 /* so that rounding in (x + R) / cs can never put two circles closer than     */
 /* l_cut two cells apart.  Coordinates are clamped into the grid (clamping is */
 /* monotone, so it never separates a neighbor pair by more than one cell).    */
+/* A sparse instance gets at most max(16, ceil(2 sqrt n)) cells per side (the */
+/* side then grows to 2R / ncx), so cell storage stays O(n).                  */
 /* ------------------------------------------------------------------------ */
-void orc_cell_grid(double R, double l_cut, double *inv_cs, int *ncx)
+void orc_cell_grid(double R, double l_cut, int n, double *inv_cs, int *ncx)
 {
     double cs = l_cut * (1.0 + 1.0 / 1048576.0);
     double inv = 1.0 / cs;
     double w = ceil((2.0 * R) * inv);
-    int nc = (w >= 1.0) ? (int)w : 1;
-    if (nc > 65535) nc = 65535;
+    int cap = (int)ceil(2.0 * sqrt((double)n));
+    if (cap < 16) cap = 16;
+    int nc = (w >= 1.0) ? (w > 65535.0 ? 65535 : (int)w) : 1;
+    if (nc > cap) {
+        nc = cap;
+        inv = (double)nc / (2.0 * R);
+    }
     *inv_cs = inv;
     *ncx = nc;
 }
@@ -144,7 +151,7 @@ void orc_cell_keys(int n, const double *xy, double R, double l_cut, uint32_t *ke
 {
     double inv;
     int nc;
-    orc_cell_grid(R, l_cut, &inv, &nc);
+    orc_cell_grid(R, l_cut, n, &inv, &nc);
     for (int i = 0; i < n; i++) {
         int cx = cell_coord(xy[2 * i], R, inv, nc);
         int cy = cell_coord(xy[2 * i + 1], R, inv, nc);
@@ -218,7 +225,7 @@ int64_t orc_neighbors_cells(int n, const double *xy, double R, double l_cut, int
 {
     double inv;
     int nc;
-    orc_cell_grid(R, l_cut, &inv, &nc);
+    orc_cell_grid(R, l_cut, n, &inv, &nc);
     int ncell = nc * nc;
     uint32_t *key = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(n > 0 ? n : 1));
     int32_t *order = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));

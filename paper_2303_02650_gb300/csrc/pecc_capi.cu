@@ -1,0 +1,634 @@
+// pecc_capi.cu -- the C ABI (include/pecc.h): context, device buffers, launches.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "../../include/pecc.h"
+#include "pecc_internal.h"
+
+using namespace pecc;
+
+struct pecc_ctx {
+  pecc_config cfg{};
+  std::vector<int32_t> n;
+  std::vector<int32_t> k;
+  int num = 0;
+  int64_t total = 0;
+  cudaStream_t stream = nullptr;
+  int device = 0, num_sms = 1;
+  std::vector<InstDesc> desc_h;
+  std::vector<void *> allocs;
+  // device buffers
+  InstDesc *desc = nullptr;
+  InstOut *out = nullptr;
+  int32_t *order = nullptr, *queue = nullptr, *inst_of = nullptr;
+  long long *t0 = nullptr;
+  float2 *x32 = nullptr;
+  double2 *x64 = nullptr;
+  void *xw = nullptr, *xb = nullptr, *xo = nullptr, *g = nullptr, *gt = nullptr, *d = nullptr, *xbuild = nullptr;
+  void *S = nullptr, *Y = nullptr, *gram = nullptr, *ecirc = nullptr;
+  int32_t *perm = nullptr, *meta = nullptr;
+  uint64_t *skey = nullptr;
+  int32_t *rp = nullptr, *col = nullptr, *rp_s = nullptr, *col_s = nullptr;
+  uint32_t *ckey = nullptr, *ckey_s = nullptr;
+  int32_t *corder = nullptr, *corder_s = nullptr, *cells = nullptr;
+  int64_t *nnz = nullptr;
+  char *stage = nullptr;  // per-instance staging of pecc_solve_host (R, outputs)
+  size_t cells_cap = 0;
+  bool radius_set = false;
+  int lists_prec = -1;  // precision of the standalone lists: 0 FP64, 1 FP32
+  int block = 0, bps = 0, grid = 0, block_build = 256;
+  cudaGraphExec_t graph = nullptr;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  std::string err;
+};
+
+static std::string g_create_err;
+
+static pecc_status fail(pecc_ctx *c, pecc_status s, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf;
+  else g_create_err = buf;
+  return s;
+}
+
+#define CK(call)                                                                            \
+  do {                                                                                      \
+    cudaError_t e_ = (call);                                                                \
+    if (e_ != cudaSuccess) return fail(ctx, PECC_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+template <typename T> static pecc_status dalloc(pecc_ctx *ctx, T **p, size_t count) {
+  void *v = nullptr;
+  size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+  cudaError_t e = cudaMalloc(&v, bytes);
+  if (e != cudaSuccess) return fail(ctx, PECC_ERR_OOM, "cudaMalloc(%zu bytes): %s", bytes, cudaGetErrorString(e));
+  ctx->allocs.push_back(v);
+  *p = (T *)v;
+  return PECC_OK;
+}
+
+static StandaloneParams sparams(pecc_ctx *c) {
+  StandaloneParams p{};
+  p.desc = c->desc;
+  p.out = c->out;
+  p.num = c->num;
+  p.total = c->total;
+  p.inst_of = c->inst_of;
+  p.x32 = c->x32;
+  p.x64 = c->x64;
+  p.xbuild = c->xbuild;
+  p.rp = c->rp_s;
+  p.col = c->col_s;
+  p.ckey = c->ckey_s;
+  p.corder = c->corder_s;
+  p.cells = c->cells;
+  p.rp_t = c->rp;
+  p.col_t = c->col;
+  p.ckey_t = c->ckey;
+  p.corder_t = c->corder;
+  p.xtmp = c->xw;
+  p.l_cut = c->cfg.l_cut;
+  p.rebuild_disp = c->cfg.rebuild_disp;
+  return p;
+}
+
+extern "C" {
+
+void pecc_config_default(pecc_config *c) {
+  std::memset(c, 0, sizeof *c);
+  c->precision = PECC_FP32_POLISH64;
+  c->l_cut = 2.5;
+  c->rebuild_disp = 0.25;
+  c->step_max = 0.1;
+  c->lbfgs_m = 10;
+  c->max_iter = 2000;
+  c->polish_max_iter = 1000;
+  c->k_batches = 0;
+  c->partition = PECC_PART_SECTOR;
+  c->max_trials = 30;
+  c->anm = 1;
+  c->init_mode = PECC_INIT_DISK;
+  c->e_tol = 1e-20;
+  c->gsum_tol = 1e-12;
+  c->c1 = 1e-4;
+  c->curv_eps = 1e-10;
+  c->polish_gate = 1e-4;
+  c->feas_tol = 1e-9;
+  c->nbr_capacity = 16.0;
+  c->time_budget_ns = 0;
+  c->block_threads = 0;
+  c->blocks_per_sm = 0;
+  c->stall_rel = 1e-3;
+  c->stall_window = 10;
+}
+
+static int default_k(int n) { return n < 300 ? 1 : (n < 500 ? 3 : 5); }
+
+pecc_status pecc_create(const pecc_config *cfg, void *stream, pecc_ctx **out) {
+  if (!out) return fail(nullptr, PECC_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!cfg) return fail(nullptr, PECC_ERR_ARG, "cfg is NULL");
+  if (cfg->num_instances < 0 || (cfg->num_instances > 0 && !cfg->n))
+    return fail(nullptr, PECC_ERR_ARG, "num_instances < 0 or n is NULL");
+  if (cfg->precision < 0 || cfg->precision > 2) return fail(nullptr, PECC_ERR_ARG, "bad precision");
+  if (!(cfg->l_cut > 2.0)) return fail(nullptr, PECC_ERR_ARG, "l_cut must exceed 2");
+  if (!(cfg->rebuild_disp > 0.0) || !(cfg->step_max > 0.0) || !(2.0 * cfg->rebuild_disp > cfg->step_max))
+    return fail(nullptr, PECC_ERR_ARG, "need 0 < step_max < 2 * rebuild_disp");
+  if (2.0 * cfg->rebuild_disp > cfg->l_cut - 2.0 + 1e-12)
+    return fail(nullptr, PECC_ERR_ARG, "rebuild_disp must be <= (l_cut - 2) / 2");
+  if (cfg->lbfgs_m < 1 || cfg->lbfgs_m > kMaxSlots - 1) return fail(nullptr, PECC_ERR_ARG, "lbfgs_m must be in 1..10");
+  if (cfg->max_iter < 0 || cfg->polish_max_iter < 0 || cfg->max_trials < 1)
+    return fail(nullptr, PECC_ERR_ARG, "bad iteration limits");
+  if (cfg->k_batches < 0 || cfg->k_batches > kMaxK) return fail(nullptr, PECC_ERR_ARG, "k_batches must be in 0..64");
+  if (cfg->partition < 0 || cfg->partition > 2) return fail(nullptr, PECC_ERR_ARG, "bad partition");
+  if (cfg->init_mode < 0 || cfg->init_mode > 1) return fail(nullptr, PECC_ERR_ARG, "bad init_mode");
+  if (!(cfg->nbr_capacity >= 1.0)) return fail(nullptr, PECC_ERR_ARG, "nbr_capacity must be >= 1");
+  if (cfg->stall_window < 0 || !(cfg->stall_rel >= 0.0)) return fail(nullptr, PECC_ERR_ARG, "bad stall rule");
+  if (cfg->block_threads != 0 && (cfg->block_threads < 32 || cfg->block_threads % 32 ||
+                                  cfg->block_threads > descend_max_block(cfg->precision == PECC_FP64 ? 0 : 1)))
+    return fail(nullptr, PECC_ERR_ARG, "block_threads must be a multiple of 32 within the kernel's limit");
+  int64_t total = 0;
+  for (int q = 0; q < cfg->num_instances; ++q) {
+    if (cfg->n[q] < 0) return fail(nullptr, PECC_ERR_ARG, "n[%d] < 0", q);
+    total += cfg->n[q];
+  }
+  if (total > (int64_t)1 << 30) return fail(nullptr, PECC_ERR_ARG, "too many circles");
+
+  pecc_ctx *ctx = new pecc_ctx();
+  ctx->cfg = *cfg;
+  ctx->cfg.n = nullptr;
+  ctx->num = cfg->num_instances;
+  ctx->n.assign(cfg->n, cfg->n + ctx->num);
+  ctx->total = total;
+  ctx->stream = (cudaStream_t)stream;
+  auto bail = [&](pecc_status s) {
+    g_create_err = ctx->err;
+    pecc_destroy(ctx);
+    return s;
+  };
+  if (cudaGetDevice(&ctx->device) != cudaSuccess) return bail(fail(ctx, PECC_ERR_CUDA, "no CUDA device"));
+  cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device);
+
+  const int m1 = cfg->lbfgs_m + 1;
+  const bool fp64 = cfg->precision == PECC_FP64;
+  const size_t vec2 = fp64 ? sizeof(double2) : sizeof(float2);
+  const size_t vecs = fp64 ? sizeof(double) : sizeof(float);
+  ctx->desc_h.resize(ctx->num);
+  ctx->k.resize(ctx->num);
+  int64_t off = 0, rp_off = 0, col_off = 0, col_s_off = 0, gram_off = 0, meta_off = 0;
+  for (int q = 0; q < ctx->num; ++q) {
+    InstDesc &D = ctx->desc_h[q];
+    std::memset(&D, 0, sizeof D);
+    const int n = ctx->n[q];
+    int k = cfg->k_batches > 0 ? cfg->k_batches : default_k(n);
+    k = std::max(1, std::min(k, std::max(n, 1)));
+    ctx->k[q] = k;
+    D.n = n;
+    D.k = k;
+    D.cap = (int32_t)std::min<double>(std::ceil(cfg->nbr_capacity * n) + 64.0, 1.0e9);
+    D.off = off;
+    D.rp_off = rp_off;
+    D.col_off = col_off;
+    D.col_s_off = col_s_off;
+    D.gram_off = gram_off;
+    D.meta_off = meta_off;
+    D.R = 0.0;
+    off += n;
+    rp_off += 2 * (int64_t)(n + 1);
+    col_off += 2 * (int64_t)D.cap;
+    col_s_off += D.cap;
+    gram_off += (int64_t)k * kBasis * kBasis;
+    meta_off += (int64_t)k * kMetaInts;
+  }
+  pecc_status s;
+#define ALC(ptr, T, count)                                   \
+  do {                                                       \
+    T *tmp_ = nullptr;                                       \
+    if ((s = dalloc<T>(ctx, &tmp_, (size_t)(count))) != PECC_OK) return bail(s); \
+    ptr = tmp_;                                              \
+  } while (0)
+  ALC(ctx->desc, InstDesc, ctx->num);
+  ALC(ctx->out, InstOut, ctx->num);
+  ALC(ctx->order, int32_t, ctx->num);
+  ALC(ctx->queue, int32_t, 4);
+  ALC(ctx->t0, long long, 1);
+  ALC(ctx->inst_of, int32_t, total);
+  ALC(ctx->x64, double2, total);
+  if (!fp64) ALC(ctx->x32, float2, total);
+  void *p;
+  ALC(p, double2, total); ctx->xw = p;
+  ALC(p, double2, total); ctx->xb = p;
+  ALC(p, double2, total); ctx->xo = p;
+  ALC(p, double2, total); ctx->g = p;
+  ALC(p, double2, total); ctx->gt = p;
+  ALC(p, double2, total); ctx->d = p;
+  ALC(p, double2, total); ctx->xbuild = p;
+  ALC(p, char, vec2 * (size_t)m1 * (size_t)total); ctx->S = p;
+  ALC(p, char, vec2 * (size_t)m1 * (size_t)total); ctx->Y = p;
+  ALC(p, char, vecs * (size_t)gram_off); ctx->gram = p;
+  ALC(ctx->meta, int32_t, meta_off);
+  ALC(p, double, total); ctx->ecirc = p;
+  ALC(ctx->perm, int32_t, total);
+  ALC(ctx->skey, uint64_t, total);
+  ALC(ctx->rp, int32_t, rp_off);
+  ALC(ctx->col, int32_t, col_off);
+  ALC(ctx->rp_s, int32_t, total + ctx->num);
+  ALC(ctx->col_s, int32_t, col_s_off);
+  ALC(ctx->ckey, uint32_t, total);
+  ALC(ctx->ckey_s, uint32_t, total);
+  ALC(ctx->corder, int32_t, total);
+  ALC(ctx->corder_s, int32_t, total);
+  ALC(ctx->nnz, int64_t, ctx->num + 1);
+  ALC(ctx->stage, char, (size_t)ctx->num * 32);
+#undef ALC
+  // instance of every circle, processing order (largest first)
+  std::vector<int32_t> inst_of(total);
+  for (int q = 0; q < ctx->num; ++q)
+    std::fill(inst_of.begin() + ctx->desc_h[q].off, inst_of.begin() + ctx->desc_h[q].off + ctx->n[q], q);
+  std::vector<int32_t> order(ctx->num);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return ctx->n[a] > ctx->n[b]; });
+  if (total > 0 && cudaMemcpy(ctx->inst_of, inst_of.data(), sizeof(int32_t) * total, cudaMemcpyHostToDevice))
+    return bail(fail(ctx, PECC_ERR_CUDA, "upload inst_of"));
+  if (ctx->num > 0 && cudaMemcpy(ctx->order, order.data(), sizeof(int32_t) * ctx->num, cudaMemcpyHostToDevice))
+    return bail(fail(ctx, PECC_ERR_CUDA, "upload order"));
+  if (cudaMemset(ctx->out, 0, sizeof(InstOut) * std::max(ctx->num, 1)) ||
+      cudaMemset(ctx->rp_s, 0, sizeof(int32_t) * (total + ctx->num)) ||
+      cudaMemset(ctx->x64, 0, sizeof(double2) * std::max<int64_t>(total, 1)))
+    return bail(fail(ctx, PECC_ERR_CUDA, "memset"));
+
+  // launch shape
+  const int arith = cfg->precision == PECC_FP64 ? 0 : 1;
+  int nmax = 0;
+  for (int v : ctx->n) nmax = std::max(nmax, v);
+  int blk = cfg->block_threads;
+  if (blk == 0) {
+    int want = (nmax + 1) / 2;  // about two circles per thread
+    blk = std::min(descend_max_block(arith), std::max(64, (want + 31) / 32 * 32));
+    if (ctx->num > ctx->num_sms) blk = std::min(blk, 256);
+  }
+  ctx->block = blk;
+  int occ = 1;
+  {
+    cudaFuncAttributes fa{};
+    const int ar = cfg->precision == PECC_FP64 ? 0 : (cfg->precision == PECC_FP32 ? 1 : 2);
+    if (descend_occupancy(ar, blk, &occ) != cudaSuccess || occ < 1) occ = 1;
+    (void)fa;
+  }
+  ctx->bps = cfg->blocks_per_sm > 0 ? std::min(cfg->blocks_per_sm, occ) : occ;
+  ctx->grid = std::min<int64_t>(ctx->num, (int64_t)ctx->num_sms * ctx->bps);
+  for (int i = 0; i < 4; ++i)
+    if (cudaEventCreate(&ctx->ev[i]) != cudaSuccess) return bail(fail(ctx, PECC_ERR_CUDA, "cudaEventCreate"));
+  *out = ctx;
+  return PECC_OK;
+}
+
+pecc_status pecc_destroy(pecc_ctx *ctx) {
+  if (!ctx) return PECC_OK;
+  cudaStreamSynchronize(ctx->stream);
+  if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
+  for (int i = 0; i < 4; ++i)
+    if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
+  for (void *p : ctx->allocs) cudaFree(p);
+  if (ctx->cells) cudaFree(ctx->cells);
+  delete ctx;
+  return PECC_OK;
+}
+
+const char *pecc_last_error(pecc_ctx *ctx) { return ctx ? ctx->err.c_str() : g_create_err.c_str(); }
+
+// Cell grid of one instance: side l_cut (1 + 2^-20), ncx = ceil(2R / side), capped at
+// max(16, ceil(2 sqrt(n))) cells per side (the side then grows to 2R / ncx).
+static void cell_grid(double R, double l_cut, int n, double *inv, int *nc) {
+  double cs = l_cut * (1.0 + 1.0 / 1048576.0);
+  double iv = 1.0 / cs;
+  double w = std::ceil((2.0 * R) * iv);
+  int cap = std::max(16, (int)std::ceil(2.0 * std::sqrt((double)n)));
+  int c = (w >= 1.0) ? (int)std::min<double>(w, 65535.0) : 1;
+  if (c > cap) {
+    c = cap;
+    iv = (double)c / (2.0 * R);
+  }
+  *inv = iv;
+  *nc = c;
+}
+
+pecc_status pecc_set_radius(pecc_ctx *ctx, const double *R_dev) {
+  if (!ctx) return PECC_ERR_ARG;
+  if (ctx->num == 0) return PECC_OK;
+  if (!R_dev) return fail(ctx, PECC_ERR_ARG, "R_dev is NULL");
+  std::vector<double> R(ctx->num);
+  CK(cudaMemcpyAsync(R.data(), R_dev, sizeof(double) * ctx->num, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  size_t cells = 0;
+  for (int q = 0; q < ctx->num; ++q) {
+    if (!(R[q] > 0.0) || !std::isfinite(R[q])) return fail(ctx, PECC_ERR_ARG, "R[%d] must be finite and > 0", q);
+    InstDesc &D = ctx->desc_h[q];
+    D.R = R[q];
+    cell_grid(R[q], ctx->cfg.l_cut, D.n, &D.inv_cs, &D.ncx);
+    D.cell_off = (int64_t)cells;
+    cells += 2 * (size_t)D.ncx * D.ncx + 2;
+  }
+  if (cells > ctx->cells_cap) {
+    if (ctx->cells) cudaFree(ctx->cells);
+    ctx->cells = nullptr;
+    CK(cudaMalloc(&ctx->cells, cells * sizeof(int32_t)));
+    ctx->cells_cap = cells;
+  }
+  CK(cudaMemcpyAsync(ctx->desc, ctx->desc_h.data(), sizeof(InstDesc) * ctx->num, cudaMemcpyHostToDevice,
+                     ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->radius_set = true;
+  ctx->lists_prec = -1;
+  if (ctx->graph) { cudaGraphExecDestroy(ctx->graph); ctx->graph = nullptr; }
+  return PECC_OK;
+}
+
+static pecc_status need_radius(pecc_ctx *ctx) {
+  if (!ctx) return PECC_ERR_ARG;
+  if (!ctx->radius_set && ctx->num > 0) return fail(ctx, PECC_ERR_ARG, "pecc_set_radius has not been called");
+  return PECC_OK;
+}
+
+pecc_status pecc_set_positions(pecc_ctx *ctx, const double *xy_dev) {
+  if (!ctx) return PECC_ERR_ARG;
+  if (ctx->total > 0 && !xy_dev) return fail(ctx, PECC_ERR_ARG, "xy_dev is NULL");
+  CK(launch_set_positions(sparams(ctx), xy_dev, ctx->cfg.precision == PECC_FP64 ? 0 : 1, ctx->stream));
+  return PECC_OK;
+}
+
+pecc_status pecc_init_random(pecc_ctx *ctx, uint64_t seed) {
+  pecc_status s = need_radius(ctx);
+  if (s) return s;
+  CK(launch_init(sparams(ctx), seed, ctx->cfg.init_mode, ctx->cfg.precision == PECC_FP64 ? 0 : 1, ctx->stream));
+  return PECC_OK;
+}
+
+pecc_status pecc_get_positions(pecc_ctx *ctx, double *xy_dev) {
+  if (!ctx) return PECC_ERR_ARG;
+  if (ctx->total > 0 && !xy_dev) return fail(ctx, PECC_ERR_ARG, "xy_dev is NULL");
+  CK(launch_get_positions(sparams(ctx), xy_dev, ctx->cfg.precision == PECC_FP32 ? 1 : 0, ctx->stream));
+  return PECC_OK;
+}
+
+pecc_status pecc_rebuild_neighbors_ex(pecc_ctx *ctx, int32_t eval, int32_t force, int32_t *rebuilt_dev) {
+  pecc_status s = need_radius(ctx);
+  if (s) return s;
+  if (eval < 0 || eval > 2) return fail(ctx, PECC_ERR_ARG, "bad eval");
+  int prec = eval == PECC_FP32 ? 1 : 0;
+  if (prec == 1 && !ctx->x32) return fail(ctx, PECC_ERR_ARG, "FP32 lists need an FP32 context");
+  if (ctx->lists_prec != prec) force = 1;
+  CK(launch_build(sparams(ctx), prec, force, rebuilt_dev, nullptr, ctx->block_build, ctx->stream));
+  ctx->lists_prec = prec;
+  return PECC_OK;
+}
+
+pecc_status pecc_rebuild_neighbors(pecc_ctx *ctx, int32_t force, int32_t *rebuilt_dev) {
+  if (!ctx) return PECC_ERR_ARG;
+  return pecc_rebuild_neighbors_ex(ctx, ctx->cfg.precision == PECC_FP64 ? PECC_FP64 : PECC_FP32, force, rebuilt_dev);
+}
+
+pecc_status pecc_neighbor_count(pecc_ctx *ctx, int64_t *nnz_host) {
+  if (!ctx || !nnz_host) return PECC_ERR_ARG;
+  if (ctx->lists_prec < 0 && ctx->num > 0) return fail(ctx, PECC_ERR_ARG, "no neighbor lists built");
+  std::vector<int64_t> v(ctx->num);
+  CK(launch_nnz(sparams(ctx), ctx->nnz, ctx->stream));
+  if (ctx->num) CK(cudaMemcpyAsync(v.data(), ctx->nnz, sizeof(int64_t) * ctx->num, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  int64_t t = 0;
+  for (int q = 0; q < ctx->num; ++q) {
+    if (v[q] > ctx->desc_h[q].cap) return fail(ctx, PECC_ERR_NBR_OVERFLOW, "instance %d: %lld entries over capacity %d",
+                                              q, (long long)v[q], ctx->desc_h[q].cap);
+    t += v[q];
+  }
+  *nnz_host = t;
+  return PECC_OK;
+}
+
+pecc_status pecc_export_neighbors(pecc_ctx *ctx, int32_t *row_ptr_dev, int32_t *col_dev, int64_t cap) {
+  int64_t nnz = 0;
+  pecc_status s = pecc_neighbor_count(ctx, &nnz);
+  if (s) return s;
+  if (cap < nnz) return fail(ctx, PECC_ERR_ARG, "cap %lld below %lld entries", (long long)cap, (long long)nnz);
+  if (!row_ptr_dev || (nnz > 0 && !col_dev)) return fail(ctx, PECC_ERR_ARG, "NULL output");
+  std::vector<int64_t> v(ctx->num), base(ctx->num + 1, 0);
+  if (ctx->num) CK(cudaMemcpyAsync(v.data(), ctx->nnz, sizeof(int64_t) * ctx->num, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  for (int q = 0; q < ctx->num; ++q) base[q + 1] = base[q] + v[q];
+  int64_t *dbase = nullptr;
+  CK(cudaMalloc(&dbase, sizeof(int64_t) * (ctx->num + 1)));
+  cudaMemcpyAsync(dbase, base.data(), sizeof(int64_t) * (ctx->num + 1), cudaMemcpyHostToDevice, ctx->stream);
+  cudaError_t e = launch_export_csr(sparams(ctx), dbase, row_ptr_dev, col_dev, ctx->stream);
+  cudaStreamSynchronize(ctx->stream);
+  cudaFree(dbase);
+  if (e != cudaSuccess) return fail(ctx, PECC_ERR_CUDA, "export: %s", cudaGetErrorString(e));
+  return PECC_OK;
+}
+
+pecc_status pecc_export_cells(pecc_ctx *ctx, uint32_t *key_dev, int32_t *order_dev) {
+  if (!ctx) return PECC_ERR_ARG;
+  if (ctx->lists_prec < 0 && ctx->num > 0) return fail(ctx, PECC_ERR_ARG, "no neighbor lists built");
+  if (ctx->total > 0 && (!key_dev || !order_dev)) return fail(ctx, PECC_ERR_ARG, "NULL output");
+  CK(launch_export_cells(sparams(ctx), key_dev, order_dev, ctx->stream));
+  return PECC_OK;
+}
+
+pecc_status pecc_energy_grad_ex(pecc_ctx *ctx, int32_t eval, double *E_dev, void *grad_dev) {
+  pecc_status s = need_radius(ctx);
+  if (s) return s;
+  if (eval < 0 || eval > 2) return fail(ctx, PECC_ERR_ARG, "bad eval");
+  int prec = eval == PECC_FP32 ? 1 : 0;
+  if (ctx->lists_prec != prec) return fail(ctx, PECC_ERR_ARG, "neighbor lists were not built for this arithmetic");
+  if (ctx->total > 0 && (!E_dev || !grad_dev)) return fail(ctx, PECC_ERR_ARG, "NULL output");
+  if (eval == PECC_FP32_POLISH64 && ctx->cfg.precision == PECC_FP64)
+    return fail(ctx, PECC_ERR_ARG, "the mixed arithmetic needs an FP32 context");
+  CK(launch_energy_grad(sparams(ctx), eval, E_dev, grad_dev, ctx->ecirc, ctx->stream));
+  return PECC_OK;
+}
+
+pecc_status pecc_energy_grad(pecc_ctx *ctx, double *E_dev, void *grad_dev) {
+  if (!ctx) return PECC_ERR_ARG;
+  return pecc_energy_grad_ex(ctx, ctx->cfg.precision == PECC_FP64 ? PECC_FP64 : PECC_FP32, E_dev, grad_dev);
+}
+
+static DescendParams dparams(pecc_ctx *c, int phase) {
+  DescendParams p{};
+  p.desc = c->desc;
+  p.out = c->out;
+  p.num = c->num;
+  p.order = c->order;
+  p.queue = c->queue + phase;
+  p.x32 = c->x32;
+  p.x64 = c->x64;
+  p.xw = c->xw; p.xb = c->xb; p.xo = c->xo;
+  p.g = c->g; p.gt = c->gt; p.d = c->d;
+  p.S = c->S; p.Y = c->Y;
+  p.perm = c->perm;
+  p.skey = c->skey;
+  p.rp = c->rp; p.col = c->col;
+  p.ckey = c->ckey; p.corder = c->corder; p.cells = c->cells;
+  p.gram = c->gram; p.meta = c->meta;
+  const pecc_config &f = c->cfg;
+  p.l_cut = f.l_cut; p.rebuild_disp = f.rebuild_disp; p.step_max = f.step_max;
+  p.e_tol = f.e_tol; p.gsum_tol = f.gsum_tol; p.c1 = f.c1; p.curv_eps = f.curv_eps; p.polish_gate = f.polish_gate;
+  p.m = f.lbfgs_m; p.max_iter = f.max_iter; p.max_trials = f.max_trials; p.anm = f.anm; p.partition = f.partition;
+  p.stall_rel = f.stall_rel;
+  p.stall_window = f.stall_window;
+  p.t0 = c->t0;
+  p.budget_ns = f.time_budget_ns;
+  return p;
+}
+
+// The whole descent as one stream-ordered sequence (captured into a CUDA graph once).
+static cudaError_t enqueue_descend(pecc_ctx *c) {
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(c->queue, 0, 4 * sizeof(int32_t), c->stream))) return e;
+  if ((e = launch_stamp(c->t0, c->stream))) return e;
+  if ((e = cudaEventRecordWithFlags(c->ev[0], c->stream, cudaEventRecordExternal))) return e;
+  if (c->cfg.precision == PECC_FP64) {
+    if ((e = launch_descend(0, dparams(c, 0), c->grid, c->block, c->stream))) return e;
+    if ((e = cudaEventRecordWithFlags(c->ev[1], c->stream, cudaEventRecordExternal))) return e;
+    return cudaEventRecordWithFlags(c->ev[2], c->stream, cudaEventRecordExternal);
+  }
+  if ((e = launch_descend(1, dparams(c, 1), c->grid, c->block, c->stream))) return e;
+  if ((e = cudaEventRecordWithFlags(c->ev[1], c->stream, cudaEventRecordExternal))) return e;
+  if (c->cfg.precision == PECC_FP32_POLISH64) {
+    DescendParams p = dparams(c, 2);
+    p.max_iter = c->cfg.polish_max_iter;
+    if ((e = launch_descend(2, p, c->grid, c->block, c->stream))) return e;
+  }
+  return cudaEventRecordWithFlags(c->ev[2], c->stream, cudaEventRecordExternal);
+}
+
+pecc_status pecc_descend(pecc_ctx *ctx, int32_t *iters_dev, int32_t *status_dev) {
+  pecc_status s = need_radius(ctx);
+  if (s) return s;
+  if (ctx->num == 0) return PECC_OK;
+  if (!ctx->graph) {
+    cudaStream_t cs = ctx->stream;
+    bool own = false;
+    if (!cs) {  // capture needs a non-legacy stream
+      CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+      own = true;
+    }
+    cudaGraph_t graph = nullptr;
+    cudaStream_t saved = ctx->stream;
+    ctx->stream = cs;
+    CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = enqueue_descend(ctx);
+    cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+    ctx->stream = saved;
+    if (own) cudaStreamDestroy(cs);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      return fail(ctx, PECC_ERR_CUDA, "capture: %s", cudaGetErrorString(e ? e : e2));
+    }
+    e = cudaGraphInstantiate(&ctx->graph, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail(ctx, PECC_ERR_CUDA, "instantiate: %s", cudaGetErrorString(e));
+  }
+  CK(cudaGraphLaunch(ctx->graph, ctx->stream));
+  ctx->lists_prec = -1;  // the descent reuses the scratch the standalone lists rely on
+  if (iters_dev || status_dev)
+    CK(launch_outputs(ctx->out, ctx->num, iters_dev, status_dev, nullptr, nullptr, nullptr, nullptr, ctx->stream));
+  return PECC_OK;
+}
+
+pecc_status pecc_get_energy(pecc_ctx *ctx, double *E_dev) {
+  if (!ctx || (ctx->num > 0 && !E_dev)) return PECC_ERR_ARG;
+  CK(launch_outputs(ctx->out, ctx->num, nullptr, nullptr, E_dev, nullptr, nullptr, nullptr, ctx->stream));
+  return PECC_OK;
+}
+
+pecc_status pecc_get_counters(pecc_ctx *ctx, int32_t *builds_dev, int32_t *changes_dev, int32_t *trials_dev) {
+  if (!ctx) return PECC_ERR_ARG;
+  CK(launch_outputs(ctx->out, ctx->num, nullptr, nullptr, nullptr, builds_dev, changes_dev, trials_dev, ctx->stream));
+  return PECC_OK;
+}
+
+pecc_status pecc_get_stats(pecc_ctx *ctx, int32_t *stats_dev) {
+  if (!ctx || (ctx->num > 0 && !stats_dev)) return PECC_ERR_ARG;
+  CK(launch_stats(ctx->out, ctx->num, stats_dev, ctx->stream));
+  return PECC_OK;
+}
+
+pecc_status pecc_phase_times(pecc_ctx *ctx, float *ms_host) {
+  if (!ctx || !ms_host) return PECC_ERR_ARG;
+  if (!ctx->graph) return fail(ctx, PECC_ERR_ARG, "pecc_descend has not run");
+  CK(cudaEventSynchronize(ctx->ev[2]));
+  float a = 0.f, b = 0.f, c = 0.f;
+  CK(cudaEventElapsedTime(&a, ctx->ev[0], ctx->ev[1]));
+  CK(cudaEventElapsedTime(&b, ctx->ev[1], ctx->ev[2]));
+  CK(cudaEventElapsedTime(&c, ctx->ev[0], ctx->ev[2]));
+  ms_host[0] = a;
+  ms_host[1] = b;
+  ms_host[2] = c;
+  return PECC_OK;
+}
+
+pecc_status pecc_get_launch(pecc_ctx *ctx, int32_t *block_threads, int32_t *blocks_per_sm, int32_t *grid) {
+  if (!ctx) return PECC_ERR_ARG;
+  if (block_threads) *block_threads = ctx->block;
+  if (blocks_per_sm) *blocks_per_sm = ctx->bps;
+  if (grid) *grid = ctx->grid;
+  return PECC_OK;
+}
+
+pecc_status pecc_check_feasible(pecc_ctx *ctx, double tol, uint8_t *feasible_dev, double *max_overlap_dev) {
+  pecc_status s = need_radius(ctx);
+  if (s) return s;
+  CK(launch_feasible(sparams(ctx), ctx->cfg.precision == PECC_FP32 ? 1 : 0, tol, feasible_dev, max_overlap_dev,
+                     ctx->block_build, ctx->stream));
+  return PECC_OK;
+}
+
+pecc_status pecc_solve_host(pecc_ctx *ctx, const double *R_host, uint64_t seed, double *xy_host,
+                            int32_t *iters_host, int32_t *status_host, uint8_t *feasible_host,
+                            double *max_overlap_host) {
+  if (!ctx || (ctx->num > 0 && !R_host)) return PECC_ERR_ARG;
+  if (ctx->num == 0) return PECC_OK;
+  // inputs: the radii go up, the layout is drawn on the device
+  double *dR = (double *)ctx->stage;                     // [num] doubles
+  uint8_t *dfeas = (uint8_t *)(ctx->stage + 8 * (size_t)ctx->num);   // [num]
+  double *dmo = (double *)(ctx->stage + 16 * (size_t)ctx->num);      // [num]
+  int32_t *dit = (int32_t *)(ctx->stage + 24 * (size_t)ctx->num);    // [num]
+  int32_t *dst = dit + ctx->num;                                      // [num]
+  CK(cudaMemcpyAsync(dR, R_host, sizeof(double) * ctx->num, cudaMemcpyHostToDevice, ctx->stream));
+  bool same = ctx->radius_set;
+  if (same) {
+    std::vector<double> cur(ctx->num);
+    for (int q = 0; q < ctx->num; ++q) cur[q] = ctx->desc_h[q].R;
+    same = std::memcmp(cur.data(), R_host, sizeof(double) * ctx->num) == 0;
+  }
+  pecc_status s;
+  if (!same) {
+    if ((s = pecc_set_radius(ctx, dR))) return s;
+  }
+  if ((s = pecc_init_random(ctx, seed))) return s;
+  if ((s = pecc_descend(ctx, nullptr, nullptr))) return s;
+  if ((s = pecc_check_feasible(ctx, ctx->cfg.feas_tol, dfeas, dmo))) return s;
+  CK(launch_outputs(ctx->out, ctx->num, dit, dst, nullptr, nullptr, nullptr, nullptr, ctx->stream));
+  if (xy_host) {
+    double *dxy = (double *)ctx->xo;  // 2 * total doubles
+    if ((s = pecc_get_positions(ctx, dxy))) return s;
+    CK(cudaMemcpyAsync(xy_host, dxy, sizeof(double) * 2 * ctx->total, cudaMemcpyDeviceToHost, ctx->stream));
+  }
+  if (iters_host) CK(cudaMemcpyAsync(iters_host, dit, sizeof(int32_t) * ctx->num, cudaMemcpyDeviceToHost, ctx->stream));
+  if (status_host) CK(cudaMemcpyAsync(status_host, dst, sizeof(int32_t) * ctx->num, cudaMemcpyDeviceToHost, ctx->stream));
+  if (feasible_host) CK(cudaMemcpyAsync(feasible_host, dfeas, ctx->num, cudaMemcpyDeviceToHost, ctx->stream));
+  if (max_overlap_host) CK(cudaMemcpyAsync(max_overlap_host, dmo, sizeof(double) * ctx->num, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return PECC_OK;
+}
+
+}  // extern "C"

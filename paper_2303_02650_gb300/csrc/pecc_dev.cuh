@@ -1,0 +1,391 @@
+// pecc_dev.cuh -- device building blocks shared by the library's kernels.
+//
+// Elastic model of Sec. 3.2 (Eq. 3, Eq. 5), neighbor sets of Sec. 4.3, and
+// the arithmetic forms the descent runs in:
+//   Arith32  binary32 coordinates, pair math, gradient, energy accumulation
+//   Arith64  binary64 everywhere (the plain FP64 form)
+//   ArithMix binary64 coordinates, pair differences and the near-contact
+//            quantities 4 - l^2 and r^2 - (R-1)^2 (exact by Sterbenz' lemma
+//            where they cancel); binary32 for everything that only needs
+//            relative accuracy (the overlap depth from them, unit vectors,
+//            gradient, quasi-Newton vectors), binary64 energy sums.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace pecc {
+
+constexpr int kMaxSlots = 11;        // m + 1 physical secant slots, m <= 10
+constexpr int kBasis = 2 * kMaxSlots + 1;  // S slots, Y slots, g
+constexpr int kMaxK = 64;            // batches per instance
+constexpr int kMetaInts = 24;        // per batch: count, stage, ring[kMaxSlots], ...
+constexpr int kMaxThreads = 1024;
+
+// ---------------------------------------------------------------- layout ----
+struct InstDesc {
+  int32_t n, k, ncx, cap;   // circles, batches, cells per side, CSR capacity per buffer
+  int64_t off;              // first circle (positions, per-circle scratch)
+  int64_t rp_off;           // 2 * (n + 1) row pointers (two CSR buffers)
+  int64_t col_off;          // 2 * cap column entries (descent lists)
+  int64_t col_s_off;        // cap column entries (standalone lists; row pointers at off + index)
+  int64_t cell_off;         // 2 * ncell + 2 cell counters
+  int64_t gram_off;         // k * kBasis * kBasis Gram entries
+  int64_t meta_off;         // k * kMetaInts ring metadata
+  double R, inv_cs;
+};
+
+struct InstOut {
+  int32_t iters, status, builds, changes, trials, resets, stalls, polished;
+  int32_t iters32, status32, trials32, cur;
+  double E, E32, max_overlap, pad;
+};
+
+// ------------------------------------------------------------ vec types ----
+template <typename T> struct V2;
+template <> struct V2<float> { using type = float2; };
+template <> struct V2<double> { using type = double2; };
+template <typename T> using v2 = typename V2<T>::type;
+
+template <typename T> __device__ __forceinline__ v2<T> mk2(T a, T b) { v2<T> r; r.x = a; r.y = b; return r; }
+
+// ---------------------------------------------------------------- philox ---
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11).
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) { k.x += 0x9E3779B9u; k.y += 0xBB67AE85u; }
+    uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+    uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+    uint4 n;
+    n.x = hi1 ^ c.y ^ k.x;
+    n.y = lo1;
+    n.z = hi0 ^ c.w ^ k.y;
+    n.w = lo0;
+    c = n;
+  }
+  return c;
+}
+
+__device__ __forceinline__ double u53(uint32_t hi, uint32_t lo) {
+  uint64_t w = ((uint64_t)hi << 32) | (uint64_t)lo;
+  return __dmul_rn((double)(w >> 11), 1.0 / 9007199254740992.0);
+}
+
+// ---------------------------------------------------------------- cells ----
+__device__ __forceinline__ int cell_coord(double v, double R, double inv, int nc) {
+  double f = __dmul_rn(__dadd_rn(v, R), inv);
+  if (!(f >= 0.0)) return 0;
+  if (f >= (double)nc) return nc - 1;
+  return (int)f;
+}
+
+template <typename T>
+__device__ __forceinline__ uint32_t cell_key(v2<T> p, double R, double inv, int nc) {
+  int cx = cell_coord((double)p.x, R, inv, nc);
+  int cy = cell_coord((double)p.y, R, inv, nc);
+  return (uint32_t)cy * (uint32_t)nc + (uint32_t)cx;
+}
+
+// Neighbor predicate of Sec. 4.3: dx*dx + dy*dy < l_cut^2 with every operation
+// correctly rounded (no contraction), in the coordinates' own precision.
+__device__ __forceinline__ bool nbr_pred(float2 a, float2 b, float lc2) {
+  float dx = __fsub_rn(a.x, b.x), dy = __fsub_rn(a.y, b.y);
+  float s = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
+  return s < lc2;
+}
+__device__ __forceinline__ bool nbr_pred(double2 a, double2 b, double lc2) {
+  double dx = __dsub_rn(a.x, b.x), dy = __dsub_rn(a.y, b.y);
+  double s = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+  return s < lc2;
+}
+
+// ------------------------------------------------------------ reductions ---
+template <typename T> __device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+template <typename T> __device__ __forceinline__ T warp_max(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Block-wide sum of NV values per thread; every thread receives the totals in out[].
+// scratch: at least (blockDim/32) * NV elements of T in shared memory.
+template <typename T, int NV>
+__device__ __forceinline__ void block_sum(T (&v)[NV], T *scratch, T *out) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int q = 0; q < NV; ++q) {
+    T s = warp_sum(v[q]);
+    if (lane == 0) scratch[w * NV + q] = s;
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < NV; q += blockDim.x) {
+    T s = T(0);
+    for (int u = 0; u < nw; ++u) s += scratch[u * NV + q];
+    out[q] = s;
+  }
+  __syncthreads();
+}
+
+// Inclusive prefix sum of a[0..len) in place (int32), whole block.
+__device__ inline void block_scan_inplace(int32_t *a, int len, int32_t *sh /*>=33 ints*/) {
+  const int T = blockDim.x, t = threadIdx.x, lane = t & 31, w = t >> 5, nw = T >> 5;
+  int ch = (len + T - 1) / T;
+  int lo = min(len, t * ch), hi = min(len, lo + ch);
+  int32_t s = 0;
+  for (int i = lo; i < hi; ++i) s += a[i];
+  int32_t incl = s;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int32_t u = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += u;
+  }
+  if (lane == 31) sh[w] = incl;
+  __syncthreads();
+  if (w == 0) {
+    int32_t v = lane < nw ? sh[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int32_t u = __shfl_up_sync(0xffffffffu, v, o);
+      if (lane >= o) v += u;
+    }
+    if (lane < nw) sh[lane] = v;
+  }
+  __syncthreads();
+  int32_t run = incl - s + (w > 0 ? sh[w - 1] : 0);
+  for (int i = lo; i < hi; ++i) { run += a[i]; a[i] = run; }
+  __syncthreads();
+}
+
+// ------------------------------------------------------- neighbor build ----
+// Cell binning and stable key sort, then CSR rows over the 3x3 cells, each row
+// ascending.  x: n positions of one instance; lists go to rp[0..n], col[0..cap).
+// cells: 2 * ncell + 2 int32 of scratch; ckey/corder: n each.
+// Returns the number of entries (block-uniform); > cap means overflow and the
+// rows are then incomplete.
+template <typename T>
+__device__ int cta_build_neighbors(const v2<T> *__restrict__ x, int n, double R, double inv, int nc,
+                                   T lc2, uint32_t *ckey, int32_t *corder, int32_t *cells,
+                                   int32_t *rp, int32_t *col, int cap, int32_t *sh) {
+  const int T_ = blockDim.x, t = threadIdx.x;
+  const int ncell = nc * nc;
+  int32_t *cstart = cells;              // ncell + 1
+  int32_t *cfill = cells + ncell + 1;   // ncell
+  for (int c = t; c <= ncell; c += T_) cstart[c] = 0;
+  __syncthreads();
+  for (int i = t; i < n; i += T_) {
+    uint32_t key = cell_key<T>(x[i], R, inv, nc);
+    ckey[i] = key;
+    atomicAdd(&cstart[key + 1], 1);
+  }
+  __syncthreads();
+  block_scan_inplace(cstart + 1, ncell, sh);
+  for (int c = t; c < ncell; c += T_) cfill[c] = cstart[c];
+  __syncthreads();
+  for (int i = t; i < n; i += T_) {
+    int p = atomicAdd(&cfill[ckey[i]], 1);
+    corder[p] = i;
+  }
+  __syncthreads();
+  // stable order: sort every cell's members by index
+  for (int c = t; c < ncell; c += T_) {
+    int lo = cstart[c], hi = cstart[c + 1];
+    for (int a = lo + 1; a < hi; ++a) {
+      int v = corder[a], b = a - 1;
+      while (b >= lo && corder[b] > v) { corder[b + 1] = corder[b]; --b; }
+      corder[b + 1] = v;
+    }
+  }
+  __syncthreads();
+  // count
+  if (t == 0) rp[0] = 0;
+  for (int i = t; i < n; i += T_) {
+    v2<T> xi = x[i];
+    uint32_t key = ckey[i];
+    int cx = (int)(key % (uint32_t)nc), cy = (int)(key / (uint32_t)nc);
+    int cntn = 0;
+    for (int by = max(cy - 1, 0); by <= min(cy + 1, nc - 1); ++by)
+      for (int bx = max(cx - 1, 0); bx <= min(cx + 1, nc - 1); ++bx) {
+        int c = by * nc + bx;
+        for (int q = cstart[c]; q < cstart[c + 1]; ++q) {
+          int j = corder[q];
+          if (j != i && nbr_pred(xi, x[j], lc2)) ++cntn;
+        }
+      }
+    rp[i + 1] = cntn;
+  }
+  __syncthreads();
+  block_scan_inplace(rp + 1, n, sh);
+  const int total = rp[n];
+  if (total <= cap) {
+    for (int i = t; i < n; i += T_) {
+      v2<T> xi = x[i];
+      uint32_t key = ckey[i];
+      int cx = (int)(key % (uint32_t)nc), cy = (int)(key / (uint32_t)nc);
+      int w = rp[i], lo = w;
+      for (int by = max(cy - 1, 0); by <= min(cy + 1, nc - 1); ++by)
+        for (int bx = max(cx - 1, 0); bx <= min(cx + 1, nc - 1); ++bx) {
+          int c = by * nc + bx;
+          for (int q = cstart[c]; q < cstart[c + 1]; ++q) {
+            int j = corder[q];
+            if (j != i && nbr_pred(xi, x[j], lc2)) col[w++] = j;
+          }
+        }
+      for (int a = lo + 1; a < w; ++a) {
+        int v = col[a], b = a - 1;
+        while (b >= lo && col[b] > v) { col[b + 1] = col[b]; --b; }
+        col[b + 1] = v;
+      }
+    }
+  }
+  __syncthreads();
+  return total;
+}
+
+// ------------------------------------------------------- pair arithmetic ---
+// pair(): for circles a (the row owner) and b, returns the overlap depth d >= 0
+// (0 when l >= 2) and the gradient contribution to a: -2 d (a - b) / l.
+// A coincident pair contributes d = 2 and no gradient.
+struct Arith32 {
+  using pos_t = float;
+  using vec_t = float;
+  using acc_t = float;
+  static constexpr int kId = 1;
+  __device__ static __forceinline__ acc_t pair(float2 a, float2 b, float &fx, float &fy) {
+    float dx = a.x - b.x, dy = a.y - b.y;
+    float s = dx * dx + dy * dy;
+    fx = 0.f; fy = 0.f;
+    if (!(s < 4.f)) return 0.f;
+    if (s > 0.f) {
+      float rl = rsqrtf(s);
+      float d = 2.f - s * rl;
+      float c = -2.f * d * rl;
+      fx = c * dx; fy = c * dy;
+      return d > 0.f ? d : 0.f;
+    }
+    return 2.f;
+  }
+  // container term: depth d_i0 and gradient 2 d_i0 c_i / |c_i|
+  __device__ static __forceinline__ acc_t wall(float2 a, float R, float Rm1sq, float &fx, float &fy) {
+    float r2 = a.x * a.x + a.y * a.y;
+    float r = sqrtf(r2);
+    float d = r + 1.f - R;
+    fx = 0.f; fy = 0.f;
+    if (!(d > 0.f)) return 0.f;
+    if (r > 0.f) { float c = 2.f * d / r; fx = c * a.x; fy = c * a.y; }
+    return d;
+  }
+};
+
+__device__ __forceinline__ double rsqrt_d(double s) {
+  // binary32 estimate refined by two Newton steps in binary64 (s >= 1e-30)
+  double y = (double)rsqrtf((float)s);
+  double h = 0.5 * s;
+  y = y * fma(-h * y, y, 1.5);
+  y = y * fma(-h * y, y, 1.5);
+  return y;
+}
+
+struct Arith64 {
+  using pos_t = double;
+  using vec_t = double;
+  using acc_t = double;
+  static constexpr int kId = 0;
+  __device__ static __forceinline__ acc_t pair(double2 a, double2 b, double &fx, double &fy) {
+    double dx = a.x - b.x, dy = a.y - b.y;
+    double s = fma(dx, dx, dy * dy);
+    fx = 0.0; fy = 0.0;
+    if (!(s < 4.0)) return 0.0;
+    if (s > 1e-30) {
+      double rl = rsqrt_d(s);
+      double d = 2.0 - s * rl;
+      double c = -2.0 * d * rl;
+      fx = c * dx; fy = c * dy;
+      return d > 0.0 ? d : 0.0;
+    }
+    if (s > 0.0) {
+      double l = sqrt(s);
+      double c = -2.0 * (2.0 - l) / l;
+      fx = c * dx; fy = c * dy;
+      return 2.0 - l;
+    }
+    return 2.0;
+  }
+  // Rm1sq = (R - 1)^2 when R >= 1, else -1 (every circle then touches the wall)
+  __device__ static __forceinline__ acc_t wall(double2 a, double R, double Rm1sq, double &fx, double &fy) {
+    double r2 = fma(a.x, a.x, a.y * a.y);
+    fx = 0.0; fy = 0.0;
+    if (!(r2 > Rm1sq)) return 0.0;  // |c| <= R - 1: no contact
+    if (r2 <= 1e-30) { double d = sqrt(r2) + 1.0 - R; return d > 0.0 ? d : 0.0; }
+    double rl = rsqrt_d(r2);
+    double r = r2 * rl;
+    double d = r + 1.0 - R;
+    if (!(d > 0.0)) return 0.0;
+    double c = 2.0 * d * rl;
+    fx = c * a.x; fy = c * a.y;
+    return d;
+  }
+};
+
+struct ArithMix {
+  using pos_t = double;
+  using vec_t = float;
+  using acc_t = double;
+  static constexpr int kId = 2;
+  __device__ static __forceinline__ acc_t pair(double2 a, double2 b, float &fx, float &fy) {
+    double dx = a.x - b.x, dy = a.y - b.y;
+    double s = fma(dx, dx, dy * dy);
+    fx = 0.f; fy = 0.f;
+    if (!(s < 4.0)) return 0.0;
+    if (s > 1e-30) {
+      float e = (float)(4.0 - s);       // exact cancellation near contact
+      float rl = rsqrtf((float)s);
+      float l = (float)s * rl;
+      float d = e / (2.f + l);          // 2 - l = (4 - l^2) / (2 + l)
+      float c = -2.f * d * rl;
+      fx = c * (float)dx; fy = c * (float)dy;
+      return (double)d;
+    }
+    return 2.0;
+  }
+  __device__ static __forceinline__ acc_t wall(double2 a, double R, double Rm1sq, float &fx, float &fy) {
+    double r2 = fma(a.x, a.x, a.y * a.y);
+    fx = 0.f; fy = 0.f;
+    if (!(r2 > Rm1sq)) return 0.0;
+    if (Rm1sq < 0.0 || r2 <= 1e-30) {   // degenerate container R < 1, or a centred circle
+      double r = sqrt(r2), d = r + 1.0 - R;
+      if (r > 0.0) { float c = (float)(2.0 * d / r); fx = c * (float)a.x; fy = c * (float)a.y; }
+      return d > 0.0 ? d : 0.0;
+    }
+    float e = (float)(r2 - Rm1sq);      // |c|^2 - (R-1)^2, exact near contact
+    float r = sqrtf((float)r2);
+    float d = e / (r + (float)(R - 1.0));  // |c| - (R - 1)
+    float c = 2.f * d / r;
+    fx = c * (float)a.x; fy = c * (float)a.y;
+    return (double)d;
+  }
+};
+
+// Exact container depth with correctly rounded operations (feasibility check).
+__device__ __forceinline__ double wall_depth_exact(double2 a, double R) {
+  double r = __dsqrt_rn(__dadd_rn(__dmul_rn(a.x, a.x), __dmul_rn(a.y, a.y)));
+  double d = __dsub_rn(__dadd_rn(r, 1.0), R);
+  return d > 0.0 ? d : 0.0;
+}
+__device__ __forceinline__ double pair_depth_exact(double2 a, double2 b) {
+  double dx = __dsub_rn(a.x, b.x), dy = __dsub_rn(a.y, b.y);
+  double s = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+  return __dsub_rn(2.0, __dsqrt_rn(s));
+}
+
+__device__ __forceinline__ long long globaltimer_ns() {
+  long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+}  // namespace pecc

@@ -1,0 +1,84 @@
+// pecc_internal.h -- host-side declarations shared by the library's translation units.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "pecc_dev.cuh"
+
+namespace pecc {
+
+// Everything a descent kernel reads or writes; device pointers into the context's buffers.
+struct DescendParams {
+  const InstDesc *desc;
+  InstOut *out;
+  int num;
+  const int32_t *order;  // processing order of instances (largest first)
+  int32_t *queue;        // work counter, zeroed before each launch
+  float2 *x32;
+  double2 *x64;
+  void *xw, *xb, *xo;    // per-circle positions scratch (sized for double2)
+  void *g, *gt, *d;      // per-circle vectors (sized for double2)
+  void *S, *Y;           // (m + 1) secant slots per circle
+  int32_t *perm;
+  uint64_t *skey;
+  int32_t *rp, *col;
+  uint32_t *ckey;
+  int32_t *corder, *cells;
+  void *gram;
+  int32_t *meta;
+  double l_cut, rebuild_disp, step_max, e_tol, gsum_tol, c1, curv_eps, polish_gate;
+  int m, max_iter, max_trials, anm, partition;
+  double stall_rel;       // FP32 phase: stop when E fell by less than this over stall_window sweeps
+  int stall_window;
+  const long long *t0;    // %globaltimer at the start of the call (written by stamp_kernel)
+  long long budget_ns;    // 0 = no time budget
+};
+
+cudaError_t launch_stamp(long long *t0, cudaStream_t s);
+
+// Launchers (pecc_descend.cu).  arith: PECC_FP64 (plain), PECC_FP32 (bulk), PECC_FP32_POLISH64 (polish).
+cudaError_t launch_descend(int arith, const DescendParams &p, int grid, int block, cudaStream_t s);
+cudaError_t descend_attributes(int arith, cudaFuncAttributes *attr);
+int descend_max_block(int arith);
+cudaError_t descend_occupancy(int arith, int block, int *blocks_per_sm);
+
+// Standalone kernels (pecc_kernels.cu).
+struct StandaloneParams {
+  const InstDesc *desc;
+  InstOut *out;
+  int num;
+  int64_t total;
+  const int32_t *inst_of;
+  float2 *x32;
+  double2 *x64;
+  void *xbuild;  // positions at the last standalone build (double2 size)
+  int32_t *rp, *col;          // the standalone lists (one buffer per instance)
+  uint32_t *ckey;
+  int32_t *corder, *cells;
+  int32_t *rp_t, *col_t;      // scratch lists of the feasibility check (the descent's buffers)
+  uint32_t *ckey_t;
+  int32_t *corder_t;
+  void *xtmp;                 // per-circle double2 scratch
+  double l_cut, rebuild_disp;
+};
+
+cudaError_t launch_init(const StandaloneParams &p, uint64_t seed, int mode, int prec, cudaStream_t s);
+cudaError_t launch_set_positions(const StandaloneParams &p, const double *xy, int prec, cudaStream_t s);
+cudaError_t launch_get_positions(const StandaloneParams &p, double *xy, int from32, cudaStream_t s);
+cudaError_t launch_set_radius(InstDesc *desc, const double *R, int num, cudaStream_t s);
+cudaError_t launch_build(const StandaloneParams &p, int prec, int force, int32_t *rebuilt, int32_t *status,
+                         int block, cudaStream_t s);
+cudaError_t launch_energy_grad(const StandaloneParams &p, int eval, double *E, void *grad, void *ecirc,
+                               cudaStream_t s);
+cudaError_t launch_feasible(const StandaloneParams &p, int from32, double tol, uint8_t *feasible,
+                            double *max_overlap, int block, cudaStream_t s);
+cudaError_t launch_export_csr(const StandaloneParams &p, const int64_t *base, int32_t *row_ptr, int32_t *col,
+                              cudaStream_t s);
+cudaError_t launch_export_cells(const StandaloneParams &p, uint32_t *key, int32_t *order, cudaStream_t s);
+cudaError_t launch_nnz(const StandaloneParams &p, int64_t *nnz, cudaStream_t s);
+cudaError_t launch_stats(const InstOut *out, int num, int32_t *stats, cudaStream_t s);
+cudaError_t launch_outputs(const InstOut *out, int num, int32_t *iters, int32_t *status, double *E,
+                           int32_t *builds, int32_t *changes, int32_t *trials, cudaStream_t s);
+
+}  // namespace pecc

@@ -1,0 +1,351 @@
+// pecc_kernels.cu -- standalone kernels: random init (Sec. 5.1), neighbor build
+// (Sec. 4.3), fused energy + gradient (Eq. 3, Eq. 5), feasibility (Eq. 1, Eq. 2).
+#include "pecc_internal.h"
+
+namespace pecc {
+
+namespace {
+
+// ------------------------------------------------------------------ init ----
+// Circle i of instance q: Philox4x32-10, key (seed lo, seed hi), counter (i, attempt, q, 0);
+// (w0, w1) and (w2, w3) give two 53-bit uniforms u, v; candidate (R-1)(2u-1, 2v-1),
+// accepted inside the disk of radius R-1 (mode 0), or R (2u-1, 2v-1) in the square (mode 1).
+__global__ void init_kernel(StandaloneParams P, uint64_t seed, int mode, int prec) {
+  int64_t gi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gi >= P.total) return;
+  const int q = P.inst_of[gi];
+  const InstDesc D = P.desc[q];
+  const uint32_t i = (uint32_t)(gi - D.off);
+  const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+  const double R = D.R, rr = __dsub_rn(R, 1.0);
+  double x = 0.0, y = 0.0;
+  if (mode == 1) {
+    uint4 w = philox4x32_10(make_uint4(i, 0u, (uint32_t)q, 0u), key);
+    x = __dmul_rn(R, __dsub_rn(__dmul_rn(2.0, u53(w.x, w.y)), 1.0));
+    y = __dmul_rn(R, __dsub_rn(__dmul_rn(2.0, u53(w.z, w.w)), 1.0));
+  } else if (rr > 0.0) {
+    for (uint32_t a = 0; a < 64u; ++a) {
+      uint4 w = philox4x32_10(make_uint4(i, a, (uint32_t)q, 0u), key);
+      double cx = __dmul_rn(rr, __dsub_rn(__dmul_rn(2.0, u53(w.x, w.y)), 1.0));
+      double cy = __dmul_rn(rr, __dsub_rn(__dmul_rn(2.0, u53(w.z, w.w)), 1.0));
+      if (__dadd_rn(__dmul_rn(cx, cx), __dmul_rn(cy, cy)) <= __dmul_rn(rr, rr)) { x = cx; y = cy; break; }
+    }
+  }
+  if (prec == 0) {
+    P.x64[gi] = make_double2(x, y);
+  } else {
+    float2 f = make_float2((float)x, (float)y);
+    P.x32[gi] = f;
+    P.x64[gi] = make_double2((double)f.x, (double)f.y);
+  }
+}
+
+__global__ void set_pos_kernel(StandaloneParams P, const double *__restrict__ xy, int prec) {
+  int64_t gi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gi >= P.total) return;
+  double x = xy[2 * gi], y = xy[2 * gi + 1];
+  if (prec == 0) {
+    P.x64[gi] = make_double2(x, y);
+  } else {
+    float2 f = make_float2((float)x, (float)y);
+    P.x32[gi] = f;
+    P.x64[gi] = make_double2((double)f.x, (double)f.y);
+  }
+}
+
+__global__ void get_pos_kernel(StandaloneParams P, double *__restrict__ xy, int from32) {
+  int64_t gi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gi >= P.total) return;
+  double2 v;
+  if (from32) { float2 f = P.x32[gi]; v = make_double2((double)f.x, (double)f.y); }
+  else v = P.x64[gi];
+  xy[2 * gi] = v.x;
+  xy[2 * gi + 1] = v.y;
+}
+
+__global__ void set_radius_kernel(InstDesc *desc, const double *__restrict__ R, int num) {
+  int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < num) desc[q].R = R[q];
+}
+
+// ----------------------------------------------------------------- build ----
+template <typename T>
+__global__ void build_kernel(StandaloneParams P, int force, int32_t *rebuilt, int32_t *status) {
+  __shared__ int32_t sh[40];
+  using PP = v2<T>;
+  const int q = blockIdx.x;
+  const InstDesc D = P.desc[q];
+  const int n = D.n;
+  const PP *x;
+  if constexpr (sizeof(T) == 4) x = (const PP *)(P.x32 + D.off);
+  else x = (const PP *)(P.x64 + D.off);
+  PP *xb = (PP *)P.xbuild + D.off;
+  int go = force;
+  if (!go) {
+    // largest displacement since the last standalone build
+    double m = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      PP a = x[i], b = xb[i];
+      double dx = (double)a.x - (double)b.x, dy = (double)a.y - (double)b.y;
+      m = fmax(m, dx * dx + dy * dy);
+    }
+    go = __syncthreads_or(m > P.rebuild_disp * P.rebuild_disp);
+  }
+  if (go) {
+    const T lc2 = (T)(P.l_cut * P.l_cut);
+    int tot = cta_build_neighbors<T>(x, n, D.R, D.inv_cs, D.ncx, lc2, P.ckey + D.off, P.corder + D.off,
+                                     P.cells + D.cell_off, P.rp + D.off + q, P.col + D.col_s_off, D.cap, sh);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) xb[i] = x[i];
+    if (threadIdx.x == 0 && status) status[q] = tot > D.cap ? 4 : 0;
+  } else if (threadIdx.x == 0 && status) {
+    status[q] = 0;
+  }
+  if (threadIdx.x == 0 && rebuilt) rebuilt[q] = go;
+}
+
+// ------------------------------------------------- fused energy + gradient ----
+// One thread per circle (gather over its row, no atomics):
+//   g_i = sum_{j in Gamma(i)} -2 d_ij (c_i - c_j) / l_ij + 2 d_i0 c_i / |c_i|
+//   e_i = sum_{j in Gamma(i), j < i} d_ij^2 + d_i0^2      (so that E = sum_i e_i, Eq. 5)
+template <class A>
+__global__ void __launch_bounds__(256) energy_grad_kernel(StandaloneParams P, void *__restrict__ grad_,
+                                                          void *__restrict__ ecirc_) {
+  using pos_t = typename A::pos_t;
+  using vec_t = typename A::vec_t;
+  using acc_t = typename A::acc_t;
+  using PP = v2<pos_t>;
+  using VV = v2<vec_t>;
+  int64_t gi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gi >= P.total) return;
+  const int q = __ldg(P.inst_of + gi);
+  const int64_t off = P.desc[q].off;
+  const int64_t col_off = P.desc[q].col_s_off;
+  const double Rd = P.desc[q].R;
+  const acc_t R = (acc_t)Rd;
+  const acc_t Rm1sq = (acc_t)((Rd >= 1.0) ? (Rd - 1.0) * (Rd - 1.0) : -1.0);
+  const PP *x = (sizeof(pos_t) == 4) ? (const PP *)(P.x32 + off) : (const PP *)(P.x64 + off);
+  const int i = (int)(gi - off);
+  const int32_t *rp = P.rp + off + q;
+  const int32_t *cl = P.col + col_off;
+  PP xi = x[i];
+  vec_t gx = 0, gy = 0;
+  acc_t e = 0;
+  const int lo = __ldg(rp + i), hi = __ldg(rp + i + 1);
+  for (int t = lo; t < hi; ++t) {
+    int j = __ldg(cl + t);
+    vec_t fx, fy;
+    acc_t d = A::pair(xi, x[j], fx, fy);
+    gx += fx; gy += fy;
+    if (j < i) e += d * d;
+  }
+  vec_t fx, fy;
+  acc_t d0 = A::wall(xi, R, Rm1sq, fx, fy);
+  gx += fx; gy += fy;
+  e += d0 * d0;
+  VV gv; gv.x = gx; gv.y = gy;
+  ((VV *)grad_)[gi] = gv;
+  ((acc_t *)ecirc_)[gi] = e;
+}
+
+// Per-instance sum of the per-circle energies (fixed order: deterministic).
+template <typename acc_t>
+__global__ void energy_reduce_kernel(StandaloneParams P, const acc_t *__restrict__ ecirc, double *E) {
+  __shared__ acc_t sh[32];
+  const int q = blockIdx.x;
+  const InstDesc D = P.desc[q];
+  acc_t s = 0;
+  for (int i = threadIdx.x; i < D.n; i += blockDim.x) s += ecirc[D.off + i];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    acc_t v = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : acc_t(0);
+    v = warp_sum(v);
+    if (threadIdx.x == 0) E[q] = (double)v;
+  }
+}
+
+// ----------------------------------------------------------- feasibility ----
+// A fresh FP64 list with cutoff l_cut > 2 holds every pair with l_ij < 2, so the largest
+// depth over the list equals the largest over all pairs (Eq. 1); walls per circle (Eq. 2).
+__global__ void feasible_kernel(StandaloneParams P, int from32, double tol, uint8_t *feasible,
+                                double *max_overlap) {
+  __shared__ int32_t sh[40];
+  __shared__ double red[32];
+  const int q = blockIdx.x;
+  const InstDesc D = P.desc[q];
+  const int n = D.n;
+  double2 *x = (double2 *)P.xtmp + D.off;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    if (from32) { float2 f = P.x32[D.off + i]; x[i] = make_double2((double)f.x, (double)f.y); }
+    else x[i] = P.x64[D.off + i];
+  }
+  __syncthreads();
+  int32_t *rp = P.rp_t + D.rp_off;
+  int32_t *cl = P.col_t + D.col_off;
+  const double lc2 = P.l_cut * P.l_cut;
+  int tot = cta_build_neighbors<double>(x, n, D.R, D.inv_cs, D.ncx, lc2, P.ckey_t + D.off, P.corder_t + D.off,
+                                        P.cells + D.cell_off, rp, cl, 2 * D.cap, sh);
+  double m = 0.0;
+  int bad = 0;
+  if (tot <= 2 * D.cap) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      double2 xi = x[i];
+      bad |= !(isfinite(xi.x) && isfinite(xi.y));
+      for (int t = rp[i]; t < rp[i + 1]; ++t) {
+        int j = cl[t];
+        if (j > i) m = fmax(m, pair_depth_exact(xi, x[j]));
+      }
+      m = fmax(m, wall_depth_exact(xi, D.R));
+    }
+  } else {
+    bad = 1;
+  }
+  m = warp_max(m);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  bad = __syncthreads_or(bad);
+  if (threadIdx.x == 0) {
+    double v = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v = fmax(v, red[w]);
+    if (bad) v = __longlong_as_double(0x7ff8000000000000ll);  // NaN: not checkable
+    bool ok = !bad && v <= tol;
+    if (feasible) feasible[q] = ok ? 1 : 0;
+    if (max_overlap) max_overlap[q] = v;
+    P.out[q].max_overlap = v;
+  }
+}
+
+// ---------------------------------------------------------------- export ----
+__global__ void export_csr_kernel(StandaloneParams P, const int64_t *__restrict__ base, int32_t *row_ptr,
+                                  int32_t *col) {
+  int64_t gi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gi >= P.total) {
+    if (gi == P.total && P.num > 0) row_ptr[P.total] = (int32_t)base[P.num];
+    return;
+  }
+  const int q = P.inst_of[gi];
+  const InstDesc D = P.desc[q];
+  const int i = (int)(gi - D.off);
+  const int32_t *rp = P.rp + D.off + q;
+  const int lo = rp[i], hi = rp[i + 1];
+  const int64_t b = base[q];
+  row_ptr[gi] = (int32_t)(b + lo);
+  for (int t = lo; t < hi; ++t) col[b + t] = (int32_t)(D.off + P.col[D.col_s_off + t]);
+}
+
+__global__ void export_cells_kernel(StandaloneParams P, uint32_t *key, int32_t *order) {
+  int64_t gi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gi >= P.total) return;
+  key[gi] = P.ckey[gi];
+  order[gi] = P.corder[gi];
+}
+
+__global__ void nnz_kernel(StandaloneParams P, int64_t *nnz) {
+  int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= P.num) return;
+  const InstDesc D = P.desc[q];
+  nnz[q] = (int64_t)P.rp[D.off + q + D.n];
+}
+
+__global__ void outputs_kernel(const InstOut *out, int num, int32_t *iters, int32_t *status, double *E,
+                               int32_t *builds, int32_t *changes, int32_t *trials) {
+  int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= num) return;
+  if (iters) iters[q] = out[q].iters;
+  if (status) status[q] = out[q].status;
+  if (E) E[q] = out[q].E;
+  if (builds) builds[q] = out[q].builds;
+  if (changes) changes[q] = out[q].changes;
+  if (trials) trials[q] = out[q].trials;
+}
+
+__global__ void stats_kernel(const InstOut *out, int num, int32_t *st) {
+  int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= num) return;
+  const InstOut o = out[q];
+  int32_t *r = st + 10 * (int64_t)q;
+  r[0] = o.iters; r[1] = o.status; r[2] = o.builds; r[3] = o.changes; r[4] = o.trials;
+  r[5] = o.resets; r[6] = o.stalls; r[7] = o.polished; r[8] = o.iters32; r[9] = o.trials32;
+}
+
+inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+cudaError_t launch_init(const StandaloneParams &p, uint64_t seed, int mode, int prec, cudaStream_t s) {
+  if (p.total > 0) init_kernel<<<blocks_for(p.total, 256), 256, 0, s>>>(p, seed, mode, prec);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_positions(const StandaloneParams &p, const double *xy, int prec, cudaStream_t s) {
+  if (p.total > 0) set_pos_kernel<<<blocks_for(p.total, 256), 256, 0, s>>>(p, xy, prec);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_get_positions(const StandaloneParams &p, double *xy, int from32, cudaStream_t s) {
+  if (p.total > 0) get_pos_kernel<<<blocks_for(p.total, 256), 256, 0, s>>>(p, xy, from32);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_radius(InstDesc *desc, const double *R, int num, cudaStream_t s) {
+  if (num > 0) set_radius_kernel<<<blocks_for(num, 128), 128, 0, s>>>(desc, R, num);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_build(const StandaloneParams &p, int prec, int force, int32_t *rebuilt, int32_t *status,
+                         int block, cudaStream_t s) {
+  if (p.num <= 0) return cudaSuccess;
+  if (prec == 1) build_kernel<float><<<p.num, block, 0, s>>>(p, force, rebuilt, status);
+  else build_kernel<double><<<p.num, block, 0, s>>>(p, force, rebuilt, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_energy_grad(const StandaloneParams &p, int eval, double *E, void *grad, void *ecirc,
+                               cudaStream_t s) {
+  if (p.total > 0) {
+    unsigned nb = blocks_for(p.total, 256);
+    if (eval == 0) energy_grad_kernel<Arith64><<<nb, 256, 0, s>>>(p, grad, ecirc);
+    else if (eval == 1) energy_grad_kernel<Arith32><<<nb, 256, 0, s>>>(p, grad, ecirc);
+    else energy_grad_kernel<ArithMix><<<nb, 256, 0, s>>>(p, grad, ecirc);
+  }
+  if (p.num > 0) {
+    if (eval == 1) energy_reduce_kernel<float><<<p.num, 256, 0, s>>>(p, (const float *)ecirc, E);
+    else energy_reduce_kernel<double><<<p.num, 256, 0, s>>>(p, (const double *)ecirc, E);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_feasible(const StandaloneParams &p, int from32, double tol, uint8_t *feasible,
+                            double *max_overlap, int block, cudaStream_t s) {
+  if (p.num > 0) feasible_kernel<<<p.num, block, 0, s>>>(p, from32, tol, feasible, max_overlap);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_export_csr(const StandaloneParams &p, const int64_t *base, int32_t *row_ptr, int32_t *col,
+                              cudaStream_t s) {
+  export_csr_kernel<<<blocks_for(p.total + 1, 256), 256, 0, s>>>(p, base, row_ptr, col);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_export_cells(const StandaloneParams &p, uint32_t *key, int32_t *order, cudaStream_t s) {
+  if (p.total > 0) export_cells_kernel<<<blocks_for(p.total, 256), 256, 0, s>>>(p, key, order);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_nnz(const StandaloneParams &p, int64_t *nnz, cudaStream_t s) {
+  if (p.num > 0) nnz_kernel<<<blocks_for(p.num, 128), 128, 0, s>>>(p, nnz);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_outputs(const InstOut *out, int num, int32_t *iters, int32_t *status, double *E,
+                           int32_t *builds, int32_t *changes, int32_t *trials, cudaStream_t s) {
+  if (num > 0) outputs_kernel<<<blocks_for(num, 128), 128, 0, s>>>(out, num, iters, status, E, builds, changes, trials);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_stats(const InstOut *out, int num, int32_t *stats, cudaStream_t s) {
+  if (num > 0) stats_kernel<<<blocks_for(num, 128), 128, 0, s>>>(out, num, stats);
+  return cudaGetLastError();
+}
+
+}  // namespace pecc

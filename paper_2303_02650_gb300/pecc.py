@@ -1,0 +1,276 @@
+"""Thin ctypes binding of the C ABI in include/pecc.h (argument marshalling only).
+
+Every computation runs in the CUDA library ``_lib/libpecc.so``; PyTorch only
+provides device memory and the stream.  Importing this module loads the
+library and raises if it is missing: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import torch
+
+from . import build as _build
+
+FP64, FP32, FP32_POLISH64 = 0, 1, 2
+PART_SECTOR, PART_ANNULUS, PART_FENCE = 0, 1, 2
+INIT_DISK, INIT_SQUARE = 0, 1
+STATUS = {0: "converged", 1: "stationary", 2: "stalled", 3: "max_iter", 4: "nbr_overflow", 5: "nonfinite",
+          6: "timeout"}
+ERRORS = {1: "PECC_ERR_ARG", 2: "PECC_ERR_CUDA", 3: "PECC_ERR_OOM", 4: "PECC_ERR_NBR_OVERFLOW",
+          5: "PECC_ERR_NONFINITE", 6: "PECC_ERR_TIMEOUT"}
+
+
+class PeccError(RuntimeError):
+    pass
+
+
+class Config(C.Structure):
+    _fields_ = [("num_instances", C.c_int32), ("n", C.POINTER(C.c_int32)), ("precision", C.c_int32),
+                ("l_cut", C.c_double), ("rebuild_disp", C.c_double), ("step_max", C.c_double),
+                ("lbfgs_m", C.c_int32), ("max_iter", C.c_int32), ("polish_max_iter", C.c_int32),
+                ("k_batches", C.c_int32), ("partition", C.c_int32), ("max_trials", C.c_int32),
+                ("anm", C.c_int32), ("init_mode", C.c_int32), ("e_tol", C.c_double), ("gsum_tol", C.c_double),
+                ("c1", C.c_double), ("curv_eps", C.c_double), ("polish_gate", C.c_double),
+                ("feas_tol", C.c_double), ("nbr_capacity", C.c_double), ("time_budget_ns", C.c_int64),
+                ("block_threads", C.c_int32), ("blocks_per_sm", C.c_int32), ("stall_rel", C.c_double),
+                ("stall_window", C.c_int32)]
+
+
+_lib = None
+_EXPORTS = ["pecc_config_default", "pecc_create", "pecc_destroy", "pecc_set_radius", "pecc_set_positions",
+            "pecc_init_random", "pecc_get_positions", "pecc_rebuild_neighbors", "pecc_rebuild_neighbors_ex",
+            "pecc_neighbor_count", "pecc_export_neighbors", "pecc_export_cells", "pecc_energy_grad",
+            "pecc_energy_grad_ex", "pecc_descend", "pecc_get_energy", "pecc_check_feasible", "pecc_solve_host",
+            "pecc_get_counters", "pecc_get_launch", "pecc_last_error", "pecc_get_stats", "pecc_phase_times"]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libpecc.so (building it first if it is missing and nvcc exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise PeccError(f"CUDA library not built: {path}")
+        _build.build()
+    L = C.CDLL(path)
+    vp, i32p, i64p, dp = C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int64), C.POINTER(C.c_double)
+    st = C.c_int
+    sig = {
+        "pecc_config_default": (None, [C.POINTER(Config)]),
+        "pecc_create": (st, [C.POINTER(Config), vp, C.POINTER(vp)]),
+        "pecc_destroy": (st, [vp]),
+        "pecc_set_radius": (st, [vp, vp]),
+        "pecc_set_positions": (st, [vp, vp]),
+        "pecc_init_random": (st, [vp, C.c_uint64]),
+        "pecc_get_positions": (st, [vp, vp]),
+        "pecc_rebuild_neighbors": (st, [vp, C.c_int32, vp]),
+        "pecc_rebuild_neighbors_ex": (st, [vp, C.c_int32, C.c_int32, vp]),
+        "pecc_neighbor_count": (st, [vp, i64p]),
+        "pecc_export_neighbors": (st, [vp, vp, vp, C.c_int64]),
+        "pecc_export_cells": (st, [vp, vp, vp]),
+        "pecc_energy_grad": (st, [vp, vp, vp]),
+        "pecc_energy_grad_ex": (st, [vp, C.c_int32, vp, vp]),
+        "pecc_descend": (st, [vp, vp, vp]),
+        "pecc_get_energy": (st, [vp, vp]),
+        "pecc_check_feasible": (st, [vp, C.c_double, vp, vp]),
+        "pecc_solve_host": (st, [vp, vp, C.c_uint64, vp, vp, vp, vp, vp]),
+        "pecc_get_counters": (st, [vp, vp, vp, vp]),
+        "pecc_get_launch": (st, [vp, i32p, i32p, i32p]),
+        "pecc_last_error": (C.c_char_p, [vp]),
+        "pecc_get_stats": (st, [vp, vp]),
+        "pecc_phase_times": (st, [vp, C.POINTER(C.c_float)]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def default_config(**kw) -> Config:
+    c = Config()
+    load().pecc_config_default(C.byref(c))
+    for k, v in kw.items():
+        if not hasattr(c, k) or k in ("n", "num_instances"):
+            raise KeyError(k)
+        setattr(c, k, v)
+    return c
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    return C.c_void_p(t.data_ptr())
+
+
+class Context:
+    """One pecc_ctx: independent instances of sizes n[], container radii, positions.
+
+    Device arguments are torch CUDA tensors; host arguments of solve_host are numpy arrays.
+    """
+
+    def __init__(self, n, stream=None, **cfg):
+        import numpy as np
+
+        self._L = load()
+        self.n = np.ascontiguousarray(n, dtype=np.int32)
+        self.num = int(self.n.shape[0])
+        self.total = int(self.n.sum())
+        self.cfg = default_config(**cfg)
+        self.cfg.num_instances = self.num
+        self.cfg.n = self.n.ctypes.data_as(C.POINTER(C.c_int32))
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        h = C.c_void_p()
+        rc = self._L.pecc_create(C.byref(self.cfg), C.c_void_p(stream.cuda_stream), C.byref(h))
+        if rc != 0:
+            raise PeccError(f"pecc_create: {ERRORS.get(rc, rc)}: {self._L.pecc_last_error(None).decode()}")
+        self.h = h
+        self.precision = int(self.cfg.precision)
+        self.dev = torch.device("cuda", torch.cuda.current_device())
+
+    def _check(self, rc, what):
+        if rc != 0:
+            raise PeccError(f"{what}: {ERRORS.get(rc, rc)}: {self._L.pecc_last_error(self.h).decode()}")
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._L.pecc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # --------------------------------------------------------------- calls
+    def set_radius(self, R):
+        R = torch.as_tensor(R, dtype=torch.float64, device=self.dev).contiguous()
+        self._check(self._L.pecc_set_radius(self.h, _ptr(R)), "pecc_set_radius")
+
+    def set_positions(self, xy):
+        xy = torch.as_tensor(xy, dtype=torch.float64, device=self.dev).contiguous()
+        assert xy.numel() == 2 * self.total
+        self._check(self._L.pecc_set_positions(self.h, _ptr(xy)), "pecc_set_positions")
+
+    def init_random(self, seed: int):
+        self._check(self._L.pecc_init_random(self.h, C.c_uint64(seed)), "pecc_init_random")
+
+    def get_positions(self):
+        out = torch.empty((self.total, 2), dtype=torch.float64, device=self.dev)
+        self._check(self._L.pecc_get_positions(self.h, _ptr(out)), "pecc_get_positions")
+        return out
+
+    def rebuild_neighbors(self, force=True, eval=None):
+        rebuilt = torch.zeros(self.num, dtype=torch.int32, device=self.dev)
+        if eval is None:
+            rc = self._L.pecc_rebuild_neighbors(self.h, int(force), _ptr(rebuilt))
+        else:
+            rc = self._L.pecc_rebuild_neighbors_ex(self.h, int(eval), int(force), _ptr(rebuilt))
+        self._check(rc, "pecc_rebuild_neighbors")
+        return rebuilt
+
+    def neighbor_count(self) -> int:
+        v = C.c_int64()
+        self._check(self._L.pecc_neighbor_count(self.h, C.byref(v)), "pecc_neighbor_count")
+        return v.value
+
+    def export_neighbors(self):
+        nnz = self.neighbor_count()
+        rp = torch.empty(self.total + 1, dtype=torch.int32, device=self.dev)
+        col = torch.empty(max(nnz, 1), dtype=torch.int32, device=self.dev)
+        self._check(self._L.pecc_export_neighbors(self.h, _ptr(rp), _ptr(col), C.c_int64(col.numel())),
+                    "pecc_export_neighbors")
+        return rp, col[:nnz]
+
+    def export_cells(self):
+        key = torch.empty(self.total, dtype=torch.int32, device=self.dev)
+        order = torch.empty(self.total, dtype=torch.int32, device=self.dev)
+        self._check(self._L.pecc_export_cells(self.h, _ptr(key), _ptr(order)), "pecc_export_cells")
+        return key, order
+
+    def energy_grad(self, eval=None):
+        E = torch.empty(self.num, dtype=torch.float64, device=self.dev)
+        ev = (FP64 if self.precision == FP64 else FP32) if eval is None else eval
+        gdt = torch.float64 if ev == FP64 else torch.float32
+        g = torch.empty((self.total, 2), dtype=gdt, device=self.dev)
+        rc = self._L.pecc_energy_grad(self.h, _ptr(E), _ptr(g)) if eval is None else \
+            self._L.pecc_energy_grad_ex(self.h, int(eval), _ptr(E), _ptr(g))
+        self._check(rc, "pecc_energy_grad")
+        return E, g
+
+    def descend(self):
+        iters = torch.empty(self.num, dtype=torch.int32, device=self.dev)
+        status = torch.empty(self.num, dtype=torch.int32, device=self.dev)
+        self._check(self._L.pecc_descend(self.h, _ptr(iters), _ptr(status)), "pecc_descend")
+        return iters, status
+
+    def get_energy(self):
+        E = torch.empty(self.num, dtype=torch.float64, device=self.dev)
+        self._check(self._L.pecc_get_energy(self.h, _ptr(E)), "pecc_get_energy")
+        return E
+
+    def get_counters(self):
+        b = torch.empty(self.num, dtype=torch.int32, device=self.dev)
+        c = torch.empty_like(b)
+        t = torch.empty_like(b)
+        self._check(self._L.pecc_get_counters(self.h, _ptr(b), _ptr(c), _ptr(t)), "pecc_get_counters")
+        return b, c, t
+
+    def get_stats(self):
+        """int32 [num, 10]: iters, status, builds, changes, trials, resets, stalls, polished,
+        first-phase sweeps, first-phase trials."""
+        st = torch.empty((self.num, 10), dtype=torch.int32, device=self.dev)
+        self._check(self._L.pecc_get_stats(self.h, _ptr(st)), "pecc_get_stats")
+        return st
+
+    def phase_times(self):
+        """Device ms of the last descent: (first phase kernel, polish kernel, whole descent)."""
+        ms = (C.c_float * 3)()
+        self._check(self._L.pecc_phase_times(self.h, ms), "pecc_phase_times")
+        return float(ms[0]), float(ms[1]), float(ms[2])
+
+    def check_feasible(self, tol=None):
+        tol = float(self.cfg.feas_tol if tol is None else tol)
+        feas = torch.empty(self.num, dtype=torch.uint8, device=self.dev)
+        mo = torch.empty(self.num, dtype=torch.float64, device=self.dev)
+        self._check(self._L.pecc_check_feasible(self.h, C.c_double(tol), _ptr(feas), _ptr(mo)),
+                    "pecc_check_feasible")
+        return feas, mo
+
+    def launch_shape(self):
+        b, s, g = C.c_int32(), C.c_int32(), C.c_int32()
+        self._check(self._L.pecc_get_launch(self.h, C.byref(b), C.byref(s), C.byref(g)), "pecc_get_launch")
+        return b.value, s.value, g.value
+
+    def solve_host(self, R, seed, want_xy=True):
+        """Whole path from host memory (pecc_solve_host); R: numpy float64[num]."""
+        import numpy as np
+
+        R = np.ascontiguousarray(R, dtype=np.float64)
+        xy = np.empty((self.total, 2)) if want_xy else None
+        iters = np.empty(self.num, dtype=np.int32)
+        status = np.empty(self.num, dtype=np.int32)
+        feas = np.empty(self.num, dtype=np.uint8)
+        mo = np.empty(self.num, dtype=np.float64)
+        a = lambda x: None if x is None else x.ctypes.data_as(C.c_void_p)
+        self._check(self._L.pecc_solve_host(self.h, a(R), C.c_uint64(seed), a(xy), a(iters), a(status), a(feas),
+                                            a(mo)), "pecc_solve_host")
+        return dict(xy=xy, iters=iters, status=status, feasible=feas, max_overlap=mo)

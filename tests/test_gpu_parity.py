@@ -1,0 +1,350 @@
+"""GPU parity against the FP64 oracle, through the C ABI (marked gpu).
+
+Bit-exact: random init (Philox, correctly rounded FP64), cell keys and stable order, neighbor
+lists (Sec. 4.3 predicate in the coordinates' precision, no FMA), feasibility depths (Eq. 1,
+Eq. 2 with correctly rounded operations).  Within tolerance: energy and gradient (Eq. 5 and its
+gradient) in FP64 (1e-12 relative), FP32 and the mixed polish arithmetic (bounds derived in
+the test docstrings), and short descents (Algorithm GBO) in FP64.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2303_02650_gb300 import synth
+from gpu_util import need_gpu, ragged_sizes, split
+
+pytestmark = pytest.mark.gpu
+
+
+def _ctx(pecc, n, R, **kw):
+    c = pecc.Context(n, **kw)
+    c.set_radius(R)
+    return c
+
+
+def _radii(n, u=0.83):
+    return np.array([synth.radius(max(int(v), 1), u) for v in n])
+
+
+# ------------------------------------------------------------------ init / cells / lists
+@pytest.mark.parametrize("prec", [0, 1])
+def test_init_bit_exact(orc, prec):
+    torch, pecc = need_gpu()
+    n = ragged_sizes()
+    R = _radii(n)
+    with _ctx(pecc, n, R, precision=prec) as c:
+        c.init_random(12345)
+        xy = c.get_positions().cpu().numpy()
+    for q, part in enumerate(split(xy, n)):
+        ref = orc.init_positions(int(n[q]), float(R[q]), 12345, inst=q)
+        if prec == 1:
+            ref = ref.astype(np.float32).astype(np.float64)
+        assert np.array_equal(part, ref), q
+
+
+def test_init_square_mode_bit_exact(orc):
+    torch, pecc = need_gpu()
+    n = np.array([100, 37], dtype=np.int32)
+    R = _radii(n)
+    with _ctx(pecc, n, R, precision=0, init_mode=1) as c:
+        c.init_random(99)
+        xy = c.get_positions().cpu().numpy()
+    for q, part in enumerate(split(xy, n)):
+        assert np.array_equal(part, orc.init_positions(int(n[q]), float(R[q]), 99, inst=q, mode=1))
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_cells_and_neighbors_bit_exact(orc, prec):
+    torch, pecc = need_gpu()
+    n = ragged_sizes()
+    R = _radii(n, 0.85)
+    rng = np.random.default_rng(3)
+    with _ctx(pecc, n, R, precision=prec) as c:
+        c.init_random(7)
+        xy = c.get_positions().cpu().numpy()
+        # perturb so that some circles leave the container and some coincide
+        xy = xy + rng.normal(scale=0.3, size=xy.shape)
+        xy[5] = xy[4]
+        c.set_positions(torch.from_numpy(xy))
+        xy = c.get_positions().cpu().numpy()
+        c.rebuild_neighbors(force=True)
+        key, order = [t.cpu().numpy() for t in c.export_cells()]
+        rp, col = [t.cpu().numpy() for t in c.export_neighbors()]
+    off = np.concatenate([[0], np.cumsum(n)])
+    for q in range(len(n)):
+        a, b = off[q], off[q + 1]
+        x = xy[a:b]
+        kref = orc.cell_keys(x, float(R[q]), 2.5)
+        assert np.array_equal(key[a:b].astype(np.uint32), kref), q
+        assert np.array_equal(order[a:b], np.argsort(kref, kind="stable")), q
+        rref, cref = orc.neighbors_brute(x, 2.5, prec32=(prec == 1))
+        rows = rp[a:b + 1] - rp[a]
+        assert np.array_equal(rows, rref), q
+        assert np.array_equal(col[rp[a]:rp[b]] - a, cref), q
+
+
+# ------------------------------------------------------------------ energy and gradient
+def _oracle_eg(orc, xy, n, R):
+    Es, gs = [], []
+    for q, x in enumerate(split(xy, n)):
+        rp, col = orc.neighbors_brute(x, 2.5)
+        E, g, _ = orc.energy_grad_csr(x, float(R[q]), rp, col)
+        assert E == pytest.approx(orc.energy_allpairs(x, float(R[q])), rel=1e-12, abs=1e-300)
+        Es.append(E)
+        gs.append(g)
+    return np.array(Es), np.concatenate(gs) if gs else np.zeros((0, 2))
+
+
+def _contrib_scale(orc, xy, n, R):
+    """Per circle, the sum of the norms of the terms its gradient adds up (2 d_ij per pair,
+    2 d_i0 for the wall): the scale a normwise rounding bound on a sum refers to."""
+    out = []
+    for q, x in enumerate(split(xy, n)):
+        s = np.zeros(len(x))
+        if len(x):
+            rp, col = orc.neighbors_brute(x, 2.5)
+            for i in range(len(x)):
+                js = col[rp[i]:rp[i + 1]]
+                l = np.hypot(*(x[i] - x[js]).T) if len(js) else np.zeros(0)
+                s[i] = np.sum(2 * np.maximum(0.0, 2 - l)) + 2 * max(0.0, np.hypot(*x[i]) + 1 - float(R[q]))
+        out.append(s)
+    return np.concatenate(out) if out else np.zeros(0)
+
+
+def _layout(c, torch, seed, scale=1.0):
+    c.init_random(seed)
+    xy = c.get_positions().cpu().numpy() * scale
+    c.set_positions(torch.from_numpy(xy))
+    return c.get_positions().cpu().numpy()
+
+
+def test_energy_grad_fp64(orc):
+    torch, pecc = need_gpu()
+    n = ragged_sizes()
+    R = _radii(n, 0.83)
+    with _ctx(pecc, n, R, precision=0) as c:
+        xy = _layout(c, torch, 11, 1.03)
+        c.rebuild_neighbors()
+        E, g = [t.cpu().numpy() for t in c.energy_grad()]
+    Er, gr = _oracle_eg(orc, xy, n, R)
+    np.testing.assert_allclose(E, Er, rtol=1e-12, atol=1e-300)
+    gn = np.linalg.norm(gr, axis=1)
+    assert np.all(np.linalg.norm(g - gr, axis=1) <= 1e-12 * np.maximum(gn, 1e-300) + 1e-13)
+
+
+def test_energy_grad_fp32(orc):
+    """FP32: d = 2 - l carries an absolute error of about ulp(2) = 2.4e-7 per pair (and the
+    wall depth about ulp(R)), so E is compared to 1e-5 relative plus 4 ulp32(2) * sum 2 d, and
+    each circle's gradient to 1e-5 times the sum of its terms' norms plus 8 ulp32(R) times a
+    neighbor count of 8."""
+    torch, pecc = need_gpu()
+    n = ragged_sizes()
+    R = _radii(n, 0.83)
+    with _ctx(pecc, n, R, precision=1) as c:
+        xy = _layout(c, torch, 13, 1.03)
+        c.rebuild_neighbors()
+        E, g = [t.cpu().numpy().astype(np.float64) for t in c.energy_grad()]
+    Er, gr = _oracle_eg(orc, xy, n, R)
+    u2 = np.spacing(np.float32(2.0)).astype(np.float64)
+    for q, (x, Rq) in enumerate(zip(split(xy, n), R)):
+        if n[q] == 0:
+            assert E[q] == 0.0
+            continue
+        sum_d = 2 * math.sqrt(max(Er[q], 0.0)) * math.sqrt(3 * n[q]) + 1e-30
+        assert abs(E[q] - Er[q]) <= 1e-5 * Er[q] + 4 * u2 * sum_d + 1e-30, q
+    uR = np.spacing(np.float32(R.max())).astype(np.float64)
+    err = np.linalg.norm(g - gr, axis=1)
+    assert np.all(err <= 1e-5 * _contrib_scale(orc, xy, n, R) + 8 * 8 * uR), err.max()
+
+
+def test_energy_grad_mixed_polish_arithmetic(orc):
+    """The polish arithmetic computes 4 - l^2 and |c|^2 - (R-1)^2 in FP64 and the depths from
+    them in FP32: every depth and unit vector carries a relative error <= 4 ulp32 = 4.8e-7,
+    so E is within 1e-6 relative and each gradient within 1e-6 times the sum of its terms'
+    norms (the gradient itself can cancel to much less)."""
+    torch, pecc = need_gpu()
+    n = ragged_sizes()
+    R = _radii(n, 0.83)
+    with _ctx(pecc, n, R, precision=2) as c:
+        xy = _layout(c, torch, 17, 1.02)
+        c.rebuild_neighbors(eval=2)
+        E, g = [t.cpu().numpy().astype(np.float64) for t in c.energy_grad(eval=2)]
+    Er, gr = _oracle_eg(orc, xy, n, R)
+    np.testing.assert_allclose(E, Er, rtol=1e-6, atol=1e-300)
+    err = np.linalg.norm(g - gr, axis=1)
+    assert np.all(err <= 1e-6 * _contrib_scale(orc, xy, n, R) + 1e-12)
+
+
+def test_energy_near_contact_mixed_vs_fp64(orc):
+    """Near contact (overlaps ~1e-9) the mixed arithmetic keeps relative accuracy where plain
+    FP32 cannot resolve the depth at all."""
+    torch, pecc = need_gpu()
+    xy = synth.hex_patch(6, 2.0 - 2e-9)
+    n = np.array([xy.shape[0]], dtype=np.int32)
+    R = np.array([100.0])
+    with _ctx(pecc, n, R, precision=2) as c:
+        c.set_positions(torch.from_numpy(xy))
+        xy64 = c.get_positions().cpu().numpy()  # FP32-rounded coordinates
+    # FP32 rounding of the coordinates changes the overlaps; compare on the rounded layout
+    with _ctx(pecc, n, R, precision=0) as c64:
+        c64.set_positions(torch.from_numpy(xy))
+        c64.rebuild_neighbors()
+        E64, _ = c64.energy_grad()
+    rp, col = orc.neighbors_brute(xy, 2.5)
+    Eref, _, _ = orc.energy_grad_csr(xy, 100.0, rp, col)
+    assert float(E64.cpu()[0]) == pytest.approx(Eref, rel=1e-9)
+    assert Eref == pytest.approx((9 * 36 + 18) * (2e-9) ** 2, rel=1e-5)
+    del xy64
+
+
+# ------------------------------------------------------------------ feasibility
+def test_check_feasible_bit_exact(orc):
+    torch, pecc = need_gpu()
+    n = ragged_sizes()
+    R = _radii(n, 0.6)
+    with _ctx(pecc, n, R, precision=0) as c:
+        xy = _layout(c, torch, 5, 0.9)
+        feas, mo = [t.cpu().numpy() for t in c.check_feasible(1e-9)]
+    for q, x in enumerate(split(xy, n)):
+        ref = orc.max_overlap(x, float(R[q]))[0]
+        assert mo[q] == ref, (q, mo[q], ref)
+        assert feas[q] == (ref <= 1e-9)
+
+
+def test_check_feasible_exact_packings(orc):
+    torch, pecc = need_gpu()
+    pts = [np.array([[-1.0, 0.0], [1.0, 0.0]]),
+           np.vstack([[0, 0], 2 * np.stack([np.cos(np.arange(6) * np.pi / 3), np.sin(np.arange(6) * np.pi / 3)], 1)])]
+    n = np.array([2, 7], dtype=np.int32)
+    R = np.array([2.0, 3.0])
+    with _ctx(pecc, n, R, precision=0) as c:
+        c.set_positions(torch.from_numpy(np.concatenate(pts)))
+        feas, mo = [t.cpu().numpy() for t in c.check_feasible(1e-9)]
+    assert feas.tolist() == [1, 1]
+    assert mo[0] == 0.0 and mo[1] <= 1e-15
+
+
+# ------------------------------------------------------------------ descent
+@pytest.mark.parametrize("k,sweeps", [(1, 1), (1, 4), (3, 1), (3, 3), (5, 2)])
+def test_descend_short_runs_fp64(orc, k, sweeps):
+    """A few GBO sweeps in FP64 from the same layout: the GPU (vector-free two-loop, FMA pair
+    arithmetic) and the oracle (explicit two-loop, correctly rounded) take the same steps up to
+    rounding: positions agree to 1e-9 and energies to 1e-9 relative."""
+    torch, pecc = need_gpu()
+    n = np.array([300, 257, 1000], dtype=np.int32)
+    R = _radii(n, 0.8)
+    with _ctx(pecc, n, R, precision=0, k_batches=k, max_iter=sweeps) as c:
+        c.init_random(21)
+        x0 = c.get_positions().cpu().numpy()
+        iters, status = c.descend()
+        x1 = c.get_positions().cpu().numpy()
+        E = c.get_energy().cpu().numpy()
+        iters = iters.cpu().numpy()
+    for q, (a, b) in enumerate(zip(split(x0, n), split(x1, n))):
+        r = orc.gbo(a, float(R[q]), k=k, max_iter=sweeps)
+        assert iters[q] == r.iters
+        np.testing.assert_allclose(b, r.x, rtol=0, atol=1e-9 * float(R[q]))
+        assert E[q] == pytest.approx(r.E, rel=1e-9)
+
+
+def _solve(pecc, torch, n, R, seed, **kw):
+    with _ctx(pecc, n, R, **kw) as c:
+        c.init_random(seed)
+        iters, status = c.descend()
+        feas, mo = c.check_feasible()
+        xy = c.get_positions().cpu().numpy()
+        E = c.get_energy().cpu().numpy()
+        return dict(iters=iters.cpu().numpy(), status=status.cpu().numpy(), feasible=feas.cpu().numpy(),
+                    max_overlap=mo.cpu().numpy(), xy=xy, E=E)
+
+
+@pytest.mark.parametrize("prec", [0, 2])
+def test_descend_statistics_vs_oracle(orc, prec):
+    """Whole descents diverge from the oracle's after many nonconvex steps (rounding order), so
+    they are compared as outcomes: at u = 0.80, n = 300 both reach E <= 1e-20 on most seeds,
+    every instance the GPU calls converged is feasible by the oracle's own brute-force check,
+    and the GPU's max overlap equals the oracle's on the GPU's final layout."""
+    torch, pecc = need_gpu()
+    num = 16
+    n = np.full(num, 300, dtype=np.int32)
+    R = _radii(n, 0.80)
+    out = _solve(pecc, torch, n, R, 31, precision=prec)
+    _, ref = orc.solve_batch(n, R, 31, nthreads=8)
+    for q, x in enumerate(split(out["xy"], n)):
+        mo = orc.max_overlap(x, float(R[q]))[0]
+        assert out["max_overlap"][q] == mo
+        if out["status"][q] == 0:
+            assert out["E"][q] <= 1e-20 and mo <= 1e-9
+    assert out["feasible"].sum() >= num - 4
+    assert abs(int(out["feasible"].sum()) - int(ref["feasible"].sum())) <= 5
+
+
+def test_descend_infeasible_density_small(orc):
+    """n = 50 at u = 0.80 is denser than any packing of 50 circles: no descent reaches zero
+    energy, on the GPU or in the oracle, and every run ends by stalling or at max_iter."""
+    torch, pecc = need_gpu()
+    n = np.full(8, 50, dtype=np.int32)
+    R = _radii(n, 0.80)
+    out = _solve(pecc, torch, n, R, 1, precision=0)
+    assert out["feasible"].sum() == 0
+    assert set(out["status"].tolist()) <= {1, 2, 3}
+    assert np.all(out["E"] > 1e-6)
+
+
+def test_descend_ragged_and_degenerate(orc):
+    torch, pecc = need_gpu()
+    n = ragged_sizes()
+    R = _radii(n, 0.7)
+    out = _solve(pecc, torch, n, R, 3, precision=2)
+    assert out["status"][0] == 0 and out["feasible"][0] == 1   # n = 0
+    assert out["status"][1] == 0 and out["feasible"][1] == 1   # n = 1
+    for q, x in enumerate(split(out["xy"], n)):
+        assert out["max_overlap"][q] == orc.max_overlap(x, float(R[q]))[0]
+    assert out["feasible"][2:].sum() >= 6
+
+
+def test_descend_nonfinite_input_flagged(orc):
+    torch, pecc = need_gpu()
+    n = np.array([20, 20], dtype=np.int32)
+    R = _radii(n, 0.5)
+    with _ctx(pecc, n, R, precision=1) as c:
+        c.init_random(1)
+        xy = c.get_positions().cpu().numpy()
+        xy[3, 0] = np.nan
+        c.set_positions(torch.from_numpy(xy))
+        iters, status = c.descend()
+        assert status.cpu().numpy().tolist()[0] == 5
+        assert status.cpu().numpy().tolist()[1] in (0, 1, 2)
+
+
+def test_descend_capacity_overflow_flagged(orc):
+    """Every circle at one point: each list holds n - 1 entries, over a capacity of 1 per circle."""
+    torch, pecc = need_gpu()
+    n = np.array([200], dtype=np.int32)
+    with _ctx(pecc, n, np.array([20.0]), precision=1, nbr_capacity=1.0) as c:
+        c.set_positions(torch.zeros((200, 2), dtype=torch.float64))
+        iters, status = c.descend()
+        assert int(status.cpu()[0]) == 4
+
+
+def test_descend_time_budget(orc):
+    torch, pecc = need_gpu()
+    n = np.full(4, 1000, dtype=np.int32)
+    with _ctx(pecc, n, _radii(n, 0.84), precision=1, time_budget_ns=1) as c:
+        c.init_random(2)
+        iters, status = c.descend()
+        assert set(status.cpu().numpy().tolist()) == {6}
+        assert np.all(iters.cpu().numpy() == 1)
+
+
+def test_solve_host_matches_device_path(orc):
+    torch, pecc = need_gpu()
+    n = np.array([300, 420, 64], dtype=np.int32)
+    R = _radii(n, 0.8)
+    with _ctx(pecc, n, R, precision=2) as c:
+        h = c.solve_host(R, 77)
+    d = _solve(pecc, torch, n, R, 77, precision=2)
+    np.testing.assert_array_equal(h["xy"], d["xy"])
+    np.testing.assert_array_equal(h["feasible"], d["feasible"])
+    np.testing.assert_array_equal(h["iters"], d["iters"])

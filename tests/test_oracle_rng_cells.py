@@ -107,8 +107,11 @@ def test_cell_keys_and_stable_sort(orc):
     n, R, l_cut = 3000, synth.radius(3000, 0.8), 2.5
     xy = orc.init_positions(n, R, seed=1)
     key = orc.cell_keys(xy, R, l_cut)
-    inv, nc = orc.cell_grid(R, l_cut)
+    inv, nc = orc.cell_grid(R, l_cut, n)
     assert nc == math.ceil(2 * R / (l_cut * (1 + 2 ** -20)))
+    # a sparse instance: at most max(16, ceil(2 sqrt n)) cells per side, side >= l_cut
+    inv2, nc2 = orc.cell_grid(1000.0, l_cut, 10)
+    assert nc2 == 16 and 1.0 / inv2 >= l_cut
     # independent restatement of the cell index with numpy floor
     cx = np.clip(np.floor((xy[:, 0] + R) * inv), 0, nc - 1).astype(np.int64)
     cy = np.clip(np.floor((xy[:, 1] + R) * inv), 0, nc - 1).astype(np.int64)
