@@ -108,6 +108,7 @@ typedef struct {
                                E fell by less than stall_rel (relative) over stall_window sweeps:
                                binary32 has reached its resolution; 1e-3 */
     int32_t stall_window;   /* sweeps per stagnation check of the FP32 phase; 10 (0 = off) */
+    int32_t polish_k;       /* batches of the FP64 polish (at most k_batches); 1 (0 = k_batches) */
 } pecc_config;
 
 /* Fill *cfg with the defaults listed above (num_instances = 0, n = NULL). */

@@ -8,7 +8,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/pecc.h"
+#include "pecc.h"
 #include "pecc_internal.h"
 
 using namespace pecc;
@@ -43,6 +43,8 @@ struct pecc_ctx {
   bool radius_set = false;
   int lists_prec = -1;  // precision of the standalone lists: 0 FP64, 1 FP32
   int block = 0, bps = 0, grid = 0, block_build = 256;
+  struct Launch { int block = 0, bps = 0, grid = 0; size_t smem = 0; } lc[3];  // per arithmetic
+  bool lc_ready = false;
   cudaGraphExec_t graph = nullptr;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   std::string err;
@@ -97,6 +99,7 @@ static StandaloneParams sparams(pecc_ctx *c) {
   p.ckey_t = c->ckey;
   p.corder_t = c->corder;
   p.xtmp = c->xw;
+  p.xtmp2 = c->xo;
   p.l_cut = c->cfg.l_cut;
   p.rebuild_disp = c->cfg.rebuild_disp;
   return p;
@@ -130,6 +133,7 @@ void pecc_config_default(pecc_config *c) {
   c->blocks_per_sm = 0;
   c->stall_rel = 1e-3;
   c->stall_window = 10;
+  c->polish_k = 1;
 }
 
 static int default_k(int n) { return n < 300 ? 1 : (n < 500 ? 3 : 5); }
@@ -154,6 +158,7 @@ pecc_status pecc_create(const pecc_config *cfg, void *stream, pecc_ctx **out) {
   if (cfg->init_mode < 0 || cfg->init_mode > 1) return fail(nullptr, PECC_ERR_ARG, "bad init_mode");
   if (!(cfg->nbr_capacity >= 1.0)) return fail(nullptr, PECC_ERR_ARG, "nbr_capacity must be >= 1");
   if (cfg->stall_window < 0 || !(cfg->stall_rel >= 0.0)) return fail(nullptr, PECC_ERR_ARG, "bad stall rule");
+  if (cfg->polish_k < 0 || cfg->polish_k > kMaxK) return fail(nullptr, PECC_ERR_ARG, "polish_k must be in 0..64");
   if (cfg->block_threads != 0 && (cfg->block_threads < 32 || cfg->block_threads % 32 ||
                                   cfg->block_threads > descend_max_block(cfg->precision == PECC_FP64 ? 0 : 1)))
     return fail(nullptr, PECC_ERR_ARG, "block_threads must be a multiple of 32 within the kernel's limit");
@@ -278,15 +283,8 @@ pecc_status pecc_create(const pecc_config *cfg, void *stream, pecc_ctx **out) {
     if (ctx->num > ctx->num_sms) blk = std::min(blk, 256);
   }
   ctx->block = blk;
-  int occ = 1;
-  {
-    cudaFuncAttributes fa{};
-    const int ar = cfg->precision == PECC_FP64 ? 0 : (cfg->precision == PECC_FP32 ? 1 : 2);
-    if (descend_occupancy(ar, blk, &occ) != cudaSuccess || occ < 1) occ = 1;
-    (void)fa;
-  }
-  ctx->bps = cfg->blocks_per_sm > 0 ? std::min(cfg->blocks_per_sm, occ) : occ;
-  ctx->grid = std::min<int64_t>(ctx->num, (int64_t)ctx->num_sms * ctx->bps);
+  ctx->bps = 0;
+  ctx->grid = 0;
   for (int i = 0; i < 4; ++i)
     if (cudaEventCreate(&ctx->ev[i]) != cudaSuccess) return bail(fail(ctx, PECC_ERR_CUDA, "cudaEventCreate"));
   *out = ctx;
@@ -309,8 +307,8 @@ const char *pecc_last_error(pecc_ctx *ctx) { return ctx ? ctx->err.c_str() : g_c
 
 // Cell grid of one instance: side l_cut (1 + 2^-20), ncx = ceil(2R / side), capped at
 // max(16, ceil(2 sqrt(n))) cells per side (the side then grows to 2R / ncx).
-static void cell_grid(double R, double l_cut, int n, double *inv, int *nc) {
-  double cs = l_cut * (1.0 + 1.0 / 1048576.0);
+static void cell_grid(double R, double l_cut, int n, double *inv, int *nc, double margin = 1.0 / 1048576.0) {
+  double cs = l_cut * (1.0 + margin);
   double iv = 1.0 / cs;
   double w = std::ceil((2.0 * R) * iv);
   int cap = std::max(16, (int)std::ceil(2.0 * std::sqrt((double)n)));
@@ -336,6 +334,16 @@ pecc_status pecc_set_radius(pecc_ctx *ctx, const double *R_dev) {
     InstDesc &D = ctx->desc_h[q];
     D.R = R[q];
     cell_grid(R[q], ctx->cfg.l_cut, D.n, &D.inv_cs, &D.ncx);
+    {
+      double invf;
+      int ncf;
+      cell_grid(R[q], ctx->cfg.l_cut, D.n, &invf, &ncf, 1.0 / 1024.0);
+      // round the binary32 inverse side down so the side only grows
+      float f = (float)invf;
+      if ((double)f > invf) f = nextafterf(f, 0.0f);
+      D.inv_f = f;
+      D.ncx_f = std::min(ncf, D.ncx);
+    }
     D.cell_off = (int64_t)cells;
     cells += 2 * (size_t)D.ncx * D.ncx + 2;
   }
@@ -350,6 +358,7 @@ pecc_status pecc_set_radius(pecc_ctx *ctx, const double *R_dev) {
   CK(cudaStreamSynchronize(ctx->stream));
   ctx->radius_set = true;
   ctx->lists_prec = -1;
+  ctx->lc_ready = false;
   if (ctx->graph) { cudaGraphExecDestroy(ctx->graph); ctx->graph = nullptr; }
   return PECC_OK;
 }
@@ -461,6 +470,45 @@ pecc_status pecc_energy_grad(pecc_ctx *ctx, double *E_dev, void *grad_dev) {
   return pecc_energy_grad_ex(ctx, ctx->cfg.precision == PECC_FP64 ? PECC_FP64 : PECC_FP32, E_dev, grad_dev);
 }
 
+// Launch shape of one descent arithmetic: block size from the config (or about two circles per
+// thread), dynamic shared memory for the largest working set capped so that two blocks share
+// an SM when instances outnumber SMs, blocks per SM from the occupancy calculator.
+static pecc_status plan_launch(pecc_ctx *ctx, int arith) {
+  pecc_ctx::Launch &L = ctx->lc[arith];
+  int dev = ctx->device, optin = 0, per_sm = 0;
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  const size_t stat = descend_static_smem(arith) + 1024;
+  size_t need = 0;
+  for (int q = 0; q < ctx->num; ++q) {
+    const InstDesc &D = ctx->desc_h[q];
+    int k = D.k;
+    if (arith == 2 && ctx->cfg.polish_k > 0) k = std::min(ctx->cfg.polish_k, D.k);
+    need = std::max(need, descend_smem_need(arith, D.n, k, arith == 1 ? D.ncx_f : D.ncx));
+  }
+  const bool many = ctx->num > ctx->num_sms;
+  size_t cap = many ? (size_t)per_sm / 2 - stat : (size_t)optin - stat;
+  cap = std::min(cap, (size_t)optin - stat);
+  L.smem = std::min(need, cap) & ~size_t(15);
+  int blk = ctx->cfg.block_threads;
+  if (blk == 0) {
+    int nmax = 0;
+    for (int v : ctx->n) nmax = std::max(nmax, v);
+    int want = (nmax + 1) / 2;
+    blk = std::min(descend_max_block(arith), std::max(64, (want + 31) / 32 * 32));
+    if (many) blk = std::min(blk, 256);
+  }
+  blk = std::min(blk, descend_max_block(arith));
+  L.block = blk;
+  CK(descend_prepare(arith, L.smem));
+  int occ = 0;
+  CK(descend_occupancy(arith, blk, L.smem, &occ));
+  if (occ < 1) return fail(ctx, PECC_ERR_CUDA, "descent kernel does not fit an SM (block %d, smem %zu)", blk, L.smem);
+  L.bps = ctx->cfg.blocks_per_sm > 0 ? std::min(ctx->cfg.blocks_per_sm, occ) : occ;
+  L.grid = (int)std::min<int64_t>(ctx->num, (int64_t)ctx->num_sms * L.bps);
+  return PECC_OK;
+}
+
 static DescendParams dparams(pecc_ctx *c, int phase) {
   DescendParams p{};
   p.desc = c->desc;
@@ -486,6 +534,8 @@ static DescendParams dparams(pecc_ctx *c, int phase) {
   p.stall_window = f.stall_window;
   p.t0 = c->t0;
   p.budget_ns = f.time_budget_ns;
+  p.k_override = (phase == 2) ? f.polish_k : 0;
+  p.smem_bytes = c->lc[phase].smem;
   return p;
 }
 
@@ -496,16 +546,16 @@ static cudaError_t enqueue_descend(pecc_ctx *c) {
   if ((e = launch_stamp(c->t0, c->stream))) return e;
   if ((e = cudaEventRecordWithFlags(c->ev[0], c->stream, cudaEventRecordExternal))) return e;
   if (c->cfg.precision == PECC_FP64) {
-    if ((e = launch_descend(0, dparams(c, 0), c->grid, c->block, c->stream))) return e;
+    if ((e = launch_descend(0, dparams(c, 0), c->lc[0].grid, c->lc[0].block, c->stream))) return e;
     if ((e = cudaEventRecordWithFlags(c->ev[1], c->stream, cudaEventRecordExternal))) return e;
     return cudaEventRecordWithFlags(c->ev[2], c->stream, cudaEventRecordExternal);
   }
-  if ((e = launch_descend(1, dparams(c, 1), c->grid, c->block, c->stream))) return e;
+  if ((e = launch_descend(1, dparams(c, 1), c->lc[1].grid, c->lc[1].block, c->stream))) return e;
   if ((e = cudaEventRecordWithFlags(c->ev[1], c->stream, cudaEventRecordExternal))) return e;
   if (c->cfg.precision == PECC_FP32_POLISH64) {
     DescendParams p = dparams(c, 2);
     p.max_iter = c->cfg.polish_max_iter;
-    if ((e = launch_descend(2, p, c->grid, c->block, c->stream))) return e;
+    if ((e = launch_descend(2, p, c->lc[2].grid, c->lc[2].block, c->stream))) return e;
   }
   return cudaEventRecordWithFlags(c->ev[2], c->stream, cudaEventRecordExternal);
 }
@@ -514,6 +564,18 @@ pecc_status pecc_descend(pecc_ctx *ctx, int32_t *iters_dev, int32_t *status_dev)
   pecc_status s = need_radius(ctx);
   if (s) return s;
   if (ctx->num == 0) return PECC_OK;
+  for (int q = 0; q < ctx->num; ++q)
+    if (ctx->n[q] > 65535) return fail(ctx, PECC_ERR_ARG, "pecc_descend: instance %d has more than 65535 circles", q);
+  if (!ctx->lc_ready) {
+    const int pr = ctx->cfg.precision;
+    if (pr == PECC_FP64) {
+      if ((s = plan_launch(ctx, 0))) return s;
+    } else {
+      if ((s = plan_launch(ctx, 1))) return s;
+      if (pr == PECC_FP32_POLISH64 && (s = plan_launch(ctx, 2))) return s;
+    }
+    ctx->lc_ready = true;
+  }
   if (!ctx->graph) {
     cudaStream_t cs = ctx->stream;
     bool own = false;
@@ -578,9 +640,10 @@ pecc_status pecc_phase_times(pecc_ctx *ctx, float *ms_host) {
 
 pecc_status pecc_get_launch(pecc_ctx *ctx, int32_t *block_threads, int32_t *blocks_per_sm, int32_t *grid) {
   if (!ctx) return PECC_ERR_ARG;
-  if (block_threads) *block_threads = ctx->block;
-  if (blocks_per_sm) *blocks_per_sm = ctx->bps;
-  if (grid) *grid = ctx->grid;
+  const int a = ctx->cfg.precision == PECC_FP64 ? 0 : 1;
+  if (block_threads) *block_threads = ctx->lc[a].block;
+  if (blocks_per_sm) *blocks_per_sm = ctx->lc[a].bps;
+  if (grid) *grid = ctx->lc[a].grid;
   return PECC_OK;
 }
 

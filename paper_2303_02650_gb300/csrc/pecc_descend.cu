@@ -9,12 +9,19 @@
 //     every per-circle array and "merge" is a scatter at the end.
 //   * neighbor lists: cell binning + stable key sort + 3x3-cell CSR build, in the
 //     block (cta_build_neighbors).  Rebuilt by ANM after every sweep (Algorithm
-//     ANM) and before a batch step whenever twice the largest displacement since
+//     ANM: Gamma' replaces Gamma, and whether it differs -- compared through an
+//     order-independent 64-bit digest of the pair set -- decides the deferral
+//     length) and before a batch step whenever twice the largest displacement since
 //     the last build plus the step cap could exceed l_cut - 2 (Verlet rule).
 //   * per batch step (Eq. 8): the batch energy of Eq. 7 and its gradient, the
 //     quasi-Newton direction -H g of Eq. 10 / Eq. 11 with m secant pairs, a
 //     backtracking line search in place of the argmin of Eq. 9, and a secant
 //     pair push when the curvature condition holds.
+//
+// The instance's working set (coordinates, gradients, direction, neighbor lists,
+// cell scratch, Gram matrices) is carved out of dynamic shared memory as far as it
+// fits, the rest falls back to global memory; the secant pairs stay in global
+// memory (read coalesced, L2-resident for the instances in flight).
 //
 // The direction is computed in "vector-free" form (Chen, Wang, Zhou, Burges,
 // "Large-scale L-BFGS using MapReduce", NIPS 2014): the two-loop recursion is
@@ -33,6 +40,14 @@ namespace {
 constexpr int KS = kMaxSlots;     // basis index of Y slot a is KS + a
 constexpr int GI = 2 * kMaxSlots; // basis index of g
 constexpr int NDOT = 4 * kMaxSlots + 3;
+// values of the first reduction of a batch step, padded to a multiple of 32 for the reduce-scatter:
+//   [0] g'g, [1 + a] g's_a and [1 + KS + a] g'y_a for every physical slot a,
+//   [OP + a], [OP + KS + a], [OP + 2 KS + a], [OP + 3 KS + a]: s's_a, s'y_a, y's_a, y'y_a of the
+//   pending pair (s, y) against physical slot a, [OP + 4 KS + 0..2]: s's, s'y, y'y.
+constexpr int OP = 1 + 2 * kMaxSlots;
+constexpr int NRA = ((OP + 4 * kMaxSlots + 3 + 31) / 32) * 32;
+constexpr int NR4 = NRA;
+constexpr int kRingInts = kMaxSlots + 3;  // count, stage, ring[kMaxSlots], pending
 
 __device__ __forceinline__ uint64_t sortable(double v) {
   uint64_t b = (uint64_t)__double_as_longlong(v);
@@ -49,20 +64,25 @@ __device__ __forceinline__ double part_key(double x, double y, int mode) {
   return (y >= 0.0) ? __dsub_rn(1.0, t) : __dadd_rn(3.0, t);
 }
 
+template <class A> struct MaxT { static constexpr int v = 512; };  // threads per block, at most
+template <> struct MaxT<Arith64> { static constexpr int v = 256; };
+template <> struct MaxT<ArithMix> { static constexpr int v = 256; };
+
 template <class A> struct Smem {
   using vec_t = typename A::vec_t;
   using acc_t = typename A::acc_t;
-  acc_t ra[32 * 2];           // reduction scratch: acc sums
-  vec_t rb[32 * NDOT];        // vec sums
-  vec_t rc[32 * 2];           // maxima
+  static constexpr int W = MaxT<A>::v / 32;
+  acc_t ra[W * 2];            // reduction scratch: acc sums
+  vec_t rb[W * NR4];          // vec sums
+  vec_t rc[W * 2];            // maxima
   acc_t oa[2];
-  vec_t ob[NDOT];
+  vec_t ob[NR4];
   vec_t oc[2];
-  vec_t gram[kBasis * kBasis];
   vec_t coef[kBasis];
   vec_t alpha[kMaxSlots];
-  int ring[kMaxSlots];
-  int count, stage;
+  int ring[kMaxK][kRingInts];  // per batch: count, stage slot, ring slots oldest -> newest
+  unsigned long long hash;
+  unsigned used;               // physical slots in the current batch's ring (bit mask)
   int32_t sh[40];
   int q;
   int flag;
@@ -97,8 +117,67 @@ __device__ __forceinline__ void reduce(Smem<A> &S, typename A::acc_t (&a)[NA], t
   __syncthreads();
 }
 
+// Block reduction of one acc sum and NV vec sums (NV a multiple of 32) by a reduce-scatter
+// within each warp, then one sum over the warps per value.
+template <class A, int NV>
+__device__ __forceinline__ void reduce_many(Smem<A> &S, typename A::acc_t a0, typename A::vec_t (&v)[NV]) {
+  using vec_t = typename A::vec_t;
+  using acc_t = typename A::acc_t;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  warp_reduce_scatter<vec_t, NV>(v);
+  acc_t a = warp_sum(a0);
+#pragma unroll
+  for (int j = 0; j < NV / 32; ++j) S.rb[w * NV + (NV / 32) * lane + j] = v[j];
+  if (lane == 0) S.ra[w] = a;
+  __syncthreads();
+  for (int q = threadIdx.x; q <= NV; q += blockDim.x) {
+    if (q < NV) {
+      vec_t s = 0; for (int u = 0; u < nw; ++u) s += S.rb[u * NV + q];
+      S.ob[q] = s;
+    } else {
+      acc_t s = 0; for (int u = 0; u < nw; ++u) s += S.ra[u];
+      S.oa[0] = s;
+    }
+  }
+  __syncthreads();
+}
+
+// Block reduction of one acc sum and one vec maximum.
 template <class A>
-__global__ void __launch_bounds__(A::kId == 0 ? 256 : 512)
+__device__ __forceinline__ void reduce_sum_max(Smem<A> &S, typename A::acc_t a0, typename A::vec_t m0) {
+  using vec_t = typename A::vec_t;
+  using acc_t = typename A::acc_t;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  acc_t a = warp_sum(a0);
+  vec_t m = warp_max(m0);
+  if (lane == 0) { S.ra[w] = a; S.rc[w] = m; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    acc_t sa = 0; vec_t sm = S.rc[0];
+    for (int u = 0; u < nw; ++u) { sa += S.ra[u]; sm = max(sm, S.rc[u]); }
+    S.oa[0] = sa; S.oc[0] = sm;
+  }
+  __syncthreads();
+}
+
+// Bump allocator over dynamic shared memory; returns the fallback when the request does not fit.
+struct Carve {
+  unsigned char *base;
+  size_t cap, used;
+  template <typename T> __device__ T *take(size_t count, T *fallback) {
+    size_t b = (count * sizeof(T) + 15) & ~size_t(15);
+    if (used + b <= cap) {
+      T *p = (T *)(base + used);
+      used += b;
+      return p;
+    }
+    return fallback;
+  }
+};
+
+
+template <class A, int MAXT>
+__global__ void __launch_bounds__(MAXT, 1)
 descend_kernel(DescendParams P) {
   using pos_t = typename A::pos_t;
   using vec_t = typename A::vec_t;
@@ -106,6 +185,7 @@ descend_kernel(DescendParams P) {
   using sc_t = acc_t;  // per-step scalars in the arithmetic's own precision
   using PP = v2<pos_t>;
   using VV = v2<vec_t>;
+  extern __shared__ __align__(16) unsigned char dsm[];
   __shared__ Smem<A> S;
   const sc_t c1 = (sc_t)P.c1, step_max = (sc_t)P.step_max, two_skin = (sc_t)(2.0 * P.rebuild_disp);
   const sc_t gsum_tol = (sc_t)P.gsum_tol, curv_eps = (sc_t)P.curv_eps;
@@ -142,29 +222,41 @@ descend_kernel(DescendParams P) {
       }
     }
     if (n == 0) {
-      if (tid == 0) { O->iters = 0; O->status = 0; O->E = 0.0; if (A::kId == 1) { O->iters32 = 0; O->status32 = 0; O->E32 = 0.0; } }
+      if (tid == 0) {
+        O->iters = 0; O->status = 0; O->E = 0.0;
+        if (A::kId == 1) { O->iters32 = 0; O->status32 = 0; O->E32 = 0.0; O->trials32 = 0; }
+      }
       __syncthreads();
       continue;
     }
+    const int k = (P.k_override > 0) ? min(P.k_override, D.k) : D.k;
 
-    PP *xw = (PP *)P.xw + D.off;
-    PP *xb = (PP *)P.xb + D.off;
-    PP *xo = (PP *)P.xo + D.off;
-    VV *g = (VV *)P.g + D.off;
-    VV *gt = (VV *)P.gt + D.off;
-    VV *dv = (VV *)P.d + D.off;
+    // ---- working set: shared memory first, global scratch as the fallback
+    Carve cv{dsm, P.smem_bytes, 0};
+    PP *xw = cv.take<PP>(n, (PP *)P.xw + D.off);
+    VV *g = cv.take<VV>(n, (VV *)P.g + D.off);
+    VV *gt = cv.take<VV>(n, (VV *)P.gt + D.off);
+    VV *dv = cv.take<VV>(n, (VV *)P.d + D.off);
+    int32_t *rp = cv.take<int32_t>(n + 1, P.rp + D.rp_off);
+    // neighbor indices are 16-bit inside the descent (instances of at most 65535 circles)
+    const int cap_s = min(D.cap, 10 * n + 64);
+    uint16_t *col_s = cv.take<uint16_t>(cap_s, (uint16_t *)nullptr);
+    uint16_t *const col_g = (uint16_t *)(P.col + D.col_off);  // 2 cap int32 = 4 cap uint16
+    uint16_t *col = col_s ? col_s : col_g;
+    int cap = col_s ? cap_s : D.cap;
+    PP *xo = cv.take<PP>(n, (PP *)P.xo + D.off);
+    vec_t *gram = cv.take<vec_t>((size_t)k * kBasis * kBasis, (vec_t *)P.gram + D.gram_off);
+    const CellGrid G = (A::kId == 1) ? CellGrid{D.R, D.inv_cs, (float)D.R, D.inv_f, D.ncx_f, true}
+                                     : CellGrid{D.R, D.inv_cs, 0.f, 0.f, D.ncx, false};
+    int32_t *cells = cv.take<int32_t>(2 * (size_t)G.nc * G.nc + 2, P.cells + D.cell_off);
+    uint32_t *ckey = cv.take<uint32_t>(n, P.ckey + D.off);
+    int32_t *corder = cv.take<int32_t>(n, P.corder + D.off);
+    PP *xb = cv.take<PP>(n, (PP *)P.xb + D.off);
     VV *Sv = (VV *)P.S + (int64_t)mm * D.off;
     VV *Yv = (VV *)P.Y + (int64_t)mm * D.off;
     int32_t *perm = P.perm + D.off;
-    uint64_t *skey = P.skey + D.off;
-    int32_t *rpb[2] = {P.rp + D.rp_off, P.rp + D.rp_off + n + 1};
-    int32_t *colb[2] = {P.col + D.col_off, P.col + D.col_off + D.cap};
-    uint32_t *ckey = P.ckey + D.off;
-    int32_t *corder = P.corder + D.off;
-    int32_t *cells = P.cells + D.cell_off;
-    vec_t *gramg = (vec_t *)P.gram + D.gram_off;
-    int32_t *meta = P.meta + D.meta_off;
-    const int k = D.k;
+    // the partition keys borrow the list storage (8 n bytes) before the first build
+    uint64_t *skey = (col_s && (size_t)cap_s * 2 >= (size_t)n * 8) ? (uint64_t *)col_s : P.skey + D.off;
     const pos_t lc2 = (pos_t)(P.l_cut * P.l_cut);
 
     // ---- 1. partition key and rank (stable by index)
@@ -192,7 +284,7 @@ descend_kernel(DescendParams P) {
       PP v;
       if (A::kId == 0) { double2 u = P.x64[D.off + i]; v.x = (pos_t)u.x; v.y = (pos_t)u.y; }
       else { float2 u = P.x32[D.off + i]; v.x = (pos_t)u.x; v.y = (pos_t)u.y; }
-      bad |= !(isfinite((double)v.x) && isfinite((double)v.y));
+      bad |= !(isfinite((float)v.x) && isfinite((float)v.y));
       xw[p] = v;
       xb[p] = v;
     }
@@ -200,30 +292,30 @@ descend_kernel(DescendParams P) {
 
     int status = 3;  // max_iter unless something else ends the run
     int iters = 0, builds = 0, changes = 0, trials = 0, resets = 0, stalls = 0;
-    int cur = 0, cnt = 0, len = 1;
+    int cnt = 0, len = 1;
+    unsigned long long hcur = 0ull;  // digest of the current lists
     sc_t Dmax = 0;  // largest displacement since the last build
     acc_t E = 0;
 
-    auto build = [&](int into) -> int {
-      return cta_build_neighbors<pos_t>(xw, n, D.R, D.inv_cs, D.ncx, lc2, ckey, corder, cells, rpb[into],
-                                        colb[into], D.cap, S.sh);
-    };
-    // ANM step (Algorithm ANM): build Gamma', compare, keep or replace; returns false on overflow
-    auto anm_rebuild = [&]() -> bool {
-      int alt = cur ^ 1;
-      int tot = build(alt);
-      if (tot > D.cap) return false;
-      ++builds;
-      int diff = 0;
-      const int32_t *ra = rpb[alt], *rc = rpb[cur];
-      for (int i = tid; i <= n; i += T) diff |= ra[i] != rc[i];
-      diff = __syncthreads_or(diff);
-      if (!diff) {
-        const int32_t *ca = colb[alt], *cc = colb[cur];
-        for (int i = tid; i < tot; i += T) diff |= ca[i] != cc[i];
-        diff = __syncthreads_or(diff);
+    // one neighbor build into the block's list storage; moves the lists to global memory when
+    // they outgrow their shared-memory share; false when even the global capacity is exceeded
+    auto build = [&]() -> bool {
+      int tot = cta_build_neighbors<pos_t, uint16_t>(xw, n, G, lc2, ckey, corder, cells, xo, rp, col, cap, S.sh,
+                                                     &S.hash, false);
+      if (tot > cap && col_s && col == col_s) {
+        col = col_g;
+        cap = D.cap;
+        tot = cta_build_neighbors<pos_t, uint16_t>(xw, n, G, lc2, ckey, corder, cells, xo, rp, col, cap, S.sh,
+                                                   &S.hash, false);
       }
-      if (diff) { cur = alt; len = 1; ++changes; }
+      return tot <= cap;
+    };
+    // ANM step (Algorithm ANM): Gamma' replaces Gamma; equal sets double the deferral length
+    auto anm_rebuild = [&]() -> bool {
+      if (!build()) return false;
+      ++builds;
+      const unsigned long long h = S.hash;
+      if (h != hcur) { hcur = h; len = 1; ++changes; }
       else if (len < (1 << 30)) len *= 2;
       cnt = 0;
       for (int p = tid; p < n; p += T) xb[p] = xw[p];
@@ -233,14 +325,13 @@ descend_kernel(DescendParams P) {
     };
     // full energy (Eq. 5 over the lists: each pair from its larger index)
     auto full_energy = [&]() -> acc_t {
-      const int32_t *rp = rpb[cur], *cl = colb[cur];
       acc_t a[1] = {0};
       vec_t b[1] = {0}, c[1] = {0};
       for (int p = tid; p < n; p += T) {
         PP xi = xw[p];
         acc_t e = 0;
         for (int t = rp[p]; t < rp[p + 1]; ++t) {
-          int j = cl[t];
+          int j = col[t];
           if (j >= p) continue;
           vec_t fx, fy;
           acc_t d = A::pair(xi, xw[j], fx, fy);
@@ -257,21 +348,22 @@ descend_kernel(DescendParams P) {
     if (bad) {
       status = 5;
     } else {
-      int tot = build(0);
-      if (tot > D.cap) status = 4;
+      if (!build()) status = 4;
       else {
         builds = 1;
+        hcur = S.hash;
         E = full_energy();
-        if (!isfinite((double)E)) status = 5;
+        if (!isfinite(E)) status = 5;
         else if (E <= (acc_t)P.e_tol) status = 0;
       }
     }
-    for (int u = tid; u < k * kMetaInts; u += T) meta[u] = 0;
-    for (int u = tid; u < k * kBasis * kBasis; u += T) gramg[u] = vec_t(0);
+    for (int u = tid; u < k * kRingInts; u += T) S.ring[u / kRingInts][u % kRingInts] = 0;
+    for (int u = tid; u < k * kBasis * kBasis; u += T) gram[u] = vec_t(0);
     __syncthreads();
 
     const int q_ = n / k, r_ = n % k;
     bool fresh = false;  // k == 1: g / E of the previous accepted trial are current
+    int e_at = 0;        // sweep after which E was last evaluated
     acc_t Ewin = E;      // FP32 phase: energy at the start of the stagnation window
 
     // ---- 3. sweeps
@@ -286,23 +378,16 @@ descend_kernel(DescendParams P) {
           if (!anm_rebuild()) { status = 4; break; }
           fresh = false;
         }
-        const int32_t *rp = rpb[cur], *cl = colb[cur];
-        // batch ring metadata and Gram block into shared memory
-        if (tid == 0) {
-          S.count = meta[p * kMetaInts + 0];
-          S.stage = meta[p * kMetaInts + 1];
-          for (int c = 0; c < kMaxSlots; ++c) S.ring[c] = meta[p * kMetaInts + 2 + c];
-        }
-        for (int u = tid; u < kBasis * kBasis; u += T) S.gram[u] = gramg[(size_t)p * kBasis * kBasis + u];
-        __syncthreads();
-        const int count = S.count;
+        int *ring = S.ring[p];  // [0] count, [1] stage, [2..] slots, [2 + KS] pending
+        vec_t *Gm = gram + (size_t)p * kBasis * kBasis;
+        const int count0 = ring[0], st = ring[1], pending = ring[2 + kMaxSlots];
 
-        // ---- pass A: batch energy (Eq. 7) and gradient, dots of g with the stored pairs
-        acc_t aA[1] = {0};
-        vec_t bA[2 + 2 * kMaxSlots];
-        vec_t cA[1] = {0};
+        // ---- pass A: batch energy (Eq. 7) and gradient, dots of g with every stored vector, and
+        // the dots of the pair written by this batch's previous step (its curvature is tested here)
+        acc_t aA = 0;
+        vec_t bA[NRA];
 #pragma unroll
-        for (int u = 0; u < 2 + 2 * kMaxSlots; ++u) bA[u] = 0;
+        for (int u = 0; u < NRA; ++u) bA[u] = 0;
         if (fresh) { VV *t_ = g; g = gt; gt = t_; }
         for (int pos = b + tid; pos < e; pos += T) {
           PP xi = xw[pos];
@@ -312,7 +397,7 @@ descend_kernel(DescendParams P) {
             vec_t gx = 0, gy = 0;
             acc_t ei = 0;
             for (int t = rp[pos]; t < rp[pos + 1]; ++t) {
-              int j = cl[t];
+              int j = col[t];
               vec_t fx, fy;
               acc_t d = A::pair(xi, xw[j], fx, fy);
               gx += fx; gy += fy;
@@ -321,65 +406,133 @@ descend_kernel(DescendParams P) {
             vec_t fx, fy;
             acc_t d0 = A::wall(xi, R, Rm1sq, fx, fy);
             gx += fx; gy += fy;
-            aA[0] += ei + d0 * d0;
+            aA += ei + d0 * d0;
             gi.x = gx; gi.y = gy;
             g[pos] = gi;
           } else {
             gi = g[pos];
           }
           bA[0] += gi.x * gi.x + gi.y * gi.y;
+          VV sp, yp;
+          if (pending) { sp = Sv[(int64_t)st * n + pos]; yp = Yv[(int64_t)st * n + pos]; }
 #pragma unroll
-          for (int c = 0; c < kMaxSlots; ++c) {
-            if (c < count) {
-              int sl = S.ring[c];
-              VV s = Sv[(int64_t)sl * n + pos], y = Yv[(int64_t)sl * n + pos];
-              bA[1 + c] += gi.x * s.x + gi.y * s.y;
-              bA[1 + kMaxSlots + c] += gi.x * y.x + gi.y * y.y;
+          for (int a = 0; a < kMaxSlots; ++a) {
+            if (a < mm) {
+              const VV s_ = Sv[(int64_t)a * n + pos], y_ = Yv[(int64_t)a * n + pos];
+              bA[1 + a] += gi.x * s_.x + gi.y * s_.y;
+              bA[1 + KS + a] += gi.x * y_.x + gi.y * y_.y;
+              if (pending) {
+                bA[OP + a] += sp.x * s_.x + sp.y * s_.y;
+                bA[OP + KS + a] += sp.x * y_.x + sp.y * y_.y;
+                bA[OP + 2 * KS + a] += yp.x * s_.x + yp.y * s_.y;
+                bA[OP + 3 * KS + a] += yp.x * y_.x + yp.y * y_.y;
+              }
             }
           }
+          if (pending) {
+            bA[OP + 4 * KS + 0] += sp.x * sp.x + sp.y * sp.y;
+            bA[OP + 4 * KS + 1] += sp.x * yp.x + sp.y * yp.y;
+            bA[OP + 4 * KS + 2] += yp.x * yp.x + yp.y * yp.y;
+          }
         }
-        reduce<A, 1, 2 + 2 * kMaxSlots, 1>(S, aA, bA, cA);
+        reduce_many<A, NRA>(S, aA, bA);
         const acc_t Ep = fresh ? E : S.oa[0];
         const vec_t gg = S.ob[0];
         const sc_t gnorm = sqrt((sc_t)gg);
         gsum += gnorm;
         fresh = false;
+        // the pending pair joins the memory when s'y > curv_eps |s| |y| (Gram rows, then the ring)
+        if (pending) {
+          const vec_t ss = S.ob[OP + 4 * KS], sy = S.ob[OP + 4 * KS + 1], yy = S.ob[OP + 4 * KS + 2];
+          const bool push = (sc_t)sy > curv_eps * sqrt((sc_t)ss) * sqrt((sc_t)yy) && P.m > 0;
+          if (push) {
+            if (tid < count0) {
+              int sl = ring[2 + tid];
+              Gm[st * kBasis + sl] = Gm[sl * kBasis + st] = S.ob[OP + sl];
+              Gm[st * kBasis + KS + sl] = Gm[(KS + sl) * kBasis + st] = S.ob[OP + KS + sl];
+              Gm[(KS + st) * kBasis + sl] = Gm[sl * kBasis + KS + st] = S.ob[OP + 2 * KS + sl];
+              Gm[(KS + st) * kBasis + KS + sl] = Gm[(KS + sl) * kBasis + KS + st] = S.ob[OP + 3 * KS + sl];
+            }
+            if (tid == 0) {
+              Gm[st * kBasis + st] = ss;
+              Gm[st * kBasis + KS + st] = Gm[(KS + st) * kBasis + st] = sy;
+              Gm[(KS + st) * kBasis + KS + st] = yy;
+            }
+          }
+          __syncthreads();
+          if (tid == 0) {
+            if (push) {
+              int c = ring[0];
+              if (c < P.m) {
+                ring[2 + c] = st;
+                ring[0] = c + 1;
+                int fr = 0;  // first slot not in the ring
+                for (; fr < mm; ++fr) {
+                  bool used = false;
+                  for (int u = 0; u <= c; ++u) used |= (ring[2 + u] == fr);
+                  if (!used) break;
+                }
+                ring[1] = fr;
+              } else {
+                int ev = ring[2];
+                for (int u = 0; u + 1 < c; ++u) ring[2 + u] = ring[3 + u];
+                ring[2 + c - 1] = st;
+                ring[1] = ev;
+              }
+            }
+            ring[2 + kMaxSlots] = 0;
+          }
+          __syncthreads();
+        }
+        const int count = ring[0];
         if (!(gnorm > sc_t(0))) {
-          if (!isfinite(gnorm)) status = 5;
+          if (!isfinite((float)gnorm)) status = 5;
           continue;
         }
 
-        // ---- scalar two-loop on the Gram matrix (warp 0), lane = basis index
+        // ---- two-loop recursion on the Gram matrix (warp 0).  With ring positions c (oldest
+        // first), rho_c = 1 / s_c'y_c, the first loop is the back substitution
+        //   alpha_c = rho_c (s_c'g - sum_{d > c} alpha_d s_c'y_d),
+        // gamma = s'y / y'y of the newest pair, and the second loop the forward substitution
+        //   beta_c = rho_c (gamma (y_c'g - sum_d alpha_d y_c'y_d) + sum_{d < c} w_d y_c's_d),
+        // w_d = alpha_d - beta_d; then -H g = -gamma g + gamma sum_c alpha_c y_c - sum_c w_c s_c.
+        // Lane c holds row c; each substitution step is one broadcast.
         if (warp == 0) {
-          vec_t *G = S.gram;
-          if (lane < count) {
-            int sl = S.ring[lane];
-            G[GI * kBasis + sl] = G[sl * kBasis + GI] = S.ob[1 + lane];
-            G[GI * kBasis + KS + sl] = G[(KS + sl) * kBasis + GI] = S.ob[1 + kMaxSlots + lane];
-          }
-          if (lane == 0) G[GI * kBasis + GI] = gg;
-          __syncwarp();
-          vec_t del = (lane == GI) ? vec_t(1) : vec_t(0);
-          for (int c = count - 1; c >= 0; --c) {
-            int sl = S.ring[c];
-            vec_t prod = (lane < kBasis) ? del * G[sl * kBasis + lane] : vec_t(0);
-            vec_t a = warp_sum(prod) / G[sl * kBasis + KS + sl];
-            if (lane == 0) S.alpha[c] = a;
-            if (lane == KS + sl) del -= a;
+          const bool act = lane < count;
+          const int sl = act ? ring[2 + lane] : 0;
+          const vec_t rho = act ? vec_t(1) / Gm[sl * kBasis + KS + sl] : vec_t(0);
+          vec_t acc = act ? S.ob[1 + sl] : vec_t(0);
+          vec_t my_alpha = 0, my_w = 0, gam = 1;
+          for (int cc = count - 1; cc >= 0; --cc) {
+            const vec_t a = __shfl_sync(0xffffffffu, rho * acc, cc);
+            if (lane == cc) my_alpha = a;
+            const int slc = ring[2 + cc];
+            if (lane < cc) acc -= a * Gm[sl * kBasis + KS + slc];
           }
           if (count > 0) {
-            int nw_ = S.ring[count - 1];
-            vec_t gam = G[nw_ * kBasis + KS + nw_] / G[(KS + nw_) * kBasis + KS + nw_];
-            del *= gam;
+            const int nw_ = ring[2 + count - 1];
+            gam = Gm[nw_ * kBasis + KS + nw_] / Gm[(KS + nw_) * kBasis + KS + nw_];
           }
-          __syncwarp();
-          for (int c = 0; c < count; ++c) {
-            int sl = S.ring[c];
-            vec_t prod = (lane < kBasis) ? del * G[(KS + sl) * kBasis + lane] : vec_t(0);
-            vec_t bb = warp_sum(prod) / G[sl * kBasis + KS + sl];
-            if (lane == sl) del += S.alpha[c] - bb;
+          vec_t t = act ? S.ob[1 + KS + sl] : vec_t(0);
+          for (int dd = 0; dd < count; ++dd) {
+            const vec_t ad = __shfl_sync(0xffffffffu, my_alpha, dd);
+            const int sld = ring[2 + dd];
+            if (act) t -= ad * Gm[(KS + sl) * kBasis + KS + sld];
           }
-          if (lane < kBasis) S.coef[lane] = -del;
+          vec_t acc2 = gam * t;
+          for (int cc = 0; cc < count; ++cc) {
+            const vec_t bcc = __shfl_sync(0xffffffffu, rho * acc2, cc);
+            const vec_t w = __shfl_sync(0xffffffffu, my_alpha, cc) - bcc;
+            if (lane == cc) my_w = w;
+            const int slc = ring[2 + cc];
+            if (act && lane > cc) acc2 += w * Gm[slc * kBasis + KS + sl];
+          }
+          if (act) {
+            S.coef[sl] = -my_w;
+            S.coef[KS + sl] = gam * my_alpha;
+          }
+          const unsigned used = __reduce_or_sync(0xffffffffu, act ? (1u << sl) : 0u);
+          if (lane == 0) { S.coef[GI] = -gam; S.used = used; }
         }
         __syncthreads();
 
@@ -388,28 +541,30 @@ descend_kernel(DescendParams P) {
         vec_t disp2 = 0;
         for (int attempt = 0; attempt < 2 && !accepted; ++attempt) {
           if (attempt == 1) {
-            if (S.count == 0) break;
+            if (ring[0] == 0) break;
             __syncthreads();
-            if (tid == 0) { S.count = 0; meta[p * kMetaInts + 0] = 0; }
+            if (tid == 0) { ring[0] = 0; S.used = 0u; }
             ++resets;
             for (int u = tid; u < kBasis; u += T) S.coef[u] = (u == GI) ? vec_t(-1) : vec_t(0);
             __syncthreads();
           }
           // ---- pass B: direction, g'd and the largest per-circle move
           for (int round = 0; round < 2; ++round) {
-            const int cnt_now = S.count;
+            const unsigned used = S.used;
             acc_t aB[1] = {0};
             vec_t bB[1] = {0}, cB[1] = {0};
             for (int pos = b + tid; pos < e; pos += T) {
               VV gi = g[pos];
               vec_t cg = S.coef[GI];
               vec_t dx = cg * gi.x, dy = cg * gi.y;
-              for (int c = 0; c < cnt_now; ++c) {
-                int sl = S.ring[c];
-                vec_t cs = S.coef[sl], cy = S.coef[KS + sl];
-                VV s = Sv[(int64_t)sl * n + pos], y = Yv[(int64_t)sl * n + pos];
-                dx += cs * s.x + cy * y.x;
-                dy += cs * s.y + cy * y.y;
+#pragma unroll
+              for (int a = 0; a < kMaxSlots; ++a) {
+                if (a < mm && ((used >> a) & 1u)) {
+                  const VV s_ = Sv[(int64_t)a * n + pos], y_ = Yv[(int64_t)a * n + pos];
+                  const vec_t cs = S.coef[a], cy = S.coef[KS + a];
+                  dx += cs * s_.x + cy * y_.x;
+                  dy += cs * s_.y + cy * y_.y;
+                }
               }
               VV dd; dd.x = dx; dd.y = dy;
               dv[pos] = dd;
@@ -419,8 +574,8 @@ descend_kernel(DescendParams P) {
             reduce<A, 1, 1, 1>(S, aB, bB, cB);
             if (S.ob[0] < vec_t(0) || round == 1) break;
             // not a descent direction: drop the memory, take -g
-            if (tid == 0) { S.count = 0; meta[p * kMetaInts + 0] = 0; }
-            if (cnt_now > 0) ++resets;
+            if (tid == 0) { ring[0] = 0; S.used = 0u; }
+            if (used != 0u) ++resets;
             for (int u = tid; u < kBasis; u += T) S.coef[u] = (u == GI) ? vec_t(-1) : vec_t(0);
             __syncthreads();
           }
@@ -440,14 +595,14 @@ descend_kernel(DescendParams P) {
             }
             __syncthreads();
             // ---- pass D: trial batch energy and gradient, displacement since the build
-            acc_t aD[1] = {0};
-            vec_t bD[1] = {0}, cD[1] = {0};
+            acc_t aD = 0;
+            vec_t cD = 0;
             for (int pos = b + tid; pos < e; pos += T) {
               PP xi = xw[pos];
               vec_t gx = 0, gy = 0;
               acc_t ei = 0;
               for (int t = rp[pos]; t < rp[pos + 1]; ++t) {
-                int j = cl[t];
+                int j = col[t];
                 vec_t fx, fy;
                 acc_t d = A::pair(xi, xw[j], fx, fy);
                 gx += fx; gy += fy;
@@ -456,14 +611,14 @@ descend_kernel(DescendParams P) {
               vec_t fx, fy;
               acc_t d0 = A::wall(xi, R, Rm1sq, fx, fy);
               gx += fx; gy += fy;
-              aD[0] += ei + d0 * d0;
+              aD += ei + d0 * d0;
               VV gg_; gg_.x = gx; gg_.y = gy;
               gt[pos] = gg_;
               PP x0 = xb[pos];
               vec_t ex = (vec_t)(xi.x - x0.x), ey = (vec_t)(xi.y - x0.y);
-              cD[0] = max(cD[0], ex * ex + ey * ey);
+              cD = max(cD, ex * ex + ey * ey);
             }
-            reduce<A, 1, 1, 1>(S, aD, bD, cD);
+            reduce_sum_max<A>(S, aD, cD);
             ++trials;
             Et = S.oa[0];
             if (Et <= Ep + c1 * al * gd) {
@@ -482,79 +637,19 @@ descend_kernel(DescendParams P) {
         moved = 1;
         Dmax = max(Dmax, (sc_t)sqrt((sc_t)disp2));
 
-        // ---- pass E: secant pair s = x_new - x_old, y = g_new - g_old and its dots
+        // ---- pass E: the secant pair s = x_new - x_old, y = g_new - g_old goes to the stage slot;
+        // its dots and its curvature test come with this batch's next step
         {
-          const int st = S.stage, cnt_now = S.count;
-          acc_t aE[1] = {0};
-          vec_t bE[NDOT];
-          vec_t cE[1] = {0};
-#pragma unroll
-          for (int u = 0; u < NDOT; ++u) bE[u] = 0;
+          const int stg = ring[1];
           for (int pos = b + tid; pos < e; pos += T) {
             PP xn = xw[pos], x0 = xo[pos];
             VV s_; s_.x = (vec_t)(xn.x - x0.x); s_.y = (vec_t)(xn.y - x0.y);
             VV gn = gt[pos], go = g[pos];
             VV y_; y_.x = gn.x - go.x; y_.y = gn.y - go.y;
-            Sv[(int64_t)st * n + pos] = s_;
-            Yv[(int64_t)st * n + pos] = y_;
-#pragma unroll
-            for (int c = 0; c < kMaxSlots; ++c) {
-              if (c < cnt_now) {
-                int sl = S.ring[c];
-                VV s = Sv[(int64_t)sl * n + pos], y = Yv[(int64_t)sl * n + pos];
-                bE[c] += s_.x * s.x + s_.y * s.y;
-                bE[kMaxSlots + c] += s_.x * y.x + s_.y * y.y;
-                bE[2 * kMaxSlots + c] += y_.x * s.x + y_.y * s.y;
-                bE[3 * kMaxSlots + c] += y_.x * y.x + y_.y * y.y;
-              }
-            }
-            bE[4 * kMaxSlots + 0] += s_.x * s_.x + s_.y * s_.y;
-            bE[4 * kMaxSlots + 1] += s_.x * y_.x + s_.y * y_.y;
-            bE[4 * kMaxSlots + 2] += y_.x * y_.x + y_.y * y_.y;
+            Sv[(int64_t)stg * n + pos] = s_;
+            Yv[(int64_t)stg * n + pos] = y_;
           }
-          reduce<A, 1, NDOT, 1>(S, aE, bE, cE);
-          const vec_t ss = S.ob[4 * kMaxSlots], sy = S.ob[4 * kMaxSlots + 1], yy = S.ob[4 * kMaxSlots + 2];
-          const bool push = (sc_t)sy > curv_eps * sqrt((sc_t)ss) * sqrt((sc_t)yy) && P.m > 0;
-          if (push) {
-            vec_t *G = S.gram;
-            if (tid < cnt_now) {
-              int sl = S.ring[tid];
-              G[st * kBasis + sl] = G[sl * kBasis + st] = S.ob[tid];
-              G[st * kBasis + KS + sl] = G[(KS + sl) * kBasis + st] = S.ob[kMaxSlots + tid];
-              G[(KS + st) * kBasis + sl] = G[sl * kBasis + KS + st] = S.ob[2 * kMaxSlots + tid];
-              G[(KS + st) * kBasis + KS + sl] = G[(KS + sl) * kBasis + KS + st] = S.ob[3 * kMaxSlots + tid];
-            }
-            if (tid == 0) {
-              G[st * kBasis + st] = ss;
-              G[st * kBasis + KS + st] = G[(KS + st) * kBasis + st] = sy;
-              G[(KS + st) * kBasis + KS + st] = yy;
-            }
-            __syncthreads();
-            for (int u = tid; u < kBasis * kBasis; u += T) gramg[(size_t)p * kBasis * kBasis + u] = S.gram[u];
-            if (tid == 0) {
-              int c = S.count;
-              if (c < P.m) {
-                S.ring[c] = st;
-                S.count = c + 1;
-                int fr = 0;  // first slot not in the ring
-                for (; fr < mm; ++fr) {
-                  bool used = false;
-                  for (int u = 0; u <= c; ++u) used |= (S.ring[u] == fr);
-                  if (!used) break;
-                }
-                S.stage = fr;
-              } else {
-                int ev = S.ring[0];
-                for (int u = 0; u + 1 < c; ++u) S.ring[u] = S.ring[u + 1];
-                S.ring[c - 1] = st;
-                S.stage = ev;
-              }
-              meta[p * kMetaInts + 0] = S.count;
-              meta[p * kMetaInts + 1] = S.stage;
-              for (int u = 0; u < kMaxSlots; ++u) meta[p * kMetaInts + 2 + u] = S.ring[u];
-            }
-            __syncthreads();
-          }
+          if (tid == 0) ring[2 + kMaxSlots] = 1;
           if (k == 1) { fresh = true; E = Et; }
         }
       }
@@ -566,8 +661,12 @@ descend_kernel(DescendParams P) {
           if (!anm_rebuild()) { status = 4; break; }
         }
       }
-      if (!(k == 1 && fresh)) { E = full_energy(); }
-      if (!isfinite((double)E)) { status = 5; break; }
+      // the FP32 phase needs the total energy only for its stagnation check (its e_tol is out of
+      // binary32's reach); the FP64 phases test E <= e_tol after every sweep
+      const bool check_now = A::kId != 1 || P.stall_window <= 0 || iters % P.stall_window == 0;
+      if (check_now && !(k == 1 && fresh)) { E = full_energy(); e_at = iters; }
+      if (k == 1 && fresh) e_at = iters;
+      if (!isfinite(E)) { status = 5; break; }
       if (E <= (acc_t)P.e_tol) { status = 0; break; }
       if (gsum <= gsum_tol) { status = 1; break; }
       if (!moved) { status = 2; break; }
@@ -585,6 +684,7 @@ descend_kernel(DescendParams P) {
       }
     }
 
+    if (status < 4 && e_at != iters) E = full_energy();  // the final energy of the run
     // ---- 4. merge: scatter back to the caller's order
     for (int pos = tid; pos < n; pos += T) {
       int i = perm[pos];
@@ -609,10 +709,13 @@ descend_kernel(DescendParams P) {
         O->builds = builds; O->changes = changes; O->trials = trials; O->resets = resets; O->stalls = stalls;
         O->iters32 = iters; O->trials32 = trials;
       }
-      O->cur = cur;
     }
     __syncthreads();
   }
+}
+
+template <class A> cudaError_t set_smem(size_t bytes) {
+  return cudaFuncSetAttribute(descend_kernel<A, MaxT<A>::v>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
 }  // namespace
@@ -626,24 +729,47 @@ cudaError_t launch_stamp(long long *t0, cudaStream_t s) {
 
 cudaError_t launch_descend(int arith, const DescendParams &p, int grid, int block, cudaStream_t s) {
   if (grid <= 0) return cudaSuccess;
-  if (arith == 0) descend_kernel<Arith64><<<grid, block, 0, s>>>(p);
-  else if (arith == 1) descend_kernel<Arith32><<<grid, block, 0, s>>>(p);
-  else descend_kernel<ArithMix><<<grid, block, 0, s>>>(p);
+  const size_t sm = p.smem_bytes;
+  if (arith == 0) descend_kernel<Arith64, MaxT<Arith64>::v><<<grid, block, sm, s>>>(p);
+  else if (arith == 1) descend_kernel<Arith32, MaxT<Arith32>::v><<<grid, block, sm, s>>>(p);
+  else descend_kernel<ArithMix, MaxT<ArithMix>::v><<<grid, block, sm, s>>>(p);
   return cudaGetLastError();
 }
 
-cudaError_t descend_attributes(int arith, cudaFuncAttributes *attr) {
-  if (arith == 0) return cudaFuncGetAttributes(attr, descend_kernel<Arith64>);
-  if (arith == 1) return cudaFuncGetAttributes(attr, descend_kernel<Arith32>);
-  return cudaFuncGetAttributes(attr, descend_kernel<ArithMix>);
+cudaError_t descend_prepare(int arith, size_t smem_bytes) {
+  if (arith == 0) return set_smem<Arith64>(smem_bytes);
+  if (arith == 1) return set_smem<Arith32>(smem_bytes);
+  return set_smem<ArithMix>(smem_bytes);
 }
 
-int descend_max_block(int arith) { return arith == 0 ? 256 : 512; }
+size_t descend_static_smem(int arith) {
+  if (arith == 0) return sizeof(Smem<Arith64>);
+  if (arith == 1) return sizeof(Smem<Arith32>);
+  return sizeof(Smem<ArithMix>);
+}
 
-cudaError_t descend_occupancy(int arith, int block, int *bps) {
-  if (arith == 0) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, descend_kernel<Arith64>, block, 0);
-  if (arith == 1) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, descend_kernel<Arith32>, block, 0);
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, descend_kernel<ArithMix>, block, 0);
+cudaError_t descend_attributes(int arith, cudaFuncAttributes *attr) {
+  if (arith == 0) return cudaFuncGetAttributes(attr, descend_kernel<Arith64, MaxT<Arith64>::v>);
+  if (arith == 1) return cudaFuncGetAttributes(attr, descend_kernel<Arith32, MaxT<Arith32>::v>);
+  return cudaFuncGetAttributes(attr, descend_kernel<ArithMix, MaxT<ArithMix>::v>);
+}
+
+int descend_max_block(int arith) { return arith == 1 ? 512 : 256; }
+
+cudaError_t descend_occupancy(int arith, int block, size_t smem, int *bps) {
+  if (arith == 0) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, descend_kernel<Arith64, MaxT<Arith64>::v>, block, smem);
+  if (arith == 1) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, descend_kernel<Arith32, MaxT<Arith32>::v>, block, smem);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, descend_kernel<ArithMix, MaxT<ArithMix>::v>, block, smem);
+}
+
+// Shared-memory bytes the working set of an instance of n circles (k batches) asks for.
+size_t descend_smem_need(int arith, int n, int k, int ncx) {
+  const size_t pos = arith == 1 ? 8 : 16, vec = arith == 0 ? 16 : 8, sc = arith == 0 ? 8 : 4;
+  auto al = [](size_t b) { return (b + 15) & ~size_t(15); };
+  size_t b = al(pos * n) + 3 * al(vec * n) + al(4 * (size_t)(n + 1)) + al(2 * (size_t)(10 * n + 64)) + al(pos * n) +
+             al(sc * (size_t)k * kBasis * kBasis) + al(4 * (2 * (size_t)ncx * ncx + 2)) + 2 * al(4 * (size_t)n) +
+             al(pos * n);
+  return b;
 }
 
 }  // namespace pecc

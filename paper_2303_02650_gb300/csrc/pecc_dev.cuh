@@ -33,6 +33,8 @@ struct InstDesc {
   int64_t gram_off;         // k * kBasis * kBasis Gram entries
   int64_t meta_off;         // k * kMetaInts ring metadata
   double R, inv_cs;
+  float inv_f;              // binary32 grid of the FP32 descent: 1 / side, side >= l_cut (1 + 2^-10)
+  int32_t ncx_f;            // its cells per side (<= ncx)
 };
 
 struct InstOut {
@@ -131,6 +133,25 @@ __device__ __forceinline__ void block_sum(T (&v)[NV], T *scratch, T *out) {
   __syncthreads();
 }
 
+// Reduce-scatter of NV values over the 32 lanes of a warp (NV a multiple of 32): after the
+// call, lane L holds in v[0 .. NV/32) the warp totals of the values with indices
+// (NV/32) * L + j.  Takes NV - NV/32 shuffles instead of 5 NV for NV separate reductions.
+template <typename T, int NV>
+__device__ __forceinline__ void warp_reduce_scatter(T (&v)[NV]) {
+  static_assert(NV % 32 == 0, "NV must be a multiple of 32");
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 16, len = NV; o > 0; o >>= 1, len >>= 1) {
+    const bool hi = (lane & o) != 0;
+#pragma unroll
+    for (int j = 0; j < len / 2; ++j) {
+      T keep = hi ? v[j + len / 2] : v[j];
+      T send = hi ? v[j] : v[j + len / 2];
+      v[j] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+}
+
 // Inclusive prefix sum of a[0..len) in place (int32), whole block.
 __device__ inline void block_scan_inplace(int32_t *a, int len, int32_t *sh /*>=33 ints*/) {
   const int T = blockDim.x, t = threadIdx.x, lane = t & 31, w = t >> 5, nw = T >> 5;
@@ -162,23 +183,60 @@ __device__ inline void block_scan_inplace(int32_t *a, int len, int32_t *sh /*>=3
 }
 
 // ------------------------------------------------------- neighbor build ----
-// Cell binning and stable key sort, then CSR rows over the 3x3 cells, each row
-// ascending.  x: n positions of one instance; lists go to rp[0..n], col[0..cap).
-// cells: 2 * ncell + 2 int32 of scratch; ckey/corder: n each.
-// Returns the number of entries (block-uniform); > cap means overflow and the
-// rows are then incomplete.
+// Cell grid of one instance.  Binary64 keys use the grid of the host (side l_cut (1 + 2^-20));
+// the binary32 descent uses its own grid with side l_cut (1 + 2^-10), a margin far above the
+// rounding of (x + R) / side in binary32, so that circles closer than l_cut are never two
+// cells apart.  Either grid only accelerates the search: the set Gamma(i) is fixed by the
+// predicate alone.
+struct CellGrid {
+  double R, inv;
+  float Rf, invf;
+  int nc;
+  bool f32;
+};
+
 template <typename T>
-__device__ int cta_build_neighbors(const v2<T> *__restrict__ x, int n, double R, double inv, int nc,
-                                   T lc2, uint32_t *ckey, int32_t *corder, int32_t *cells,
-                                   int32_t *rp, int32_t *col, int cap, int32_t *sh) {
+__device__ __forceinline__ uint32_t grid_key(v2<T> p, const CellGrid &G) {
+  if (G.f32) {
+    float fx = ((float)p.x + G.Rf) * G.invf, fy = ((float)p.y + G.Rf) * G.invf;
+    int cx = !(fx >= 0.f) ? 0 : (fx >= (float)G.nc ? G.nc - 1 : (int)fx);
+    int cy = !(fy >= 0.f) ? 0 : (fy >= (float)G.nc ? G.nc - 1 : (int)fy);
+    return (uint32_t)cy * (uint32_t)G.nc + (uint32_t)cx;
+  }
+  return cell_key<T>(p, G.R, G.inv, G.nc);
+}
+
+// 32-bit integer finaliser (xor-shift-multiply); a pair's digest term.  The digest only
+// decides ANM's deferral length, never which list is used, so a collision costs nothing but
+// a schedule change.
+__device__ __forceinline__ unsigned long long mix32(uint32_t x) {
+  x ^= x >> 16; x *= 0x7feb352du;
+  x ^= x >> 15; x *= 0x846ca68bu;
+  x ^= x >> 16;
+  return (unsigned long long)x;
+}
+
+// Cell binning and stable key sort, then CSR rows over the 3x3 cells.  x: n positions of
+// one instance; lists go to rp[0..n], col[0..cap).  cells: 2 * nc^2 + 2 int32 of scratch;
+// ckey/corder: n each; xs: n positions of scratch (the coordinates in cell order, so that
+// the three cells of a row of the 3x3 block are one contiguous range).  All pointers may
+// be shared or global memory.  sort_rows: rows ascending in j (else in cell-scan order,
+// still deterministic).  Returns the number of entries (block-uniform); > cap means
+// overflow and the rows are then not written.  hash (shared, may be null) receives an
+// order-independent 64-bit digest of the pair set, used to tell Gamma' from Gamma.
+template <typename T, typename IdxT>
+__device__ int cta_build_neighbors(const v2<T> *__restrict__ x, int n, const CellGrid &G, T lc2,
+                                   uint32_t *ckey, int32_t *corder, int32_t *cells, v2<T> *xs, int32_t *rp,
+                                   IdxT *col, int cap, int32_t *sh, unsigned long long *hash, bool sort_rows) {
   const int T_ = blockDim.x, t = threadIdx.x;
-  const int ncell = nc * nc;
+  const int nc = G.nc, ncell = nc * nc;
   int32_t *cstart = cells;              // ncell + 1
   int32_t *cfill = cells + ncell + 1;   // ncell
   for (int c = t; c <= ncell; c += T_) cstart[c] = 0;
+  if (t == 0 && hash) *hash = 0ull;
   __syncthreads();
   for (int i = t; i < n; i += T_) {
-    uint32_t key = cell_key<T>(x[i], R, inv, nc);
+    uint32_t key = grid_key<T>(x[i], G);
     ckey[i] = key;
     atomicAdd(&cstart[key + 1], 1);
   }
@@ -201,45 +259,59 @@ __device__ int cta_build_neighbors(const v2<T> *__restrict__ x, int n, double R,
     }
   }
   __syncthreads();
-  // count
+  for (int q = t; q < n; q += T_) xs[q] = x[corder[q]];
   if (t == 0) rp[0] = 0;
-  for (int i = t; i < n; i += T_) {
-    v2<T> xi = x[i];
-    uint32_t key = ckey[i];
-    int cx = (int)(key % (uint32_t)nc), cy = (int)(key / (uint32_t)nc);
+  __syncthreads();
+  // count: circles visited in cell order, candidates as three contiguous row ranges
+  for (int q0 = t; q0 < n; q0 += T_) {
+    const int i = corder[q0];
+    const v2<T> xi = xs[q0];
+    const uint32_t key = ckey[i];
+    const int cx = (int)(key % (uint32_t)nc), cy = (int)(key / (uint32_t)nc);
+    const int bx0 = max(cx - 1, 0), bx1 = min(cx + 1, nc - 1);
     int cntn = 0;
-    for (int by = max(cy - 1, 0); by <= min(cy + 1, nc - 1); ++by)
-      for (int bx = max(cx - 1, 0); bx <= min(cx + 1, nc - 1); ++bx) {
-        int c = by * nc + bx;
-        for (int q = cstart[c]; q < cstart[c + 1]; ++q) {
-          int j = corder[q];
-          if (j != i && nbr_pred(xi, x[j], lc2)) ++cntn;
-        }
-      }
+    for (int by = max(cy - 1, 0); by <= min(cy + 1, nc - 1); ++by) {
+      const int lo = cstart[by * nc + bx0], hi = cstart[by * nc + bx1 + 1];
+      for (int qq = lo; qq < hi; ++qq) cntn += nbr_pred(xi, xs[qq], lc2) && qq != q0;
+    }
     rp[i + 1] = cntn;
   }
   __syncthreads();
   block_scan_inplace(rp + 1, n, sh);
   const int total = rp[n];
   if (total <= cap) {
-    for (int i = t; i < n; i += T_) {
-      v2<T> xi = x[i];
-      uint32_t key = ckey[i];
-      int cx = (int)(key % (uint32_t)nc), cy = (int)(key / (uint32_t)nc);
-      int w = rp[i], lo = w;
-      for (int by = max(cy - 1, 0); by <= min(cy + 1, nc - 1); ++by)
-        for (int bx = max(cx - 1, 0); bx <= min(cx + 1, nc - 1); ++bx) {
-          int c = by * nc + bx;
-          for (int q = cstart[c]; q < cstart[c + 1]; ++q) {
-            int j = corder[q];
-            if (j != i && nbr_pred(xi, x[j], lc2)) col[w++] = j;
+    unsigned long long h = 0ull;
+    for (int q0 = t; q0 < n; q0 += T_) {
+      const int i = corder[q0];
+      const v2<T> xi = xs[q0];
+      const uint32_t key = ckey[i];
+      const int cx = (int)(key % (uint32_t)nc), cy = (int)(key / (uint32_t)nc);
+      const int bx0 = max(cx - 1, 0), bx1 = min(cx + 1, nc - 1);
+      int w = rp[i];
+      const int first = w;
+      for (int by = max(cy - 1, 0); by <= min(cy + 1, nc - 1); ++by) {
+        const int lo = cstart[by * nc + bx0], hi = cstart[by * nc + bx1 + 1];
+        for (int qq = lo; qq < hi; ++qq) {
+          if (nbr_pred(xi, xs[qq], lc2) && qq != q0) {
+            const int j = corder[qq];
+            col[w++] = (IdxT)j;
+            if (hash) h += mix32((uint32_t)i * 0x9E3779B1u ^ (uint32_t)j);
           }
         }
-      for (int a = lo + 1; a < w; ++a) {
-        int v = col[a], b = a - 1;
-        while (b >= lo && col[b] > v) { col[b + 1] = col[b]; --b; }
-        col[b + 1] = v;
       }
+      if (sort_rows) {
+        for (int a = first + 1; a < w; ++a) {
+          IdxT v = col[a];
+          int b = a - 1;
+          while (b >= first && col[b] > v) { col[b + 1] = col[b]; --b; }
+          col[b + 1] = v;
+        }
+      }
+    }
+    if (hash) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) h += __shfl_xor_sync(0xffffffffu, h, o);
+      if ((t & 31) == 0) atomicAdd(hash, h);
     }
   }
   __syncthreads();

@@ -33,6 +33,8 @@ struct DescendParams {
   int stall_window;
   const long long *t0;    // %globaltimer at the start of the call (written by stamp_kernel)
   long long budget_ns;    // 0 = no time budget
+  int k_override;         // > 0: batches per instance for this phase (capped at the instance's k)
+  size_t smem_bytes;      // dynamic shared memory per block for the working set
 };
 
 cudaError_t launch_stamp(long long *t0, cudaStream_t s);
@@ -41,7 +43,10 @@ cudaError_t launch_stamp(long long *t0, cudaStream_t s);
 cudaError_t launch_descend(int arith, const DescendParams &p, int grid, int block, cudaStream_t s);
 cudaError_t descend_attributes(int arith, cudaFuncAttributes *attr);
 int descend_max_block(int arith);
-cudaError_t descend_occupancy(int arith, int block, int *blocks_per_sm);
+cudaError_t descend_occupancy(int arith, int block, size_t smem, int *blocks_per_sm);
+cudaError_t descend_prepare(int arith, size_t smem_bytes);
+size_t descend_static_smem(int arith);
+size_t descend_smem_need(int arith, int n, int k, int ncx);
 
 // Standalone kernels (pecc_kernels.cu).
 struct StandaloneParams {
@@ -60,6 +65,7 @@ struct StandaloneParams {
   uint32_t *ckey_t;
   int32_t *corder_t;
   void *xtmp;                 // per-circle double2 scratch
+  void *xtmp2;                // another per-circle double2 scratch
   double l_cut, rebuild_disp;
 };
 

@@ -93,8 +93,10 @@ __global__ void build_kernel(StandaloneParams P, int force, int32_t *rebuilt, in
   }
   if (go) {
     const T lc2 = (T)(P.l_cut * P.l_cut);
-    int tot = cta_build_neighbors<T>(x, n, D.R, D.inv_cs, D.ncx, lc2, P.ckey + D.off, P.corder + D.off,
-                                     P.cells + D.cell_off, P.rp + D.off + q, P.col + D.col_s_off, D.cap, sh);
+    CellGrid G{D.R, D.inv_cs, 0.f, 0.f, D.ncx, false};
+    int tot = cta_build_neighbors<T, int32_t>(x, n, G, lc2, P.ckey + D.off, P.corder + D.off, P.cells + D.cell_off,
+                                     (PP *)P.xtmp + D.off, P.rp + D.off + q, P.col + D.col_s_off, D.cap, sh,
+                                     nullptr, true);
     for (int i = threadIdx.x; i < n; i += blockDim.x) xb[i] = x[i];
     if (threadIdx.x == 0 && status) status[q] = tot > D.cap ? 4 : 0;
   } else if (threadIdx.x == 0 && status) {
@@ -184,8 +186,9 @@ __global__ void feasible_kernel(StandaloneParams P, int from32, double tol, uint
   int32_t *rp = P.rp_t + D.rp_off;
   int32_t *cl = P.col_t + D.col_off;
   const double lc2 = P.l_cut * P.l_cut;
-  int tot = cta_build_neighbors<double>(x, n, D.R, D.inv_cs, D.ncx, lc2, P.ckey_t + D.off, P.corder_t + D.off,
-                                        P.cells + D.cell_off, rp, cl, 2 * D.cap, sh);
+  CellGrid G{D.R, D.inv_cs, 0.f, 0.f, D.ncx, false};
+  int tot = cta_build_neighbors<double, int32_t>(x, n, G, lc2, P.ckey_t + D.off, P.corder_t + D.off, P.cells + D.cell_off,
+                                        (double2 *)P.xtmp2 + D.off, rp, cl, 2 * D.cap, sh, nullptr, false);
   double m = 0.0;
   int bad = 0;
   if (tot <= 2 * D.cap) {
