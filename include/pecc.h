@@ -215,6 +215,29 @@ pecc_status pecc_phase_times(pecc_ctx *ctx, float *ms_host);
 /* The launch shape the context uses for its descent kernels. */
 pecc_status pecc_get_launch(pecc_ctx *ctx, int32_t *block_threads, int32_t *blocks_per_sm, int32_t *grid);
 
+/* Largest instance pecc_check_feasible_noalloc accepts. */
+#define PECC_NOALLOC_MAX_N 4096
+
+/* The feasibility check of pecc_check_feasible for ONE instance, without any device allocation.
+ * The paper has no counterpart: this is a service for callers that cannot call cudaMalloc
+ * (code running while its stream is captured into a CUDA graph, plug-ins whose host owns all
+ * device memory, real-time loops).  Its scratch (about 0.6 MB) is a fixed array in device
+ * memory that every GPU loading the library holds until the process exits.
+ *   xy_dev          device double[2 n], interleaved (x, y)
+ *   n               0 .. PECC_NOALLOC_MAX_N circles, else PECC_ERR_ARG (nothing launched)
+ *   R, l_cut        container radius > 0, neighbor cutoff > 2 of the FP64 cell list
+ *   tol             feasible when the largest depth <= tol
+ *   feasible_dev    device uint8[1];  max_overlap_dev  device double[1] (NaN if not checkable)
+ *   stream          cudaStream_t the kernel is enqueued on (NULL = legacy default stream)
+ * The first call on a device takes the array's device address (cudaGetSymbolAddress, with that
+ * device current); make that first call before any stream capture.  Every call shares the one
+ * array and finds the previous call's contents there (the kernel clears what must start at
+ * zero); calls whose kernels overlap on the GPU race on it, so order them on one stream.  Errors
+ * are returned synchronously; the message is in pecc_last_error(NULL).  Results are identical
+ * to pecc_check_feasible's for the same coordinates. */
+pecc_status pecc_check_feasible_noalloc(const double *xy_dev, int32_t n, double R, double l_cut, double tol,
+                                        uint8_t *feasible_dev, double *max_overlap_dev, void *stream);
+
 /* Text of the last error on this context (or of the last failed pecc_create when ctx is NULL). */
 const char *pecc_last_error(pecc_ctx *ctx);
 

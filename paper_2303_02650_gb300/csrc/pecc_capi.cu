@@ -52,6 +52,10 @@ struct pecc_ctx {
 
 static std::string g_create_err;
 
+namespace pecc {
+void set_global_error(const char *msg) { g_create_err = msg; }
+}  // namespace pecc
+
 static pecc_status fail(pecc_ctx *c, pecc_status s, const char *fmt, ...) {
   char buf[512];
   va_list ap;
@@ -305,20 +309,8 @@ pecc_status pecc_destroy(pecc_ctx *ctx) {
 
 const char *pecc_last_error(pecc_ctx *ctx) { return ctx ? ctx->err.c_str() : g_create_err.c_str(); }
 
-// Cell grid of one instance: side l_cut (1 + 2^-20), ncx = ceil(2R / side), capped at
-// max(16, ceil(2 sqrt(n))) cells per side (the side then grows to 2R / ncx).
 static void cell_grid(double R, double l_cut, int n, double *inv, int *nc, double margin = 1.0 / 1048576.0) {
-  double cs = l_cut * (1.0 + margin);
-  double iv = 1.0 / cs;
-  double w = std::ceil((2.0 * R) * iv);
-  int cap = std::max(16, (int)std::ceil(2.0 * std::sqrt((double)n)));
-  int c = (w >= 1.0) ? (int)std::min<double>(w, 65535.0) : 1;
-  if (c > cap) {
-    c = cap;
-    iv = (double)c / (2.0 * R);
-  }
-  *inv = iv;
-  *nc = c;
+  host_cell_grid(R, l_cut, n, inv, nc, margin);
 }
 
 pecc_status pecc_set_radius(pecc_ctx *ctx, const double *R_dev) {

@@ -8,6 +8,26 @@
 
 namespace pecc {
 
+// Cell grid of one instance (host side): side l_cut (1 + margin), ncx = ceil(2R / side), capped at
+// max(16, ceil(2 sqrt(n))) cells per side (the side then grows to 2R / ncx).
+inline void host_cell_grid(double R, double l_cut, int n, double *inv, int *nc, double margin = 1.0 / 1048576.0) {
+  double cs = l_cut * (1.0 + margin);
+  double iv = 1.0 / cs;
+  double w = ceil((2.0 * R) * iv);
+  int cap = (int)ceil(2.0 * sqrt((double)n));
+  if (cap < 16) cap = 16;
+  int c = (w >= 1.0) ? (int)(w > 65535.0 ? 65535.0 : w) : 1;
+  if (c > cap) {
+    c = cap;
+    iv = (double)c / (2.0 * R);
+  }
+  *inv = iv;
+  *nc = c;
+}
+
+// Message of the last failed call that has no context (read by pecc_last_error(NULL)).
+void set_global_error(const char *msg);
+
 // Everything a descent kernel reads or writes; device pointers into the context's buffers.
 struct DescendParams {
   const InstDesc *desc;

@@ -43,7 +43,9 @@ _EXPORTS = ["pecc_config_default", "pecc_create", "pecc_destroy", "pecc_set_radi
             "pecc_init_random", "pecc_get_positions", "pecc_rebuild_neighbors", "pecc_rebuild_neighbors_ex",
             "pecc_neighbor_count", "pecc_export_neighbors", "pecc_export_cells", "pecc_energy_grad",
             "pecc_energy_grad_ex", "pecc_descend", "pecc_get_energy", "pecc_check_feasible", "pecc_solve_host",
-            "pecc_get_counters", "pecc_get_launch", "pecc_last_error", "pecc_get_stats", "pecc_phase_times"]
+            "pecc_get_counters", "pecc_get_launch", "pecc_last_error", "pecc_get_stats", "pecc_phase_times",
+            "pecc_check_feasible_noalloc"]
+NOALLOC_MAX_N = 4096
 
 
 def library_path() -> str:
@@ -87,6 +89,7 @@ def load(build_if_missing: bool = True):
         "pecc_last_error": (C.c_char_p, [vp]),
         "pecc_get_stats": (st, [vp, vp]),
         "pecc_phase_times": (st, [vp, C.POINTER(C.c_float)]),
+        "pecc_check_feasible_noalloc": (st, [vp, C.c_int32, C.c_double, C.c_double, C.c_double, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -110,6 +113,22 @@ def _ptr(t):
     if t is None:
         return None
     return C.c_void_p(t.data_ptr())
+
+
+def check_feasible_noalloc(xy, R, l_cut=2.5, tol=1e-9, stream=None):
+    """pecc_check_feasible_noalloc on one instance (device tensor xy [n, 2] float64): returns
+    (feasible uint8[1], max_overlap float64[1]) device tensors; allocates no device scratch."""
+    L = load()
+    n = int(xy.shape[0]) if xy is not None else 0
+    dev = xy.device if xy is not None else torch.device("cuda")
+    feas = torch.empty(1, dtype=torch.uint8, device=dev)
+    mo = torch.empty(1, dtype=torch.float64, device=dev)
+    s = (stream or torch.cuda.current_stream()).cuda_stream
+    rc = L.pecc_check_feasible_noalloc(_ptr(xy) if n else None, n, float(R), float(l_cut), float(tol), _ptr(feas),
+                                       _ptr(mo), C.c_void_p(s))
+    if rc != 0:
+        raise PeccError(f"pecc_check_feasible_noalloc: {ERRORS.get(rc, rc)}: {L.pecc_last_error(None).decode()}")
+    return feas, mo
 
 
 class Context:
