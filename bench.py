@@ -10,6 +10,7 @@ the FP64 feasibility check.  Workloads:
   c2      one instance n = 1000, u = 0.83; FP32 + FP64 polish
   c2-fp64 the same, plain FP64
   c1      one instance n = 50, u = 0.80; plain FP64
+  c4      one instance n = 100000, u = 0.85; FP32, whole-GPU descent (pair-gradient evaluations/s)
 Prints one JSON line.  --impl reference times the FP64 CPU oracle on the same workload instead.
 """
 from __future__ import annotations
@@ -43,9 +44,12 @@ def workload(name: str):
     elif name == "c1":
         n, R = np.array([50], dtype=np.int32), np.array([synth.radius(50, 0.80)])
         desc = "plain method: 1 instance n=50, R=sqrt(n/0.80), disk init"
+    elif name == "c4":
+        n, R = np.array([100000], dtype=np.int32), np.array([synth.radius(100000, 0.85)])
+        desc = "large-n scaling: 1 instance n=100000, R=sqrt(n/0.85), disk init, FP32, whole-GPU descent"
     else:
         raise SystemExit(f"unknown workload {name}")
-    prec = 0 if (name.endswith("fp64") or name == "c1") else 2
+    prec = 0 if (name.endswith("fp64") or name == "c1") else (1 if name == "c4" else 2)
     return n, R, prec, desc
 
 
@@ -140,10 +144,18 @@ def run_ours(args, rank, world, local):
     kvec = np.minimum(kvec, np.maximum(n, 1))
     seed0 = args.seed + 1_000_003 * rank
 
-    def step(s):
+    def step(s, ev=None):
+        if ev:
+            ev[0].record()
         ctx.init_random(seed0 + s)
+        if ev:
+            ev[1].record()
         ctx.descend()
+        if ev:
+            ev[2].record()
         feas, mo = ctx.check_feasible(1e-9)
+        if ev:
+            ev[3].record()
         return feas
 
     for w in range(args.warmup):
@@ -152,27 +164,36 @@ def run_ours(args, rank, world, local):
     if dist:
         dist.barrier()
     feas_sum = torch.zeros((), dtype=torch.int64, device="cuda")
-    phase_ms, phase_bytes, phase2_ms = [], [], []
-    it_all, st_all = [], []
+    phase_ms, phase_bytes, phase2_ms, split_ms = [], [], [], []
+    it_all, st_all, tr_all = [], [], []
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    big = bool(np.any(n >= 16384))
     with Clocks(local) as clk:
         torch.cuda.synchronize()
         e0.record()
         for s in range(args.steps):
-            feas = step(s)
+            feas = step(s, evs[s])
             feas_sum += feas.to(torch.int64).sum()
             # device time of the descent kernels of this step (events inside the graph)
             ms = ctx.phase_times()
             st = ctx.get_stats().cpu().numpy()
+            if big:  # the whole-GPU kernel runs after the graph: time it by the events around the call
+                evs[s][2].synchronize()
+                ms = (evs[s][1].elapsed_time(evs[s][2]), 0.0, evs[s][1].elapsed_time(evs[s][2]))
             phase_ms.append(ms[0])
             phase2_ms.append(ms[1])
             phase_bytes.append(algorithmic_bytes_descent(n, kvec, st[:, 8], st[:, 9], 10,
                                                          16 if prec == 0 else 8))
             it_all.append(st[:, 0])
             st_all.append(st[:, 1])
+            tr_all.append(st[:, 4])
         e1.record()
         torch.cuda.synchronize()
+    for ev in evs:
+        split_ms.append([ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]), ev[2].elapsed_time(ev[3])])
+    split_ms = np.array(split_ms)
     if dist:
         dist.barrier()
     ms_total = e0.elapsed_time(e1)
@@ -190,6 +211,14 @@ def run_ours(args, rank, world, local):
     # neighbor-pair gradient evaluations per second inside the descent (first phase)
     # and the standalone fused energy + gradient kernel against the HBM roofline
     eg = energy_grad_roofline(ctx, torch, n)
+    # directed neighbor-pair gradient evaluations inside the descent: every sweep evaluates each
+    # circle's row once (the fresh pass), every line-search trial the rows of its batch
+    nnz_per_circle = eg["neighbor_entries"] / max(1, int(n.sum()))
+    evals = 0.0
+    for it, tr in zip(it_all, tr_all):
+        evals += float(np.sum(n * nnz_per_circle * (it + tr / kvec)))
+    descent_ms = float(np.sum(split_ms[:, 1]))
+    pair_evals = evals / (descent_ms / 1e3)
 
     # end to end through the host-buffer entry point (copies inside the timed region)
     e2e_ms, e2e_feas = 0.0, 0
@@ -224,17 +253,21 @@ def run_ours(args, rank, world, local):
         "success_rate": round(feasible / solved, 4),
         "iters_mean": round(float(its.mean()), 1),
         "status_counts": np.bincount(sts, minlength=7).tolist(),
-        "pair_grad_evals_per_s": eg.get("pair_evals_per_s_descent"),
+        "pair_grad_evals_per_s": round(pair_evals, 1),
+        "pair_grad_evals_note": "directed neighbor-pair gradient evaluations per second of descent time",
+        "step_split_ms": {"init": round(float(split_ms[:, 0].mean()), 3), "descend": round(float(split_ms[:, 1].mean()), 3),
+                          "check": round(float(split_ms[:, 2].mean()), 3)},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                      "frac": round(achieved / hbm, 4), "traffic": None,
-                     "kernel": "descend_kernel<Arith64>" if prec == 0 else "descend_kernel<Arith32> (FP32 bulk phase)",
+                     "kernel": ("descend_grid_kernel" if big else "descend_kernel") +
+                               ("<Arith64>" if prec == 0 else "<Arith32> (FP32 bulk phase)"),
                      "peak_kind": peak_kind, "avg_launch_ms": round(dom_ms, 3),
                      "algorithmic_bytes_per_launch": dom_bytes,
                      "polish_kernel_ms": round(float(np.mean(phase2_ms)), 3)},
         "energy_grad_roofline": eg,
         "e2e": {"value": round(e2e_feas / (e2e_ms / 1e3), 3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
-        "gpu_launches": (4 if prec == 0 else 5) * args.steps,
+        "gpu_launches": (4 if prec == 0 else 5) * args.steps + (2 if prec == 2 else 1) * args.steps * int(big),
         "clocks": clk.summary(),
     }
     ctx.close()
@@ -343,7 +376,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c3", choices=["c3", "c3-fp64", "c2", "c2-fp64", "c1"])
+    ap.add_argument("--workload", default="c3", choices=["c3", "c3-fp64", "c2", "c2-fp64", "c1", "c4"])
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--instances", type=int, default=0, help="use only the first N instances (small profiling case)")

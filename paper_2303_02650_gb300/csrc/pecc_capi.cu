@@ -47,6 +47,11 @@ struct pecc_ctx {
   bool lc_ready = false;
   cudaGraphExec_t graph = nullptr;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  // whole-GPU descent of large instances
+  std::vector<int> big;
+  GridBufs gb{};
+  GridCtl *gctl = nullptr;
+  int ggrid = 0, gblock = 256;
   std::string err;
 };
 
@@ -204,6 +209,8 @@ pecc_status pecc_create(const pecc_config *cfg, void *stream, pecc_ctx **out) {
     ctx->k[q] = k;
     D.n = n;
     D.k = k;
+    D.big = n >= kGridMinN ? 1 : 0;
+    if (D.big) ctx->big.push_back(q);
     D.cap = (int32_t)std::min<double>(std::ceil(cfg->nbr_capacity * n) + 64.0, 1.0e9);
     D.off = off;
     D.rp_off = rp_off;
@@ -259,6 +266,26 @@ pecc_status pecc_create(const pecc_config *cfg, void *stream, pecc_ctx **out) {
   ALC(ctx->corder_s, int32_t, total);
   ALC(ctx->nnz, int64_t, ctx->num + 1);
   ALC(ctx->stage, char, (size_t)ctx->num * 32);
+  if (!ctx->big.empty()) {
+    int occ = 0, nmax_big = 0, kmax = 1;
+    const int ar = cfg->precision == PECC_FP64 ? 0 : 1;
+    for (int a = ar; a <= (cfg->precision == PECC_FP32_POLISH64 ? 2 : ar); ++a) {
+      int o = 0;
+      if (grid_descend_occupancy(a, ctx->gblock, &o) != cudaSuccess || o < 1)
+        return bail(fail(ctx, PECC_ERR_CUDA, "whole-GPU descent kernel does not fit an SM"));
+      occ = occ == 0 ? o : std::min(occ, o);
+    }
+    ctx->ggrid = ctx->num_sms * occ;
+    for (int q : ctx->big) { nmax_big = std::max(nmax_big, ctx->n[q]); kmax = std::max(kmax, ctx->k[q]); }
+    ALC(ctx->gb.part, double, (size_t)ctx->ggrid * 72);
+    ALC(ctx->gb.res, double, 72);
+    ALC(ctx->gb.ipart, int32_t, ctx->ggrid);
+    ALC(ctx->gb.bucket, int32_t, 2 * (size_t)(nmax_big / 4) + 4);
+    ALC(ctx->gb.hash, unsigned long long, 1);
+    ALC(p, char, (size_t)ctx->ggrid * kmax * kBasis * kBasis * 8); ctx->gb.gram = p;
+    ctx->gb.kmax = kmax;
+    ALC(ctx->gctl, GridCtl, 1);
+  }
 #undef ALC
   // instance of every circle, processing order (largest first)
   std::vector<int32_t> inst_of(total);
@@ -474,6 +501,7 @@ static pecc_status plan_launch(pecc_ctx *ctx, int arith) {
   size_t need = 0;
   for (int q = 0; q < ctx->num; ++q) {
     const InstDesc &D = ctx->desc_h[q];
+    if (D.big) continue;
     int k = D.k;
     if (arith == 2 && ctx->cfg.polish_k > 0) k = std::min(ctx->cfg.polish_k, D.k);
     need = std::max(need, descend_smem_need(arith, D.n, k, arith == 1 ? D.ncx_f : D.ncx));
@@ -485,7 +513,8 @@ static pecc_status plan_launch(pecc_ctx *ctx, int arith) {
   int blk = ctx->cfg.block_threads;
   if (blk == 0) {
     int nmax = 0;
-    for (int v : ctx->n) nmax = std::max(nmax, v);
+    for (int q = 0; q < ctx->num; ++q)
+      if (!ctx->desc_h[q].big) nmax = std::max(nmax, ctx->n[q]);
     int want = (nmax + 1) / 2;
     blk = std::min(descend_max_block(arith), std::max(64, (want + 31) / 32 * 32));
     if (many) blk = std::min(blk, 256);
@@ -557,7 +586,8 @@ pecc_status pecc_descend(pecc_ctx *ctx, int32_t *iters_dev, int32_t *status_dev)
   if (s) return s;
   if (ctx->num == 0) return PECC_OK;
   for (int q = 0; q < ctx->num; ++q)
-    if (ctx->n[q] > 65535) return fail(ctx, PECC_ERR_ARG, "pecc_descend: instance %d has more than 65535 circles", q);
+    if (ctx->n[q] > 65535 && !ctx->desc_h[q].big)
+      return fail(ctx, PECC_ERR_ARG, "pecc_descend: instance %d has more than 65535 circles", q);
   if (!ctx->lc_ready) {
     const int pr = ctx->cfg.precision;
     if (pr == PECC_FP64) {
@@ -592,6 +622,19 @@ pecc_status pecc_descend(pecc_ctx *ctx, int32_t *iters_dev, int32_t *status_dev)
     if (e != cudaSuccess) return fail(ctx, PECC_ERR_CUDA, "instantiate: %s", cudaGetErrorString(e));
   }
   CK(cudaGraphLaunch(ctx->graph, ctx->stream));
+  // large instances: one cooperative whole-GPU launch per instance and phase
+  for (int q : ctx->big) {
+    if (ctx->cfg.precision == PECC_FP64) {
+      CK(launch_grid_descend(0, dparams(ctx, 0), q, ctx->gb, ctx->gctl, ctx->ggrid, ctx->gblock, ctx->stream));
+    } else {
+      CK(launch_grid_descend(1, dparams(ctx, 1), q, ctx->gb, ctx->gctl, ctx->ggrid, ctx->gblock, ctx->stream));
+      if (ctx->cfg.precision == PECC_FP32_POLISH64) {
+        DescendParams p2 = dparams(ctx, 2);
+        p2.max_iter = ctx->cfg.polish_max_iter;
+        CK(launch_grid_descend(2, p2, q, ctx->gb, ctx->gctl, ctx->ggrid, ctx->gblock, ctx->stream));
+      }
+    }
+  }
   ctx->lists_prec = -1;  // the descent reuses the scratch the standalone lists rely on
   if (iters_dev || status_dev)
     CK(launch_outputs(ctx->out, ctx->num, iters_dev, status_dev, nullptr, nullptr, nullptr, nullptr, ctx->stream));

@@ -201,6 +201,7 @@ descend_kernel(DescendParams P) {
     if (qi >= P.num) break;
     const int q = P.order[qi];
     const InstDesc D = P.desc[q];
+    if (D.big) continue;  // descended by the whole GPU after this launch (uniform across the block)
     InstOut *O = P.out + q;
     const int n = D.n;
     const acc_t R = (acc_t)D.R;

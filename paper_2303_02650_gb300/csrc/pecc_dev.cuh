@@ -25,6 +25,7 @@ constexpr int kMaxThreads = 1024;
 // ---------------------------------------------------------------- layout ----
 struct InstDesc {
   int32_t n, k, ncx, cap;   // circles, batches, cells per side, CSR capacity per buffer
+  int32_t big, pad_;        // 1: descended by the whole GPU (pecc_grid.cu), not by one block
   int64_t off;              // first circle (positions, per-circle scratch)
   int64_t rp_off;           // 2 * (n + 1) row pointers (two CSR buffers)
   int64_t col_off;          // 2 * cap column entries (descent lists)
@@ -316,6 +317,24 @@ __device__ int cta_build_neighbors(const v2<T> *__restrict__ x, int n, const Cel
   }
   __syncthreads();
   return total;
+}
+
+// ------------------------------------------------------------- partition ---
+// Order-preserving map of a double onto uint64 (for sorting keys of either sign).
+__device__ __forceinline__ uint64_t sortable(double v) {
+  uint64_t b = (uint64_t)__double_as_longlong(v);
+  return (b & 0x8000000000000000ull) ? ~b : (b | 0x8000000000000000ull);
+}
+
+// Partition key of Sec. 4.1 with correctly rounded operations: 0 sector (a pseudo-angle,
+// strictly increasing in the polar angle on [0, 2 pi)), 1 annulus (radius), 2 fence (x).
+__device__ __forceinline__ double part_key(double x, double y, int mode) {
+  if (mode == 1) return __dsqrt_rn(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)));
+  if (mode == 2) return x;
+  double s = __dadd_rn(fabs(x), fabs(y));
+  if (s == 0.0) return 0.0;
+  double t = __ddiv_rn(x, s);
+  return (y >= 0.0) ? __dsub_rn(1.0, t) : __dadd_rn(3.0, t);
 }
 
 // ------------------------------------------------------- pair arithmetic ---

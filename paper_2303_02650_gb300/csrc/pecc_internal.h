@@ -59,6 +59,25 @@ struct DescendParams {
 
 cudaError_t launch_stamp(long long *t0, cudaStream_t s);
 
+// Whole-GPU descent of one large instance (pecc_grid.cu).
+struct GridCtl {
+  unsigned int count, gen;  // barrier arrivals, generation
+  int err, pad;             // a wait timed out
+};
+struct GridBufs {
+  double *part;             // [grid][72] block partials
+  double *res;              // [72] totals
+  int32_t *ipart;           // [grid] block totals of integer scans
+  int32_t *bucket;          // [2 (n / 4) + 2] partition buckets
+  unsigned long long *hash; // [1] pair-set digest
+  void *gram;               // [grid][kmax][kBasis^2] per-block Gram copies
+  int kmax;
+};
+constexpr int kGridMinN = 16384;  // instances this large descend on the whole GPU
+cudaError_t grid_descend_occupancy(int arith, int block, int *blocks_per_sm);
+cudaError_t launch_grid_descend(int arith, const DescendParams &p, int q, const GridBufs &g, GridCtl *c, int grid,
+                                int block, cudaStream_t s);
+
 // Launchers (pecc_descend.cu).  arith: PECC_FP64 (plain), PECC_FP32 (bulk), PECC_FP32_POLISH64 (polish).
 cudaError_t launch_descend(int arith, const DescendParams &p, int grid, int block, cudaStream_t s);
 cudaError_t descend_attributes(int arith, cudaFuncAttributes *attr);
