@@ -215,6 +215,60 @@ pecc_status pecc_phase_times(pecc_ctx *ctx, float *ms_host);
 /* The launch shape the context uses for its descent kernels. */
 pecc_status pecc_get_launch(pecc_ctx *ctx, int32_t *block_threads, int32_t *blocks_per_sm, int32_t *grid);
 
+/* ---------------------------------------------------------------------------------------------
+ * Learned warm start.  Not in the paper: a per-circle MLP (25 -> 128 -> 128 -> 128 -> 2, ReLU,
+ * BF16 weights on the tensor cores, FP32 accumulation and FP32 master weights) maps the local
+ * neighborhood of a circle to a displacement; it is trained on displacements the descent itself
+ * makes, and the plain descent stays its fallback and judge (a warm-start move of an instance is
+ * kept only if it does not raise that instance's energy).
+ * Features of circle i (FP32, correctly rounded): frame e_r = c_i/|c_i| (e_r = (1, 0) at the
+ * origin), e_t = (-e_r.y, e_r.x); the 12 nearest other centres within 4.5 (by squared distance,
+ * then index) as offsets c_j - c_i in (e_r, e_t) coordinates, zero-padded: 24 values; then
+ * min(R - |c_i| - 1, 4.5).  Row layout float[25].
+ * Parameters: float[pecc_mlp_num_params()] = W1[128][25] b1[128] W2[128][128] b2[128]
+ * W3[128][128] b3[128] W4[2][128] b4[2]; the network reads BF16 copies of the weights and rounds
+ * every GEMM input (features, activations, back-propagated gradients) to BF16.
+ * --------------------------------------------------------------------------------------------- */
+typedef struct pecc_mlp pecc_mlp;
+
+/* Number of MLP parameters (36610). */
+int32_t pecc_mlp_num_params(void);
+
+/* Create a network with He-uniform weights from Philox4x32-10 (key = seed) and zero biases; all
+ * its calls run on stream (a cudaStream_t; NULL = legacy default stream). */
+pecc_status pecc_mlp_create(uint64_t seed, void *stream, pecc_mlp **out);
+pecc_status pecc_mlp_destroy(pecc_mlp *mlp);
+
+/* Copy the FP32 parameters to / from device memory (float[num_params]); set refreshes the BF16
+ * copies and does not touch the Adam moments. */
+pecc_status pecc_mlp_get_params(pecc_mlp *mlp, float *params_dev);
+pecc_status pecc_mlp_set_params(pecc_mlp *mlp, const float *params_dev);
+
+/* Forward: feat_dev float[rows][25] -> out_dev float[rows][2] (displacement in the circle's frame). */
+pecc_status pecc_mlp_forward(pecc_mlp *mlp, const float *feat_dev, int64_t rows, float *out_dev);
+
+/* Gradient of the loss L = (1/rows) sum_r |out_r - target_r|^2 with respect to the FP32 parameters
+ * (grad_dev float[num_params]); loss_dev (float[1], may be NULL) receives L. */
+pecc_status pecc_mlp_grad(pecc_mlp *mlp, const float *feat_dev, const float *target_dev, int64_t rows,
+                          float *grad_dev, float *loss_dev);
+
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on L with learning rate lr. */
+pecc_status pecc_mlp_train_step(pecc_mlp *mlp, const float *feat_dev, const float *target_dev, int64_t rows,
+                                float lr, float *loss_dev);
+
+/* Features of every circle of an FP32 context at its current coordinates: float[sum n][25]. */
+pecc_status pecc_features(pecc_ctx *ctx, const float *unused, float *feat_dev);
+
+/* Training targets: each circle's displacement from xbefore_dev (double[2 sum n]) to the current
+ * FP32 coordinates, in the frame of its position in xbefore: float[sum n][2]. */
+pecc_status pecc_targets(pecc_ctx *ctx, const double *xbefore_dev, float *target_dev);
+
+/* Warm start of an FP32 context: rounds x (features -> network -> move each circle by the
+ * proposal, clipped to 0.25, in the global frame); a round's move of an instance is kept only if
+ * its neighbor-list energy (Eq. 5) does not rise, else the instance is put back.  accepted_dev
+ * (int32[num_instances], may be NULL) is increased by the number of rounds kept. */
+pecc_status pecc_warm_start(pecc_ctx *ctx, pecc_mlp *mlp, int32_t rounds, int32_t *accepted_dev);
+
 /* Largest instance pecc_check_feasible_noalloc accepts. */
 #define PECC_NOALLOC_MAX_N 4096
 

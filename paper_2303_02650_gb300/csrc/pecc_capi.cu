@@ -52,6 +52,10 @@ struct pecc_ctx {
   GridBufs gb{};
   GridCtl *gctl = nullptr;
   int ggrid = 0, gblock = 256;
+  // learned warm start scratch (allocated on first use)
+  float *feat = nullptr, *dout = nullptr;
+  float2 *backup = nullptr;
+  double *Eb = nullptr, *Ea = nullptr;
   std::string err;
 };
 
@@ -679,6 +683,163 @@ pecc_status pecc_get_launch(pecc_ctx *ctx, int32_t *block_threads, int32_t *bloc
   if (block_threads) *block_threads = ctx->lc[a].block;
   if (blocks_per_sm) *blocks_per_sm = ctx->lc[a].bps;
   if (grid) *grid = ctx->lc[a].grid;
+  return PECC_OK;
+}
+
+// ------------------------------------------------------------------------------ learned part ----
+struct pecc_mlp {
+  float *params = nullptr, *m = nullptr, *v = nullptr, *grad = nullptr, *part = nullptr, *lpart = nullptr;
+  __nv_bfloat16 *wb = nullptr;
+  int step = 0, sms = 1;
+  cudaStream_t stream = nullptr;
+  std::string err;
+};
+
+static pecc_status mfail(pecc_mlp *m, pecc_status s, const char *msg) {
+  if (m) m->err = msg;
+  set_global_error(msg);
+  return s;
+}
+#define MCK(call)                                                                              \
+  do {                                                                                         \
+    cudaError_t e_ = (call);                                                                   \
+    if (e_ != cudaSuccess) return mfail(mlp, PECC_ERR_CUDA, cudaGetErrorString(e_));           \
+  } while (0)
+
+int32_t pecc_mlp_num_params(void) { return mlp_num_params(); }
+
+pecc_status pecc_mlp_destroy(pecc_mlp *mlp) {
+  if (!mlp) return PECC_OK;
+  cudaStreamSynchronize(mlp->stream);
+  for (void *p : {(void *)mlp->params, (void *)mlp->m, (void *)mlp->v, (void *)mlp->grad, (void *)mlp->part,
+                  (void *)mlp->lpart, (void *)mlp->wb})
+    if (p) cudaFree(p);
+  delete mlp;
+  return PECC_OK;
+}
+
+pecc_status pecc_mlp_create(uint64_t seed, void *stream, pecc_mlp **out) {
+  if (!out) return mfail(nullptr, PECC_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  pecc_mlp *mlp = new pecc_mlp();
+  mlp->stream = (cudaStream_t)stream;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&mlp->sms, cudaDevAttrMultiProcessorCount, dev);
+  const size_t np = (size_t)mlp_num_params();
+  const int nb = mlp_train_blocks(mlp->sms);
+  cudaError_t e = cudaSuccess;
+  e = e ? e : cudaMalloc(&mlp->params, np * 4);
+  e = e ? e : cudaMalloc(&mlp->m, np * 4);
+  e = e ? e : cudaMalloc(&mlp->v, np * 4);
+  e = e ? e : cudaMalloc(&mlp->grad, np * 4);
+  e = e ? e : cudaMalloc(&mlp->part, np * 4 * (size_t)nb);
+  e = e ? e : cudaMalloc(&mlp->lpart, 4 * (size_t)nb);
+  e = e ? e : cudaMalloc(&mlp->wb, 2 * (size_t)mlp_num_bf16());
+  e = e ? e : cudaMemsetAsync(mlp->m, 0, np * 4, mlp->stream);
+  e = e ? e : cudaMemsetAsync(mlp->v, 0, np * 4, mlp->stream);
+  e = e ? e : mlp_init(mlp->params, mlp->wb, seed, mlp->stream);
+  if (e != cudaSuccess) {
+    pecc_status st = mfail(mlp, e == cudaErrorMemoryAllocation ? PECC_ERR_OOM : PECC_ERR_CUDA, cudaGetErrorString(e));
+    pecc_mlp_destroy(mlp);
+    return st;
+  }
+  *out = mlp;
+  return PECC_OK;
+}
+
+pecc_status pecc_mlp_get_params(pecc_mlp *mlp, float *params_dev) {
+  if (!mlp || !params_dev) return PECC_ERR_ARG;
+  MCK(cudaMemcpyAsync(params_dev, mlp->params, 4 * (size_t)mlp_num_params(), cudaMemcpyDeviceToDevice, mlp->stream));
+  return PECC_OK;
+}
+
+pecc_status pecc_mlp_set_params(pecc_mlp *mlp, const float *params_dev) {
+  if (!mlp || !params_dev) return PECC_ERR_ARG;
+  MCK(cudaMemcpyAsync(mlp->params, params_dev, 4 * (size_t)mlp_num_params(), cudaMemcpyDeviceToDevice, mlp->stream));
+  MCK(mlp_sync_bf16(mlp->params, mlp->wb, mlp->stream));
+  return PECC_OK;
+}
+
+pecc_status pecc_mlp_forward(pecc_mlp *mlp, const float *feat_dev, int64_t rows, float *out_dev) {
+  if (!mlp || rows < 0 || (rows > 0 && (!feat_dev || !out_dev))) return mfail(mlp, PECC_ERR_ARG, "bad arguments");
+  MCK(mlp_forward(mlp->wb, mlp->params, feat_dev, rows, out_dev, mlp->sms, mlp->stream));
+  return PECC_OK;
+}
+
+pecc_status pecc_mlp_grad(pecc_mlp *mlp, const float *feat_dev, const float *target_dev, int64_t rows,
+                          float *grad_dev, float *loss_dev) {
+  if (!mlp || rows <= 0 || !feat_dev || !target_dev || !grad_dev) return mfail(mlp, PECC_ERR_ARG, "bad arguments");
+  MCK(mlp_grad(mlp->wb, mlp->params, feat_dev, target_dev, rows, mlp->part, mlp->lpart, grad_dev, loss_dev,
+               mlp->sms, mlp->stream));
+  return PECC_OK;
+}
+
+pecc_status pecc_mlp_train_step(pecc_mlp *mlp, const float *feat_dev, const float *target_dev, int64_t rows,
+                                float lr, float *loss_dev) {
+  if (!mlp || rows <= 0 || !feat_dev || !target_dev || !(lr > 0.f)) return mfail(mlp, PECC_ERR_ARG, "bad arguments");
+  MCK(mlp_grad(mlp->wb, mlp->params, feat_dev, target_dev, rows, mlp->part, mlp->lpart, mlp->grad, loss_dev,
+               mlp->sms, mlp->stream));
+  ++mlp->step;
+  MCK(mlp_adam(mlp->params, mlp->m, mlp->v, mlp->grad, mlp->wb, lr, mlp->step, mlp->stream));
+  return PECC_OK;
+}
+
+static pecc_status need_fp32(pecc_ctx *ctx) {
+  pecc_status s = need_radius(ctx);
+  if (s) return s;
+  if (!ctx->x32) return fail(ctx, PECC_ERR_ARG, "the learned warm start needs an FP32 context");
+  return PECC_OK;
+}
+
+static pecc_status mlp_scratch(pecc_ctx *ctx) {
+  if (ctx->feat) return PECC_OK;
+  const size_t N = (size_t)std::max<int64_t>(ctx->total, 1), I = (size_t)std::max(ctx->num, 1);
+  float *f = nullptr, *d = nullptr;
+  float2 *b = nullptr;
+  double *eb = nullptr, *ea = nullptr;
+  if (cudaMalloc(&f, N * 25 * 4) || cudaMalloc(&d, N * 2 * 4) || cudaMalloc(&b, N * sizeof(float2)) ||
+      cudaMalloc(&eb, I * 8) || cudaMalloc(&ea, I * 8))
+    return fail(ctx, PECC_ERR_OOM, "warm-start scratch");
+  for (void *p : {(void *)f, (void *)d, (void *)b, (void *)eb, (void *)ea}) ctx->allocs.push_back(p);
+  ctx->feat = f; ctx->dout = d; ctx->backup = b; ctx->Eb = eb; ctx->Ea = ea;
+  return PECC_OK;
+}
+
+pecc_status pecc_features(pecc_ctx *ctx, const float *unused, float *feat_dev) {
+  (void)unused;
+  pecc_status s = need_fp32(ctx);
+  if (s) return s;
+  if (ctx->total > 0 && !feat_dev) return fail(ctx, PECC_ERR_ARG, "feat_dev is NULL");
+  CK(mlp_features(sparams(ctx), feat_dev, ctx->stream));
+  return PECC_OK;
+}
+
+pecc_status pecc_targets(pecc_ctx *ctx, const double *xbefore_dev, float *target_dev) {
+  pecc_status s = need_fp32(ctx);
+  if (s) return s;
+  if (ctx->total > 0 && (!xbefore_dev || !target_dev)) return fail(ctx, PECC_ERR_ARG, "NULL pointer");
+  CK(mlp_targets(sparams(ctx), xbefore_dev, target_dev, ctx->stream));
+  return PECC_OK;
+}
+
+pecc_status pecc_warm_start(pecc_ctx *ctx, pecc_mlp *mlp, int32_t rounds, int32_t *accepted_dev) {
+  pecc_status s = need_fp32(ctx);
+  if (s) return s;
+  if (!mlp || rounds < 0) return fail(ctx, PECC_ERR_ARG, "bad arguments");
+  if ((s = mlp_scratch(ctx))) return s;
+  StandaloneParams sp = sparams(ctx);
+  for (int r = 0; r < rounds; ++r) {
+    CK(launch_build(sp, 1, 1, nullptr, nullptr, ctx->block_build, ctx->stream));
+    CK(launch_energy_grad(sp, 1, ctx->Eb, ctx->g, ctx->ecirc, ctx->stream));
+    CK(mlp_features(sp, ctx->feat, ctx->stream));
+    CK(mlp_forward(mlp->wb, mlp->params, ctx->feat, ctx->total, ctx->dout, mlp->sms, ctx->stream));
+    CK(mlp_apply(sp, ctx->dout, ctx->backup, ctx->stream));
+    CK(launch_build(sp, 1, 1, nullptr, nullptr, ctx->block_build, ctx->stream));
+    CK(launch_energy_grad(sp, 1, ctx->Ea, ctx->g, ctx->ecirc, ctx->stream));
+    CK(mlp_revert(sp, ctx->backup, ctx->Eb, ctx->Ea, accepted_dev, ctx->stream));
+  }
+  ctx->lists_prec = -1;
   return PECC_OK;
 }
 

@@ -225,16 +225,17 @@ __device__ __forceinline__ unsigned long long mix32(uint32_t x) {
 // still deterministic).  Returns the number of entries (block-uniform); > cap means
 // overflow and the rows are then not written.  hash (shared, may be null) receives an
 // order-independent 64-bit digest of the pair set, used to tell Gamma' from Gamma.
-template <typename T, typename IdxT>
-__device__ int cta_build_neighbors(const v2<T> *__restrict__ x, int n, const CellGrid &G, T lc2,
-                                   uint32_t *ckey, int32_t *corder, int32_t *cells, v2<T> *xs, int32_t *rp,
-                                   IdxT *col, int cap, int32_t *sh, unsigned long long *hash, bool sort_rows) {
+// Cell binning and stable key sort of one instance (the first half of a list build): ckey[i]
+// = cell of circle i, corder = circles sorted by (cell, index), cells[0..ncell] = cell starts
+// (cells[ncell + 1 ..] is scratch), xs[q] = coordinates of corder[q].
+template <typename T>
+__device__ void cta_cell_sort(const v2<T> *__restrict__ x, int n, const CellGrid &G, uint32_t *ckey,
+                              int32_t *corder, int32_t *cells, v2<T> *xs, int32_t *sh) {
   const int T_ = blockDim.x, t = threadIdx.x;
-  const int nc = G.nc, ncell = nc * nc;
+  const int ncell = G.nc * G.nc;
   int32_t *cstart = cells;              // ncell + 1
   int32_t *cfill = cells + ncell + 1;   // ncell
   for (int c = t; c <= ncell; c += T_) cstart[c] = 0;
-  if (t == 0 && hash) *hash = 0ull;
   __syncthreads();
   for (int i = t; i < n; i += T_) {
     uint32_t key = grid_key<T>(x[i], G);
@@ -261,6 +262,18 @@ __device__ int cta_build_neighbors(const v2<T> *__restrict__ x, int n, const Cel
   }
   __syncthreads();
   for (int q = t; q < n; q += T_) xs[q] = x[corder[q]];
+  __syncthreads();
+}
+
+template <typename T, typename IdxT>
+__device__ int cta_build_neighbors(const v2<T> *__restrict__ x, int n, const CellGrid &G, T lc2,
+                                   uint32_t *ckey, int32_t *corder, int32_t *cells, v2<T> *xs, int32_t *rp,
+                                   IdxT *col, int cap, int32_t *sh, unsigned long long *hash, bool sort_rows) {
+  const int T_ = blockDim.x, t = threadIdx.x;
+  const int nc = G.nc;
+  int32_t *cstart = cells;
+  if (t == 0 && hash) *hash = 0ull;
+  cta_cell_sort<T>(x, n, G, ckey, corder, cells, xs, sh);
   if (t == 0) rp[0] = 0;
   __syncthreads();
   // count: circles visited in cell order, candidates as three contiguous row ranges

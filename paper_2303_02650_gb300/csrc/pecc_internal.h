@@ -4,6 +4,9 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <cuda_bf16.h>
+
 #include "pecc_dev.cuh"
 
 namespace pecc {
@@ -125,5 +128,23 @@ cudaError_t launch_nnz(const StandaloneParams &p, int64_t *nnz, cudaStream_t s);
 cudaError_t launch_stats(const InstOut *out, int num, int32_t *stats, cudaStream_t s);
 cudaError_t launch_outputs(const InstOut *out, int num, int32_t *iters, int32_t *status, double *E,
                            int32_t *builds, int32_t *changes, int32_t *trials, cudaStream_t s);
+
+// Learned warm start (pecc_mlp.cu).
+int mlp_num_params();
+int mlp_num_bf16();
+int mlp_train_blocks(int sms);
+cudaError_t mlp_init(float *params, __nv_bfloat16 *wb, uint64_t seed, cudaStream_t s);
+cudaError_t mlp_sync_bf16(const float *params, __nv_bfloat16 *wb, cudaStream_t s);
+cudaError_t mlp_features(const StandaloneParams &p, float *feat, cudaStream_t s);
+cudaError_t mlp_targets(const StandaloneParams &p, const double *xbefore, float *target, cudaStream_t s);
+cudaError_t mlp_forward(const __nv_bfloat16 *wb, const float *params, const float *feat, int64_t rows, float *out,
+                        int sms, cudaStream_t s);
+cudaError_t mlp_grad(const __nv_bfloat16 *wb, const float *params, const float *feat, const float *target,
+                     int64_t rows, float *part, float *lpart, float *grad, float *loss, int sms, cudaStream_t s);
+cudaError_t mlp_adam(float *params, float *m, float *v, const float *grad, __nv_bfloat16 *wb, float lr, int step,
+                     cudaStream_t s);
+cudaError_t mlp_apply(const StandaloneParams &p, const float *dout, float2 *backup, cudaStream_t s);
+cudaError_t mlp_revert(const StandaloneParams &p, const float2 *backup, const double *Eb, const double *Ea,
+                       int32_t *accepted, cudaStream_t s);
 
 }  // namespace pecc

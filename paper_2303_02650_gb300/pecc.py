@@ -44,7 +44,9 @@ _EXPORTS = ["pecc_config_default", "pecc_create", "pecc_destroy", "pecc_set_radi
             "pecc_neighbor_count", "pecc_export_neighbors", "pecc_export_cells", "pecc_energy_grad",
             "pecc_energy_grad_ex", "pecc_descend", "pecc_get_energy", "pecc_check_feasible", "pecc_solve_host",
             "pecc_get_counters", "pecc_get_launch", "pecc_last_error", "pecc_get_stats", "pecc_phase_times",
-            "pecc_check_feasible_noalloc"]
+            "pecc_check_feasible_noalloc", "pecc_mlp_num_params", "pecc_mlp_create", "pecc_mlp_destroy",
+            "pecc_mlp_get_params", "pecc_mlp_set_params", "pecc_mlp_forward", "pecc_mlp_grad", "pecc_mlp_train_step",
+            "pecc_features", "pecc_targets", "pecc_warm_start"]
 NOALLOC_MAX_N = 4096
 
 
@@ -90,6 +92,17 @@ def load(build_if_missing: bool = True):
         "pecc_get_stats": (st, [vp, vp]),
         "pecc_phase_times": (st, [vp, C.POINTER(C.c_float)]),
         "pecc_check_feasible_noalloc": (st, [vp, C.c_int32, C.c_double, C.c_double, C.c_double, vp, vp, vp]),
+        "pecc_mlp_num_params": (C.c_int32, []),
+        "pecc_mlp_create": (st, [C.c_uint64, vp, C.POINTER(vp)]),
+        "pecc_mlp_destroy": (st, [vp]),
+        "pecc_mlp_get_params": (st, [vp, vp]),
+        "pecc_mlp_set_params": (st, [vp, vp]),
+        "pecc_mlp_forward": (st, [vp, vp, C.c_int64, vp]),
+        "pecc_mlp_grad": (st, [vp, vp, vp, C.c_int64, vp, vp]),
+        "pecc_mlp_train_step": (st, [vp, vp, vp, C.c_int64, C.c_float, vp]),
+        "pecc_features": (st, [vp, vp, vp]),
+        "pecc_targets": (st, [vp, vp, vp]),
+        "pecc_warm_start": (st, [vp, vp, C.c_int32, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -129,6 +142,64 @@ def check_feasible_noalloc(xy, R, l_cut=2.5, tol=1e-9, stream=None):
     if rc != 0:
         raise PeccError(f"pecc_check_feasible_noalloc: {ERRORS.get(rc, rc)}: {L.pecc_last_error(None).decode()}")
     return feas, mo
+
+
+class MLP:
+    """The learned warm start's network (pecc_mlp_*): FP32 master parameters, BF16 tensor-core copies."""
+
+    def __init__(self, seed=0, stream=None):
+        self._L = load()
+        stream = stream or torch.cuda.current_stream()
+        self.stream = stream
+        h = C.c_void_p()
+        rc = self._L.pecc_mlp_create(C.c_uint64(seed), C.c_void_p(stream.cuda_stream), C.byref(h))
+        if rc != 0:
+            raise PeccError(f"pecc_mlp_create: {ERRORS.get(rc, rc)}: {self._L.pecc_last_error(None).decode()}")
+        self.h = h
+        self.num_params = int(self._L.pecc_mlp_num_params())
+
+    def _check(self, rc, what):
+        if rc != 0:
+            raise PeccError(f"{what}: {ERRORS.get(rc, rc)}: {self._L.pecc_last_error(None).decode()}")
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._L.pecc_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get_params(self):
+        p = torch.empty(self.num_params, dtype=torch.float32, device="cuda")
+        self._check(self._L.pecc_mlp_get_params(self.h, _ptr(p)), "pecc_mlp_get_params")
+        return p
+
+    def set_params(self, p):
+        p = torch.as_tensor(p, dtype=torch.float32, device="cuda").contiguous()
+        self._check(self._L.pecc_mlp_set_params(self.h, _ptr(p)), "pecc_mlp_set_params")
+
+    def forward(self, feat):
+        feat = feat.contiguous()
+        out = torch.empty((feat.shape[0], 2), dtype=torch.float32, device=feat.device)
+        self._check(self._L.pecc_mlp_forward(self.h, _ptr(feat), feat.shape[0], _ptr(out)), "pecc_mlp_forward")
+        return out
+
+    def grad(self, feat, target):
+        g = torch.empty(self.num_params, dtype=torch.float32, device=feat.device)
+        loss = torch.empty(1, dtype=torch.float32, device=feat.device)
+        self._check(self._L.pecc_mlp_grad(self.h, _ptr(feat.contiguous()), _ptr(target.contiguous()), feat.shape[0],
+                                          _ptr(g), _ptr(loss)), "pecc_mlp_grad")
+        return g, loss
+
+    def train_step(self, feat, target, lr):
+        loss = torch.empty(1, dtype=torch.float32, device=feat.device)
+        self._check(self._L.pecc_mlp_train_step(self.h, _ptr(feat), _ptr(target), feat.shape[0], C.c_float(lr),
+                                                _ptr(loss)), "pecc_mlp_train_step")
+        return loss
 
 
 class Context:
@@ -273,6 +344,21 @@ class Context:
         self._check(self._L.pecc_check_feasible(self.h, C.c_double(tol), _ptr(feas), _ptr(mo)),
                     "pecc_check_feasible")
         return feas, mo
+
+    def features(self):
+        f = torch.empty((self.total, 25), dtype=torch.float32, device=self.dev)
+        self._check(self._L.pecc_features(self.h, None, _ptr(f)), "pecc_features")
+        return f
+
+    def targets(self, xbefore):
+        t = torch.empty((self.total, 2), dtype=torch.float32, device=self.dev)
+        self._check(self._L.pecc_targets(self.h, _ptr(xbefore.contiguous()), _ptr(t)), "pecc_targets")
+        return t
+
+    def warm_start(self, mlp, rounds=1):
+        acc = torch.zeros(self.num, dtype=torch.int32, device=self.dev)
+        self._check(self._L.pecc_warm_start(self.h, mlp.h, int(rounds), _ptr(acc)), "pecc_warm_start")
+        return acc
 
     def launch_shape(self):
         b, s, g = C.c_int32(), C.c_int32(), C.c_int32()
