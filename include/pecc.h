@@ -212,6 +212,16 @@ pecc_status pecc_get_stats(pecc_ctx *ctx, int32_t *stats_dev);
  * Synchronises on the last event. */
 pecc_status pecc_phase_times(pecc_ctx *ctx, float *ms_host);
 
+/* Autotuner of the descent's launch shape: for threads per instance block in {128, 256, 512} and
+ * a target of {1, 2, 4} blocks per SM (which sets the shared-memory share of the working set), it
+ * draws a layout from seed and times `sweeps` sweeps of the context's own instances, and keeps the
+ * shape with the most circle-sweeps per second for the following pecc_descend calls (also after
+ * pecc_set_radius, which only re-sizes the shared-memory share).  The FP64 polish of
+ * PECC_FP32_POLISH64 runs with min(block, 256) threads and the same target.  The caller's
+ * coordinates are restored.  Synchronises; allocates a temporary copy of the coordinates.
+ * block_out / bps_out (host, may be NULL) receive the chosen threads per block and target. */
+pecc_status pecc_autotune(pecc_ctx *ctx, int32_t sweeps, uint64_t seed, int32_t *block_out, int32_t *bps_out);
+
 /* The launch shape the context uses for its descent kernels. */
 pecc_status pecc_get_launch(pecc_ctx *ctx, int32_t *block_threads, int32_t *blocks_per_sm, int32_t *grid);
 

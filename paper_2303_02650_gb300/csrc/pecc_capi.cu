@@ -45,6 +45,8 @@ struct pecc_ctx {
   int block = 0, bps = 0, grid = 0, block_build = 256;
   struct Launch { int block = 0, bps = 0, grid = 0; size_t smem = 0; } lc[3];  // per arithmetic
   bool lc_ready = false;
+  bool tuned = false;  // launch shapes chosen by pecc_autotune
+  int tuned_block = 0, tuned_bps = 0;
   cudaGraphExec_t graph = nullptr;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   // whole-GPU descent of large instances
@@ -493,10 +495,12 @@ pecc_status pecc_energy_grad(pecc_ctx *ctx, double *E_dev, void *grad_dev) {
   return pecc_energy_grad_ex(ctx, ctx->cfg.precision == PECC_FP64 ? PECC_FP64 : PECC_FP32, E_dev, grad_dev);
 }
 
-// Launch shape of one descent arithmetic: block size from the config (or about two circles per
-// thread), dynamic shared memory for the largest working set capped so that two blocks share
-// an SM when instances outnumber SMs, blocks per SM from the occupancy calculator.
-static pecc_status plan_launch(pecc_ctx *ctx, int arith) {
+// Launch shape of one descent arithmetic.  block / bps_target 0 = the default: about two circles
+// per thread (at most 256 threads when instances outnumber SMs) and as many blocks per SM as fit.
+// Dynamic shared memory: the largest working set, capped so that bps_target blocks share an SM
+// (the working set spills to global memory past the cap); blocks per SM from the occupancy
+// calculator.
+static pecc_status plan_launch(pecc_ctx *ctx, int arith, int block = 0, int bps_target = 0) {
   pecc_ctx::Launch &L = ctx->lc[arith];
   int dev = ctx->device, optin = 0, per_sm = 0;
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
@@ -511,10 +515,12 @@ static pecc_status plan_launch(pecc_ctx *ctx, int arith) {
     need = std::max(need, descend_smem_need(arith, D.n, k, arith == 1 ? D.ncx_f : D.ncx));
   }
   const bool many = ctx->num > ctx->num_sms;
-  size_t cap = many ? (size_t)per_sm / 2 - stat : (size_t)optin - stat;
+  if (bps_target <= 0) bps_target = many ? 2 : 1;
+  size_t cap = (size_t)per_sm / bps_target;
+  cap = (cap > stat ? cap - stat : 0);
   cap = std::min(cap, (size_t)optin - stat);
   L.smem = std::min(need, cap) & ~size_t(15);
-  int blk = ctx->cfg.block_threads;
+  int blk = block > 0 ? block : ctx->cfg.block_threads;
   if (blk == 0) {
     int nmax = 0;
     for (int q = 0; q < ctx->num; ++q)
@@ -594,11 +600,12 @@ pecc_status pecc_descend(pecc_ctx *ctx, int32_t *iters_dev, int32_t *status_dev)
       return fail(ctx, PECC_ERR_ARG, "pecc_descend: instance %d has more than 65535 circles", q);
   if (!ctx->lc_ready) {
     const int pr = ctx->cfg.precision;
+    const int tb = ctx->tuned ? ctx->tuned_block : 0, tt = ctx->tuned ? ctx->tuned_bps : 0;
     if (pr == PECC_FP64) {
-      if ((s = plan_launch(ctx, 0))) return s;
+      if ((s = plan_launch(ctx, 0, tb, tt))) return s;
     } else {
-      if ((s = plan_launch(ctx, 1))) return s;
-      if (pr == PECC_FP32_POLISH64 && (s = plan_launch(ctx, 2))) return s;
+      if ((s = plan_launch(ctx, 1, tb, tt))) return s;
+      if (pr == PECC_FP32_POLISH64 && (s = plan_launch(ctx, 2, tb > 0 ? std::min(tb, 256) : 0, tt))) return s;
     }
     ctx->lc_ready = true;
   }
@@ -654,6 +661,81 @@ pecc_status pecc_get_energy(pecc_ctx *ctx, double *E_dev) {
 pecc_status pecc_get_counters(pecc_ctx *ctx, int32_t *builds_dev, int32_t *changes_dev, int32_t *trials_dev) {
   if (!ctx) return PECC_ERR_ARG;
   CK(launch_outputs(ctx->out, ctx->num, nullptr, nullptr, nullptr, builds_dev, changes_dev, trials_dev, ctx->stream));
+  return PECC_OK;
+}
+
+pecc_status pecc_autotune(pecc_ctx *ctx, int32_t sweeps, uint64_t seed, int32_t *block_out, int32_t *bps_out) {
+  pecc_status s = need_radius(ctx);
+  if (s) return s;
+  if (sweeps < 1) return fail(ctx, PECC_ERR_ARG, "sweeps must be >= 1");
+  if (ctx->num == 0) return PECC_OK;
+  const int arith = ctx->cfg.precision == PECC_FP64 ? 0 : 1;
+  // keep the caller's coordinates (both copies, bit for bit) and restore them afterwards
+  const size_t b64 = sizeof(double2) * (size_t)ctx->total, b32 = ctx->x32 ? sizeof(float2) * (size_t)ctx->total : 0;
+  char *saved = nullptr;
+  CK(cudaMalloc(&saved, std::max<size_t>(b64 + b32, 16)));
+  CK(cudaMemcpyAsync(saved, ctx->x64, b64, cudaMemcpyDeviceToDevice, ctx->stream));
+  if (b32) CK(cudaMemcpyAsync(saved + b64, ctx->x32, b32, cudaMemcpyDeviceToDevice, ctx->stream));
+  const pecc_config keep = ctx->cfg;
+  ctx->cfg.max_iter = sweeps;
+  ctx->cfg.stall_window = 0;
+  ctx->cfg.precision = arith == 1 ? PECC_FP32 : PECC_FP64;
+  const int blocks[3] = {128, 256, 512};
+  const int targets[3] = {1, 2, 4};
+  double best = -1.0;
+  int best_b = 0, best_t = 0;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  std::vector<int32_t> st((size_t)ctx->num * 10);
+  pecc_status err = PECC_OK;
+  for (int bi = 0; bi < 3 && !err; ++bi) {
+    for (int ti = 0; ti < 3 && !err; ++ti) {
+      if (blocks[bi] > descend_max_block(arith)) continue;
+      if ((err = plan_launch(ctx, arith, blocks[bi], targets[ti]))) break;
+      if (ctx->lc[arith].bps < targets[ti]) continue;  // that many blocks do not fit an SM
+      ctx->lc_ready = true;
+      if (ctx->graph) { cudaGraphExecDestroy(ctx->graph); ctx->graph = nullptr; }
+      if ((err = pecc_init_random(ctx, seed))) break;
+      cudaEventRecord(e0, ctx->stream);
+      if ((err = pecc_descend(ctx, nullptr, nullptr))) break;
+      cudaEventRecord(e1, ctx->stream);
+      if (cudaEventSynchronize(e1) != cudaSuccess) { err = fail(ctx, PECC_ERR_CUDA, "autotune sync"); break; }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      // circle-sweeps per second: sum over instances of n x sweeps done
+      int32_t *dstats = nullptr;
+      if (cudaMalloc(&dstats, sizeof(int32_t) * 10 * ctx->num) != cudaSuccess) { err = fail(ctx, PECC_ERR_OOM, "autotune"); break; }
+      cudaError_t ce = launch_stats(ctx->out, ctx->num, dstats, ctx->stream);
+      if (ce == cudaSuccess)
+        ce = cudaMemcpyAsync(st.data(), dstats, sizeof(int32_t) * 10 * ctx->num, cudaMemcpyDeviceToHost, ctx->stream);
+      if (ce == cudaSuccess) ce = cudaStreamSynchronize(ctx->stream);
+      cudaFree(dstats);
+      if (ce != cudaSuccess) { err = fail(ctx, PECC_ERR_CUDA, "autotune stats: %s", cudaGetErrorString(ce)); break; }
+      double work = 0.0;
+      for (int q = 0; q < ctx->num; ++q) work += (double)ctx->n[q] * st[(size_t)q * 10 + 0];
+      const double rate = work / std::max(1e-3, (double)ms);
+      if (rate > best) { best = rate; best_b = blocks[bi]; best_t = targets[ti]; }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ctx->cfg = keep;
+  if (ctx->graph) { cudaGraphExecDestroy(ctx->graph); ctx->graph = nullptr; }
+  ctx->lc_ready = false;  // a failed or empty search leaves the default shapes to the next descent
+  if (!err && best_b > 0) {
+    ctx->tuned = true;
+    ctx->tuned_block = best_b;
+    ctx->tuned_bps = best_t;
+  }
+  cudaError_t ce = cudaMemcpyAsync(ctx->x64, saved, b64, cudaMemcpyDeviceToDevice, ctx->stream);
+  if (ce == cudaSuccess && b32) ce = cudaMemcpyAsync(ctx->x32, saved + b64, b32, cudaMemcpyDeviceToDevice, ctx->stream);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(ctx->stream);
+  cudaFree(saved);
+  if (err) return err;
+  if (ce != cudaSuccess) return fail(ctx, PECC_ERR_CUDA, "autotune restore: %s", cudaGetErrorString(ce));
+  if (block_out) *block_out = best_b;
+  if (bps_out) *bps_out = best_t;
   return PECC_OK;
 }
 

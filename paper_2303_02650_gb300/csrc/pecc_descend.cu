@@ -650,7 +650,10 @@ descend_kernel(DescendParams P) {
             Sv[(int64_t)stg * n + pos] = s_;
             Yv[(int64_t)stg * n + pos] = y_;
           }
-          if (tid == 0) ring[2 + kMaxSlots] = 1;
+          // every thread raises the flag: with one batch the next read comes without a barrier in
+          // between, and each thread then reads its own store (thread 0 clears the flag only after
+          // the next step's reduction barriers)
+          ring[2 + kMaxSlots] = 1;
           if (k == 1) { fresh = true; E = Et; }
         }
       }

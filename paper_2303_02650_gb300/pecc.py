@@ -46,7 +46,7 @@ _EXPORTS = ["pecc_config_default", "pecc_create", "pecc_destroy", "pecc_set_radi
             "pecc_get_counters", "pecc_get_launch", "pecc_last_error", "pecc_get_stats", "pecc_phase_times",
             "pecc_check_feasible_noalloc", "pecc_mlp_num_params", "pecc_mlp_create", "pecc_mlp_destroy",
             "pecc_mlp_get_params", "pecc_mlp_set_params", "pecc_mlp_forward", "pecc_mlp_grad", "pecc_mlp_train_step",
-            "pecc_features", "pecc_targets", "pecc_warm_start"]
+            "pecc_features", "pecc_targets", "pecc_warm_start", "pecc_autotune"]
 NOALLOC_MAX_N = 4096
 
 
@@ -103,6 +103,7 @@ def load(build_if_missing: bool = True):
         "pecc_features": (st, [vp, vp, vp]),
         "pecc_targets": (st, [vp, vp, vp]),
         "pecc_warm_start": (st, [vp, vp, C.c_int32, vp]),
+        "pecc_autotune": (st, [vp, C.c_int32, C.c_uint64, i32p, i32p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -359,6 +360,13 @@ class Context:
         acc = torch.zeros(self.num, dtype=torch.int32, device=self.dev)
         self._check(self._L.pecc_warm_start(self.h, mlp.h, int(rounds), _ptr(acc)), "pecc_warm_start")
         return acc
+
+    def autotune(self, sweeps=40, seed=99):
+        """pecc_autotune: pick threads per block and blocks per SM by timing short descents."""
+        b, s = C.c_int32(), C.c_int32()
+        self._check(self._L.pecc_autotune(self.h, int(sweeps), C.c_uint64(seed), C.byref(b), C.byref(s)),
+                    "pecc_autotune")
+        return b.value, s.value
 
     def launch_shape(self):
         b, s, g = C.c_int32(), C.c_int32(), C.c_int32()

@@ -280,6 +280,57 @@ def test_descend_statistics_vs_oracle(orc, prec):
     assert abs(int(out["feasible"].sum()) - int(ref["feasible"].sum())) <= 5
 
 
+def _check_outcomes(orc, out, n, R):
+    """Per instance: the max overlap equals the oracle's on the GPU's own final layout, the energy
+    the GPU reports is the oracle's energy of that layout (to 1e-2 relative: an instance left
+    unpolished reports its binary32 energy, whose overlap depths 2 - l lose up to about 2^-22 / d
+    of their value to cancellation), and converged means feasible."""
+    for q, x in enumerate(split(out["xy"], n)):
+        mo = orc.max_overlap(x, float(R[q]))[0]
+        assert out["max_overlap"][q] == mo, q
+        e_ref = orc.energy_allpairs(x, float(R[q]))
+        assert abs(out["E"][q] - e_ref) <= 1e-2 * e_ref + 1e-18, q
+        if out["status"][q] == 0:
+            assert out["E"][q] <= 1e-20 and mo <= 1e-9, q
+
+
+@pytest.mark.parametrize("block", [128, 512])
+def test_descend_launch_shapes(orc, block):
+    """FP32 descent and FP64 polish at 128 and 512 threads per block (the polish at min(block,
+    256)), over instances of one batch (n < 300, and every polish) and of several: the same
+    outcomes as the oracle's (22 of these 24 reach zero energy in the oracle)."""
+    torch, pecc = need_gpu()
+    n = np.array([120, 200, 299, 300, 420, 640] * 4, dtype=np.int32)
+    R = _radii(n, 0.80)
+    out = _solve(pecc, torch, n, R, 41, precision=2, block_threads=block)
+    _check_outcomes(orc, out, n, R)
+    _, ref = orc.solve_batch(n, R, 41, nthreads=8)
+    assert out["feasible"].sum() >= len(n) - 6
+    assert abs(int(out["feasible"].sum()) - int(ref["feasible"].sum())) <= 5
+
+
+def test_autotune_restores_coordinates_and_descends(orc):
+    """pecc_autotune times short descents at every launch shape, then hands the caller back its
+    coordinates bit for bit; the descent that follows runs at the chosen shape with the same
+    outcomes as the oracle's."""
+    torch, pecc = need_gpu()
+    n = np.array([120, 200, 299, 300, 420, 640] * 4, dtype=np.int32)
+    R = _radii(n, 0.80)
+    with _ctx(pecc, n, R, precision=2) as c:
+        c.init_random(41)
+        x0 = c.get_positions().cpu().numpy()
+        b, t = c.autotune(sweeps=5, seed=9)
+        assert b in (128, 256, 512) and t in (1, 2, 4)
+        assert np.array_equal(c.get_positions().cpu().numpy(), x0)
+        iters, status = c.descend()
+        assert c.launch_shape()[0] == b
+        feas, mo = c.check_feasible()
+        out = dict(status=status.cpu().numpy(), feasible=feas.cpu().numpy(), max_overlap=mo.cpu().numpy(),
+                   xy=c.get_positions().cpu().numpy(), E=c.get_energy().cpu().numpy())
+    _check_outcomes(orc, out, n, R)
+    assert out["feasible"].sum() >= len(n) - 6
+
+
 def test_descend_infeasible_density_small(orc):
     """n = 50 at u = 0.80 is denser than any packing of 50 circles: no descent reaches zero
     energy, on the GPU or in the oracle, and every run ends by stalling or at max_iter."""
