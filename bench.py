@@ -18,6 +18,7 @@ Prints one JSON line.  --impl reference times the FP64 CPU oracle on the same wo
 from __future__ import annotations
 
 import argparse
+import datetime
 import json
 import os
 import subprocess
@@ -65,49 +66,73 @@ def peaks():
 
 
 class Clocks:
-    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+    """nvidia-smi samples of SM clock and throttle reasons.  The sampler starts before the warm-up
+    (its start-up is then off the clock) and only samples stamped inside [mark_start, mark_end]
+    enter the summary."""
 
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, index: int):
         self.index = index
         self.p = None
+        self.lines = []
+        self.t0 = self.t1 = None
 
     def __enter__(self):
+        import threading
+
         try:
             self.p = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
                                        "--format=csv,noheader,nounits", "-lms", "200"],
                                       stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.p = None
+            return self
+
+        def pump(f, out):
+            for line in f:
+                out.append(line)
+
+        self.th = threading.Thread(target=pump, args=(self.p.stdout, self.lines), daemon=True)
+        self.th.start()
         return self
+
+    def mark_start(self):
+        self.t0 = datetime.datetime.now()
+
+    def mark_end(self):
+        self.t1 = datetime.datetime.now()
 
     def __exit__(self, *a):
         if self.p is not None:
             self.p.terminate()
             try:
-                self.out, _ = self.p.communicate(timeout=5)
+                self.p.wait(timeout=5)
             except Exception:
                 self.p.kill()
-                self.out = ""
-        else:
-            self.out = ""
+            self.th.join(timeout=5)
 
     def summary(self):
         sm, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in (self.out or "").splitlines():
+        for line in list(self.lines):
             f = [t.strip() for t in line.split(",")]
-            if len(f) < 9:
+            if len(f) < 10:
                 continue
             try:
-                sm.append(float(f[1]))
-                mx = float(f[2])
+                ts = datetime.datetime.strptime(f[0], "%Y/%m/%d %H:%M:%S.%f")
+                if self.t0 and self.t1 and not (self.t0 <= ts <= self.t1):
+                    continue
+            except ValueError:
+                pass
+            try:
+                sm.append(float(f[2]))
+                mx = float(f[3])
             except ValueError:
                 continue
-            for nm, v in zip(names, f[5:9]):
+            for nm, v in zip(names, f[6:10]):
                 if v.lower().startswith("active"):
                     reasons.add(nm)
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
@@ -140,10 +165,14 @@ def run_ours(args, rank, world, local):
         import torch.distributed as dist
 
         dist.init_process_group("nccl")
-    ctx = pecc.Context(n, precision=prec)
+    shape = {}
+    if args.launch:
+        b, t = (int(v) for v in args.launch.lower().split("x"))
+        shape = dict(block_threads=b, blocks_per_sm=t)
+    ctx = pecc.Context(n, precision=prec, **shape)
     ctx.set_radius(R)
     tuned = None
-    if not args.no_autotune and n.size > 1:
+    if not args.no_autotune and not shape and n.size > 1:
         tuned = ctx.autotune(sweeps=40, seed=args.seed + 31337)  # launch shape (untimed, before warm-up)
     kvec = np.array([1 if v < 300 else (3 if v < 500 else 5) for v in n], dtype=np.float64)
     kvec = np.minimum(kvec, np.maximum(n, 1))
@@ -190,21 +219,23 @@ def run_ours(args, rank, world, local):
         st_all.append(st[:, 1])
         tr_all.append(st[:, 4])
 
-    for w in range(args.warmup):
-        timed_step(10_000 + w, [torch.cuda.Event(enable_timing=True) for _ in range(4)], False)
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
     with Clocks(local) as clk:
+        for w in range(args.warmup):
+            timed_step(10_000 + w, [torch.cuda.Event(enable_timing=True) for _ in range(4)], False)
         torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        clk.mark_start()
         e0.record()
         for s in range(args.steps):
             timed_step(s, evs[s], True)
         e1.record()
         torch.cuda.synchronize()
+        clk.mark_end()
     for ev in evs:
         split_ms.append([ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]), ev[2].elapsed_time(ev[3])])
     split_ms = np.array(split_ms)
@@ -409,11 +440,13 @@ def run_learned(args, rank, world, local):
     train_s = time.time() - t0
     test = synth.batch_manifest(1024, seed=10**6 + 7)
     res = []
-    for s in range(args.warmup):
-        learned.gain(mlp, (test[0][:64], test[1][:64]), seed=900 + s, precision=pecc.FP32_POLISH64)
     with Clocks(local) as clk:
+        for s in range(args.warmup):
+            learned.gain(mlp, (test[0][:64], test[1][:64]), seed=900 + s, precision=pecc.FP32_POLISH64)
+        clk.mark_start()
         for s in range(args.steps):
             res.append(learned.gain(mlp, test, seed=args.seed + s, warm_rounds=2, precision=pecc.FP32_POLISH64))
+        clk.mark_end()
     wf = sum(r["warm_feasible"] for r in res)
     pf = sum(r["plain_feasible"] for r in res)
     wms = sum(r["warm_ms"] for r in res)
@@ -448,6 +481,7 @@ def main():
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shape")
+    ap.add_argument("--launch", default="", help="fixed launch shape THREADSxBLOCKS_PER_SM (no autotune), e.g. 128x4")
     ap.add_argument("--instances", type=int, default=0, help="use only the first N instances (small profiling case)")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -102,8 +102,11 @@ typedef struct {
     double feas_tol;        /* feasible when the largest overlap depth <= feas_tol; 1e-9 */
     double nbr_capacity;    /* neighbor entries reserved per circle; 16 */
     int64_t time_budget_ns; /* per pecc_descend call, measured on the device; 0 = none */
-    int32_t block_threads;  /* threads per instance block; 0 = autotuned */
-    int32_t blocks_per_sm;  /* resident instance blocks per SM; 0 = autotuned */
+    int32_t block_threads;  /* threads per instance block; 0 = about two circles per thread
+                               (at most 256 when instances outnumber SMs), or pecc_autotune's */
+    int32_t blocks_per_sm;  /* target of resident instance blocks per SM, which also caps each
+                               block's shared-memory share of the working set; 0 = 2 when
+                               instances outnumber SMs, else 1, or pecc_autotune's */
     double stall_rel;       /* FP32 phase of PECC_FP32_POLISH64 / PECC_FP32 ends (status STALLED) when
                                E fell by less than stall_rel (relative) over stall_window sweeps:
                                binary32 has reached its resolution; 1e-3 */

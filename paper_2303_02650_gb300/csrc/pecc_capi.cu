@@ -177,6 +177,7 @@ pecc_status pecc_create(const pecc_config *cfg, void *stream, pecc_ctx **out) {
   if (cfg->block_threads != 0 && (cfg->block_threads < 32 || cfg->block_threads % 32 ||
                                   cfg->block_threads > descend_max_block(cfg->precision == PECC_FP64 ? 0 : 1)))
     return fail(nullptr, PECC_ERR_ARG, "block_threads must be a multiple of 32 within the kernel's limit");
+  if (cfg->blocks_per_sm < 0 || cfg->blocks_per_sm > 32) return fail(nullptr, PECC_ERR_ARG, "blocks_per_sm must be in 0..32");
   int64_t total = 0;
   for (int q = 0; q < cfg->num_instances; ++q) {
     if (cfg->n[q] < 0) return fail(nullptr, PECC_ERR_ARG, "n[%d] < 0", q);
@@ -495,8 +496,9 @@ pecc_status pecc_energy_grad(pecc_ctx *ctx, double *E_dev, void *grad_dev) {
   return pecc_energy_grad_ex(ctx, ctx->cfg.precision == PECC_FP64 ? PECC_FP64 : PECC_FP32, E_dev, grad_dev);
 }
 
-// Launch shape of one descent arithmetic.  block / bps_target 0 = the default: about two circles
-// per thread (at most 256 threads when instances outnumber SMs) and as many blocks per SM as fit.
+// Launch shape of one descent arithmetic.  block / bps_target 0 = the config's, else the default:
+// about two circles per thread (at most 256 threads when instances outnumber SMs) and as many
+// blocks per SM as fit.
 // Dynamic shared memory: the largest working set, capped so that bps_target blocks share an SM
 // (the working set spills to global memory past the cap); blocks per SM from the occupancy
 // calculator.
@@ -515,7 +517,9 @@ static pecc_status plan_launch(pecc_ctx *ctx, int arith, int block = 0, int bps_
     need = std::max(need, descend_smem_need(arith, D.n, k, arith == 1 ? D.ncx_f : D.ncx));
   }
   const bool many = ctx->num > ctx->num_sms;
-  if (bps_target <= 0) bps_target = many ? 2 : 1;
+  if (bps_target <= 0) bps_target = ctx->cfg.blocks_per_sm;
+  const bool fixed = bps_target > 0;  // else as many blocks per SM as fit
+  if (!fixed) bps_target = many ? 2 : 1;
   size_t cap = (size_t)per_sm / bps_target;
   cap = (cap > stat ? cap - stat : 0);
   cap = std::min(cap, (size_t)optin - stat);
@@ -535,7 +539,7 @@ static pecc_status plan_launch(pecc_ctx *ctx, int arith, int block = 0, int bps_
   int occ = 0;
   CK(descend_occupancy(arith, blk, L.smem, &occ));
   if (occ < 1) return fail(ctx, PECC_ERR_CUDA, "descent kernel does not fit an SM (block %d, smem %zu)", blk, L.smem);
-  L.bps = ctx->cfg.blocks_per_sm > 0 ? std::min(ctx->cfg.blocks_per_sm, occ) : occ;
+  L.bps = fixed ? std::min(bps_target, occ) : occ;
   L.grid = (int)std::min<int64_t>(ctx->num, (int64_t)ctx->num_sms * L.bps);
   return PECC_OK;
 }
