@@ -112,6 +112,9 @@ typedef struct {
                                binary32 has reached its resolution; 1e-3 */
     int32_t stall_window;   /* sweeps per stagnation check of the FP32 phase; 10 (0 = off) */
     int32_t polish_k;       /* batches of the FP64 polish (at most k_batches); 1 (0 = k_batches) */
+    int32_t smem_per_block; /* bytes of dynamic shared memory per instance block at most (the rest
+                               of the working set stays in global memory and the SM's L1 keeps the
+                               room); 0 = the block's whole share of the SM */
 } pecc_config;
 
 /* Fill *cfg with the defaults listed above (num_instances = 0, n = NULL). */
@@ -216,7 +219,8 @@ pecc_status pecc_get_stats(pecc_ctx *ctx, int32_t *stats_dev);
 pecc_status pecc_phase_times(pecc_ctx *ctx, float *ms_host);
 
 /* Autotuner of the descent's launch shape: for threads per instance block in {128, 256, 512} and
- * a target of {1, 2, 4} blocks per SM (which sets the shared-memory share of the working set), it
+ * a target of {1, 2, 4, 5, 6} blocks per SM (which sets the shared-memory share of the working set
+ * and the compiled kernel instance: the largest register budget that reaches the target), it
  * draws a layout from seed and times `sweeps` sweeps of the context's own instances, and keeps the
  * shape with the most circle-sweeps per second for the following pecc_descend calls (also after
  * pecc_set_radius, which only re-sizes the shared-memory share).  The FP64 polish of

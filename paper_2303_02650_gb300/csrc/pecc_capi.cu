@@ -43,7 +43,7 @@ struct pecc_ctx {
   bool radius_set = false;
   int lists_prec = -1;  // precision of the standalone lists: 0 FP64, 1 FP32
   int block = 0, bps = 0, grid = 0, block_build = 256;
-  struct Launch { int block = 0, bps = 0, grid = 0; size_t smem = 0; } lc[3];  // per arithmetic
+  struct Launch { int block = 0, bps = 0, grid = 0, var = 0; size_t smem = 0; } lc[3];  // per arithmetic
   bool lc_ready = false;
   bool tuned = false;  // launch shapes chosen by pecc_autotune
   int tuned_block = 0, tuned_bps = 0;
@@ -174,6 +174,7 @@ pecc_status pecc_create(const pecc_config *cfg, void *stream, pecc_ctx **out) {
   if (!(cfg->nbr_capacity >= 1.0)) return fail(nullptr, PECC_ERR_ARG, "nbr_capacity must be >= 1");
   if (cfg->stall_window < 0 || !(cfg->stall_rel >= 0.0)) return fail(nullptr, PECC_ERR_ARG, "bad stall rule");
   if (cfg->polish_k < 0 || cfg->polish_k > kMaxK) return fail(nullptr, PECC_ERR_ARG, "polish_k must be in 0..64");
+  if (cfg->smem_per_block < 0) return fail(nullptr, PECC_ERR_ARG, "smem_per_block must be >= 0");
   if (cfg->block_threads != 0 && (cfg->block_threads < 32 || cfg->block_threads % 32 ||
                                   cfg->block_threads > descend_max_block(cfg->precision == PECC_FP64 ? 0 : 1)))
     return fail(nullptr, PECC_ERR_ARG, "block_threads must be a multiple of 32 within the kernel's limit");
@@ -507,23 +508,7 @@ static pecc_status plan_launch(pecc_ctx *ctx, int arith, int block = 0, int bps_
   int dev = ctx->device, optin = 0, per_sm = 0;
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-  const size_t stat = descend_static_smem(arith) + 1024;
-  size_t need = 0;
-  for (int q = 0; q < ctx->num; ++q) {
-    const InstDesc &D = ctx->desc_h[q];
-    if (D.big) continue;
-    int k = D.k;
-    if (arith == 2 && ctx->cfg.polish_k > 0) k = std::min(ctx->cfg.polish_k, D.k);
-    need = std::max(need, descend_smem_need(arith, D.n, k, arith == 1 ? D.ncx_f : D.ncx));
-  }
   const bool many = ctx->num > ctx->num_sms;
-  if (bps_target <= 0) bps_target = ctx->cfg.blocks_per_sm;
-  const bool fixed = bps_target > 0;  // else as many blocks per SM as fit
-  if (!fixed) bps_target = many ? 2 : 1;
-  size_t cap = (size_t)per_sm / bps_target;
-  cap = (cap > stat ? cap - stat : 0);
-  cap = std::min(cap, (size_t)optin - stat);
-  L.smem = std::min(need, cap) & ~size_t(15);
   int blk = block > 0 ? block : ctx->cfg.block_threads;
   if (blk == 0) {
     int nmax = 0;
@@ -535,13 +520,56 @@ static pecc_status plan_launch(pecc_ctx *ctx, int arith, int block = 0, int bps_
   }
   blk = std::min(blk, descend_max_block(arith));
   L.block = blk;
-  CK(descend_prepare(arith, L.smem));
-  int occ = 0;
-  CK(descend_occupancy(arith, blk, L.smem, &occ));
-  if (occ < 1) return fail(ctx, PECC_ERR_CUDA, "descent kernel does not fit an SM (block %d, smem %zu)", blk, L.smem);
-  L.bps = fixed ? std::min(bps_target, occ) : occ;
+  size_t need = 0, mand = 0;
+  for (int q = 0; q < ctx->num; ++q) {
+    const InstDesc &D = ctx->desc_h[q];
+    if (D.big) continue;
+    int k = D.k;
+    if (arith == 2 && ctx->cfg.polish_k > 0) k = std::min(ctx->cfg.polish_k, D.k);
+    need = std::max(need, descend_smem_need(arith, D.n, k, arith == 1 ? D.ncx_f : D.ncx, blk));
+    mand = std::max(mand, descend_smem_mandatory(arith, k, blk));
+  }
+  if (bps_target <= 0) bps_target = ctx->cfg.blocks_per_sm;
+  const bool fixed = bps_target > 0;  // else as many blocks per SM as fit
+  if (!fixed) bps_target = many ? 2 : 1;
+  // the compiled instance: the largest register budget that reaches the target blocks per SM (the
+  // most resident blocks when none does); without a target, the largest budget
+  const DescendVariant *vs = nullptr;
+  const int nv = descend_variants(arith, &vs);
+  int best = -1, best_occ = 0;
+  size_t best_smem = 0;
+  for (int v = 0; v < nv; ++v) {
+    if (blk > vs[v].max_threads) continue;
+    // per-block share: the SM's shared memory over the target, in whole KB (allocation
+    // granularity), less the static block state and the 1 KB the system reserves per block
+    const size_t stat = (vs[v].static_smem + 1024 + 255) & ~size_t(255);
+    size_t cap = ((size_t)per_sm / bps_target) & ~size_t(1023);
+    cap = (cap > stat ? cap - stat : 0);
+    cap = std::min(cap, (size_t)optin - stat);
+    if (ctx->cfg.smem_per_block > 0) cap = std::min(cap, (size_t)ctx->cfg.smem_per_block);
+    const size_t smem = std::max(mand, std::min(need, cap) & ~size_t(255));
+    if (smem + stat > (size_t)optin) continue;
+    CK(cudaFuncSetAttribute(vs[v].fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int occ = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, vs[v].fn, blk, smem));
+    if (occ < 1) continue;
+    if (best < 0 || occ > best_occ) { best = v; best_occ = occ; best_smem = smem; }
+    if (!fixed || occ >= bps_target) break;
+  }
+  if (best < 0)
+    return fail(ctx, PECC_ERR_ARG, "descent kernel does not fit an SM (block %d, %zu bytes of shared memory needed)", blk, mand);
+  CK(cudaFuncSetAttribute(vs[best].fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)best_smem));
+  L.var = best;
+  L.smem = best_smem;
+  L.bps = fixed ? std::min(bps_target, best_occ) : best_occ;
   L.grid = (int)std::min<int64_t>(ctx->num, (int64_t)ctx->num_sms * L.bps);
   return PECC_OK;
+}
+
+static const DescendVariant &variant_of(pecc_ctx *c, int arith) {
+  const DescendVariant *vs = nullptr;
+  descend_variants(arith, &vs);
+  return vs[c->lc[arith].var];
 }
 
 static DescendParams dparams(pecc_ctx *c, int phase) {
@@ -581,16 +609,16 @@ static cudaError_t enqueue_descend(pecc_ctx *c) {
   if ((e = launch_stamp(c->t0, c->stream))) return e;
   if ((e = cudaEventRecordWithFlags(c->ev[0], c->stream, cudaEventRecordExternal))) return e;
   if (c->cfg.precision == PECC_FP64) {
-    if ((e = launch_descend(0, dparams(c, 0), c->lc[0].grid, c->lc[0].block, c->stream))) return e;
+    if ((e = launch_descend(variant_of(c, 0), dparams(c, 0), c->lc[0].grid, c->lc[0].block, c->stream))) return e;
     if ((e = cudaEventRecordWithFlags(c->ev[1], c->stream, cudaEventRecordExternal))) return e;
     return cudaEventRecordWithFlags(c->ev[2], c->stream, cudaEventRecordExternal);
   }
-  if ((e = launch_descend(1, dparams(c, 1), c->lc[1].grid, c->lc[1].block, c->stream))) return e;
+  if ((e = launch_descend(variant_of(c, 1), dparams(c, 1), c->lc[1].grid, c->lc[1].block, c->stream))) return e;
   if ((e = cudaEventRecordWithFlags(c->ev[1], c->stream, cudaEventRecordExternal))) return e;
   if (c->cfg.precision == PECC_FP32_POLISH64) {
     DescendParams p = dparams(c, 2);
     p.max_iter = c->cfg.polish_max_iter;
-    if ((e = launch_descend(2, p, c->lc[2].grid, c->lc[2].block, c->stream))) return e;
+    if ((e = launch_descend(variant_of(c, 2), p, c->lc[2].grid, c->lc[2].block, c->stream))) return e;
   }
   return cudaEventRecordWithFlags(c->ev[2], c->stream, cudaEventRecordExternal);
 }
@@ -685,7 +713,7 @@ pecc_status pecc_autotune(pecc_ctx *ctx, int32_t sweeps, uint64_t seed, int32_t 
   ctx->cfg.stall_window = 0;
   ctx->cfg.precision = arith == 1 ? PECC_FP32 : PECC_FP64;
   const int blocks[3] = {128, 256, 512};
-  const int targets[3] = {1, 2, 4};
+  const int targets[5] = {1, 2, 4, 5, 6};
   double best = -1.0;
   int best_b = 0, best_t = 0;
   cudaEvent_t e0, e1;
@@ -694,7 +722,7 @@ pecc_status pecc_autotune(pecc_ctx *ctx, int32_t sweeps, uint64_t seed, int32_t 
   std::vector<int32_t> st((size_t)ctx->num * 10);
   pecc_status err = PECC_OK;
   for (int bi = 0; bi < 3 && !err; ++bi) {
-    for (int ti = 0; ti < 3 && !err; ++ti) {
+    for (int ti = 0; ti < 5 && !err; ++ti) {
       if (blocks[bi] > descend_max_block(arith)) continue;
       if ((err = plan_launch(ctx, arith, blocks[bi], targets[ti]))) break;
       if (ctx->lc[arith].bps < targets[ti]) continue;  // that many blocks do not fit an SM

@@ -1,728 +1,22 @@
-// pecc_descend.cu -- persistent descent kernel: Algorithm GBO (Sec. 4.1) with ANM (Sec. 4.3).
-//
-// One thread block owns one instance at a time and pops the next instance from
-// a device work queue when it is done.  Inside the block:
-//   * partition: circles ranked by the partition key (sector: pseudo-angle of
-//     the polar angle; annulus: radius; fence: x), ties by index, then cut into
-//     k contiguous batches of floor(n/k) or ceil(n/k) circles (Sec. 4.1).  The
-//     instance is renumbered in that order, so batch p is a contiguous range of
-//     every per-circle array and "merge" is a scatter at the end.
-//   * neighbor lists: cell binning + stable key sort + 3x3-cell CSR build, in the
-//     block (cta_build_neighbors).  Rebuilt by ANM after every sweep (Algorithm
-//     ANM: Gamma' replaces Gamma, and whether it differs -- compared through an
-//     order-independent 64-bit digest of the pair set -- decides the deferral
-//     length) and before a batch step whenever twice the largest displacement since
-//     the last build plus the step cap could exceed l_cut - 2 (Verlet rule).
-//   * per batch step (Eq. 8): the batch energy of Eq. 7 and its gradient, the
-//     quasi-Newton direction -H g of Eq. 10 / Eq. 11 with m secant pairs, a
-//     backtracking line search in place of the argmin of Eq. 9, and a secant
-//     pair push when the curvature condition holds.
-//
-// The instance's working set (coordinates, gradients, direction, neighbor lists,
-// cell scratch, Gram matrices) is carved out of dynamic shared memory as far as it
-// fits, the rest falls back to global memory; the secant pairs stay in global
-// memory (read coalesced, L2-resident for the instances in flight).
-//
-// The direction is computed in "vector-free" form (Chen, Wang, Zhou, Burges,
-// "Large-scale L-BFGS using MapReduce", NIPS 2014): the two-loop recursion is
-// run on the Gram matrix of the basis {s_a, y_a, g} by one warp, and the direction
-// is assembled as one linear combination.  In exact arithmetic this is the
-// two-loop recursion; it replaces 2m dependent block-wide dot products by one
-// batched reduction per step.
-#include <cfloat>
-
-#include "pecc_internal.h"
+// pecc_descend.cu -- host side of the persistent descent kernel (pecc_descend_kernel.cuh): the
+// compiled instances per arithmetic, launch, shared-memory sizing.  The binary64 and mixed
+// (polish) instances are compiled here, the binary32 ones in pecc_descend32.cu.
+#include "pecc_descend_kernel.cuh"
 
 namespace pecc {
 
-namespace {
+// Instances by arithmetic, the largest register budget first.  A block of the FP64 kernel needs
+// about 225 registers per thread for its binary64 state (fewer spill); the polish and the FP32
+// kernel run without spills at 96 registers, which lets five 128-thread blocks share an SM.
+static const DescendVariant kVar64[] = {descend_variant<Arith64, 256, 1>()};
+static const DescendVariant kVarMix[] = {descend_variant<ArithMix, 256, 2>(), descend_variant<ArithMix, 128, 5>()};
 
-constexpr int KS = kMaxSlots;     // basis index of Y slot a is KS + a
-constexpr int GI = 2 * kMaxSlots; // basis index of g
-constexpr int NDOT = 4 * kMaxSlots + 3;
-// values of the first reduction of a batch step, padded to a multiple of 32 for the reduce-scatter:
-//   [0] g'g, [1 + a] g's_a and [1 + KS + a] g'y_a for every physical slot a,
-//   [OP + a], [OP + KS + a], [OP + 2 KS + a], [OP + 3 KS + a]: s's_a, s'y_a, y's_a, y'y_a of the
-//   pending pair (s, y) against physical slot a, [OP + 4 KS + 0..2]: s's, s'y, y'y.
-constexpr int OP = 1 + 2 * kMaxSlots;
-constexpr int NRA = ((OP + 4 * kMaxSlots + 3 + 31) / 32) * 32;
-constexpr int NR4 = NRA;
-constexpr int kRingInts = kMaxSlots + 3;  // count, stage, ring[kMaxSlots], pending
-
-__device__ __forceinline__ uint64_t sortable(double v) {
-  uint64_t b = (uint64_t)__double_as_longlong(v);
-  return (b & 0x8000000000000000ull) ? ~b : (b | 0x8000000000000000ull);
+int descend_variants(int arith, const DescendVariant **v) {
+  if (arith == 0) { *v = kVar64; return (int)(sizeof(kVar64) / sizeof(kVar64[0])); }
+  if (arith == 1) return descend_variants32(v);
+  *v = kVarMix;
+  return (int)(sizeof(kVarMix) / sizeof(kVarMix[0]));
 }
-
-// Partition key of Sec. 4.1 with correctly rounded operations.
-__device__ __forceinline__ double part_key(double x, double y, int mode) {
-  if (mode == 1) return __dsqrt_rn(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)));
-  if (mode == 2) return x;
-  double s = __dadd_rn(fabs(x), fabs(y));
-  if (s == 0.0) return 0.0;
-  double t = __ddiv_rn(x, s);
-  return (y >= 0.0) ? __dsub_rn(1.0, t) : __dadd_rn(3.0, t);
-}
-
-template <class A> struct MaxT { static constexpr int v = 512; };  // threads per block, at most
-template <> struct MaxT<Arith64> { static constexpr int v = 256; };
-template <> struct MaxT<ArithMix> { static constexpr int v = 256; };
-
-template <class A> struct Smem {
-  using vec_t = typename A::vec_t;
-  using acc_t = typename A::acc_t;
-  static constexpr int W = MaxT<A>::v / 32;
-  acc_t ra[W * 2];            // reduction scratch: acc sums
-  vec_t rb[W * NR4];          // vec sums
-  vec_t rc[W * 2];            // maxima
-  acc_t oa[2];
-  vec_t ob[NR4];
-  vec_t oc[2];
-  vec_t coef[kBasis];
-  vec_t alpha[kMaxSlots];
-  int ring[kMaxK][kRingInts];  // per batch: count, stage slot, ring slots oldest -> newest
-  unsigned long long hash;
-  unsigned used;               // physical slots in the current batch's ring (bit mask)
-  int32_t sh[40];
-  int q;
-  int flag;
-};
-
-// Block reduction of NA acc sums, NB vec sums and NC vec maxima.
-template <class A, int NA, int NB, int NC>
-__device__ __forceinline__ void reduce(Smem<A> &S, typename A::acc_t (&a)[NA], typename A::vec_t (&b)[NB],
-                                       typename A::vec_t (&c)[NC]) {
-  using vec_t = typename A::vec_t;
-  using acc_t = typename A::acc_t;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-  for (int q = 0; q < NA; ++q) { acc_t v = warp_sum(a[q]); if (lane == 0) S.ra[w * NA + q] = v; }
-#pragma unroll
-  for (int q = 0; q < NB; ++q) { vec_t v = warp_sum(b[q]); if (lane == 0) S.rb[w * NB + q] = v; }
-#pragma unroll
-  for (int q = 0; q < NC; ++q) { vec_t v = warp_max(c[q]); if (lane == 0) S.rc[w * NC + q] = v; }
-  __syncthreads();
-  for (int q = threadIdx.x; q < NA + NB + NC; q += blockDim.x) {
-    if (q < NA) {
-      acc_t s = 0; for (int u = 0; u < nw; ++u) s += S.ra[u * NA + q];
-      S.oa[q] = s;
-    } else if (q < NA + NB) {
-      int r = q - NA; vec_t s = 0; for (int u = 0; u < nw; ++u) s += S.rb[u * NB + r];
-      S.ob[r] = s;
-    } else {
-      int r = q - NA - NB; vec_t s = S.rc[r]; for (int u = 1; u < nw; ++u) s = max(s, S.rc[u * NC + r]);
-      S.oc[r] = s;
-    }
-  }
-  __syncthreads();
-}
-
-// Block reduction of one acc sum and NV vec sums (NV a multiple of 32) by a reduce-scatter
-// within each warp, then one sum over the warps per value.
-template <class A, int NV>
-__device__ __forceinline__ void reduce_many(Smem<A> &S, typename A::acc_t a0, typename A::vec_t (&v)[NV]) {
-  using vec_t = typename A::vec_t;
-  using acc_t = typename A::acc_t;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  warp_reduce_scatter<vec_t, NV>(v);
-  acc_t a = warp_sum(a0);
-#pragma unroll
-  for (int j = 0; j < NV / 32; ++j) S.rb[w * NV + (NV / 32) * lane + j] = v[j];
-  if (lane == 0) S.ra[w] = a;
-  __syncthreads();
-  for (int q = threadIdx.x; q <= NV; q += blockDim.x) {
-    if (q < NV) {
-      vec_t s = 0; for (int u = 0; u < nw; ++u) s += S.rb[u * NV + q];
-      S.ob[q] = s;
-    } else {
-      acc_t s = 0; for (int u = 0; u < nw; ++u) s += S.ra[u];
-      S.oa[0] = s;
-    }
-  }
-  __syncthreads();
-}
-
-// Block reduction of one acc sum and one vec maximum.
-template <class A>
-__device__ __forceinline__ void reduce_sum_max(Smem<A> &S, typename A::acc_t a0, typename A::vec_t m0) {
-  using vec_t = typename A::vec_t;
-  using acc_t = typename A::acc_t;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  acc_t a = warp_sum(a0);
-  vec_t m = warp_max(m0);
-  if (lane == 0) { S.ra[w] = a; S.rc[w] = m; }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    acc_t sa = 0; vec_t sm = S.rc[0];
-    for (int u = 0; u < nw; ++u) { sa += S.ra[u]; sm = max(sm, S.rc[u]); }
-    S.oa[0] = sa; S.oc[0] = sm;
-  }
-  __syncthreads();
-}
-
-// Bump allocator over dynamic shared memory; returns the fallback when the request does not fit.
-struct Carve {
-  unsigned char *base;
-  size_t cap, used;
-  template <typename T> __device__ T *take(size_t count, T *fallback) {
-    size_t b = (count * sizeof(T) + 15) & ~size_t(15);
-    if (used + b <= cap) {
-      T *p = (T *)(base + used);
-      used += b;
-      return p;
-    }
-    return fallback;
-  }
-};
-
-
-template <class A, int MAXT>
-__global__ void __launch_bounds__(MAXT, 1)
-descend_kernel(DescendParams P) {
-  using pos_t = typename A::pos_t;
-  using vec_t = typename A::vec_t;
-  using acc_t = typename A::acc_t;
-  using sc_t = acc_t;  // per-step scalars in the arithmetic's own precision
-  using PP = v2<pos_t>;
-  using VV = v2<vec_t>;
-  extern __shared__ __align__(16) unsigned char dsm[];
-  __shared__ Smem<A> S;
-  const sc_t c1 = (sc_t)P.c1, step_max = (sc_t)P.step_max, two_skin = (sc_t)(2.0 * P.rebuild_disp);
-  const sc_t gsum_tol = (sc_t)P.gsum_tol, curv_eps = (sc_t)P.curv_eps;
-  const int tid = threadIdx.x, T = blockDim.x;
-  const int lane = tid & 31, warp = tid >> 5;
-  const int mm = P.m + 1;  // physical slots
-
-  for (;;) {
-    if (tid == 0) S.q = atomicAdd(P.queue, 1);
-    __syncthreads();
-    const int qi = S.q;
-    __syncthreads();
-    if (qi >= P.num) break;
-    const int q = P.order[qi];
-    const InstDesc D = P.desc[q];
-    if (D.big) continue;  // descended by the whole GPU after this launch (uniform across the block)
-    InstOut *O = P.out + q;
-    const int n = D.n;
-    const acc_t R = (acc_t)D.R;
-    const acc_t Rm1sq = (acc_t)((D.R >= 1.0) ? (D.R - 1.0) * (D.R - 1.0) : -1.0);
-
-    // ---- phase entry: the polish runs only on instances the FP32 descent left near zero energy
-    if (A::kId == 2) {
-      bool skip = !(O->E32 <= P.polish_gate) || O->status32 >= 4;
-      if (skip) {
-        for (int i = tid; i < n; i += T) {
-          float2 v = P.x32[D.off + i];
-          P.x64[D.off + i] = make_double2((double)v.x, (double)v.y);
-        }
-        if (tid == 0) {
-          O->iters = O->iters32; O->status = O->status32; O->E = O->E32; O->polished = 0;
-        }
-        __syncthreads();
-        continue;
-      }
-    }
-    if (n == 0) {
-      if (tid == 0) {
-        O->iters = 0; O->status = 0; O->E = 0.0;
-        if (A::kId == 1) { O->iters32 = 0; O->status32 = 0; O->E32 = 0.0; O->trials32 = 0; }
-      }
-      __syncthreads();
-      continue;
-    }
-    const int k = (P.k_override > 0) ? min(P.k_override, D.k) : D.k;
-
-    // ---- working set: shared memory first, global scratch as the fallback
-    Carve cv{dsm, P.smem_bytes, 0};
-    PP *xw = cv.take<PP>(n, (PP *)P.xw + D.off);
-    VV *g = cv.take<VV>(n, (VV *)P.g + D.off);
-    VV *gt = cv.take<VV>(n, (VV *)P.gt + D.off);
-    VV *dv = cv.take<VV>(n, (VV *)P.d + D.off);
-    int32_t *rp = cv.take<int32_t>(n + 1, P.rp + D.rp_off);
-    // neighbor indices are 16-bit inside the descent (instances of at most 65535 circles)
-    const int cap_s = min(D.cap, 10 * n + 64);
-    uint16_t *col_s = cv.take<uint16_t>(cap_s, (uint16_t *)nullptr);
-    uint16_t *const col_g = (uint16_t *)(P.col + D.col_off);  // 2 cap int32 = 4 cap uint16
-    uint16_t *col = col_s ? col_s : col_g;
-    int cap = col_s ? cap_s : D.cap;
-    PP *xo = cv.take<PP>(n, (PP *)P.xo + D.off);
-    vec_t *gram = cv.take<vec_t>((size_t)k * kBasis * kBasis, (vec_t *)P.gram + D.gram_off);
-    const CellGrid G = (A::kId == 1) ? CellGrid{D.R, D.inv_cs, (float)D.R, D.inv_f, D.ncx_f, true}
-                                     : CellGrid{D.R, D.inv_cs, 0.f, 0.f, D.ncx, false};
-    int32_t *cells = cv.take<int32_t>(2 * (size_t)G.nc * G.nc + 2, P.cells + D.cell_off);
-    uint32_t *ckey = cv.take<uint32_t>(n, P.ckey + D.off);
-    int32_t *corder = cv.take<int32_t>(n, P.corder + D.off);
-    PP *xb = cv.take<PP>(n, (PP *)P.xb + D.off);
-    VV *Sv = (VV *)P.S + (int64_t)mm * D.off;
-    VV *Yv = (VV *)P.Y + (int64_t)mm * D.off;
-    int32_t *perm = P.perm + D.off;
-    // the partition keys borrow the list storage (8 n bytes) before the first build
-    uint64_t *skey = (col_s && (size_t)cap_s * 2 >= (size_t)n * 8) ? (uint64_t *)col_s : P.skey + D.off;
-    const pos_t lc2 = (pos_t)(P.l_cut * P.l_cut);
-
-    // ---- 1. partition key and rank (stable by index)
-    for (int i = tid; i < n; i += T) {
-      double x, y;
-      if (A::kId == 0) { double2 v = P.x64[D.off + i]; x = v.x; y = v.y; }
-      else { float2 v = P.x32[D.off + i]; x = v.x; y = v.y; }
-      skey[i] = sortable(part_key(x, y, P.partition));
-    }
-    __syncthreads();
-    for (int i = tid; i < n; i += T) {
-      uint64_t ki = skey[i];
-      int r = 0;
-      for (int j = 0; j < n; ++j) {
-        uint64_t kj = skey[j];
-        r += (kj < ki) || (kj == ki && j < i);
-      }
-      perm[r] = i;
-    }
-    __syncthreads();
-    // ---- 2. renumber: working coordinates in partition order
-    int bad = 0;
-    for (int p = tid; p < n; p += T) {
-      int i = perm[p];
-      PP v;
-      if (A::kId == 0) { double2 u = P.x64[D.off + i]; v.x = (pos_t)u.x; v.y = (pos_t)u.y; }
-      else { float2 u = P.x32[D.off + i]; v.x = (pos_t)u.x; v.y = (pos_t)u.y; }
-      bad |= !(isfinite((float)v.x) && isfinite((float)v.y));
-      xw[p] = v;
-      xb[p] = v;
-    }
-    bad = __syncthreads_or(bad);
-
-    int status = 3;  // max_iter unless something else ends the run
-    int iters = 0, builds = 0, changes = 0, trials = 0, resets = 0, stalls = 0;
-    int cnt = 0, len = 1;
-    unsigned long long hcur = 0ull;  // digest of the current lists
-    sc_t Dmax = 0;  // largest displacement since the last build
-    acc_t E = 0;
-
-    // one neighbor build into the block's list storage; moves the lists to global memory when
-    // they outgrow their shared-memory share; false when even the global capacity is exceeded
-    auto build = [&]() -> bool {
-      int tot = cta_build_neighbors<pos_t, uint16_t>(xw, n, G, lc2, ckey, corder, cells, xo, rp, col, cap, S.sh,
-                                                     &S.hash, false);
-      if (tot > cap && col_s && col == col_s) {
-        col = col_g;
-        cap = D.cap;
-        tot = cta_build_neighbors<pos_t, uint16_t>(xw, n, G, lc2, ckey, corder, cells, xo, rp, col, cap, S.sh,
-                                                   &S.hash, false);
-      }
-      return tot <= cap;
-    };
-    // ANM step (Algorithm ANM): Gamma' replaces Gamma; equal sets double the deferral length
-    auto anm_rebuild = [&]() -> bool {
-      if (!build()) return false;
-      ++builds;
-      const unsigned long long h = S.hash;
-      if (h != hcur) { hcur = h; len = 1; ++changes; }
-      else if (len < (1 << 30)) len *= 2;
-      cnt = 0;
-      for (int p = tid; p < n; p += T) xb[p] = xw[p];
-      Dmax = 0;
-      __syncthreads();
-      return true;
-    };
-    // full energy (Eq. 5 over the lists: each pair from its larger index)
-    auto full_energy = [&]() -> acc_t {
-      acc_t a[1] = {0};
-      vec_t b[1] = {0}, c[1] = {0};
-      for (int p = tid; p < n; p += T) {
-        PP xi = xw[p];
-        acc_t e = 0;
-        for (int t = rp[p]; t < rp[p + 1]; ++t) {
-          int j = col[t];
-          if (j >= p) continue;
-          vec_t fx, fy;
-          acc_t d = A::pair(xi, xw[j], fx, fy);
-          e += d * d;
-        }
-        vec_t fx, fy;
-        acc_t d0 = A::wall(xi, R, Rm1sq, fx, fy);
-        a[0] += e + d0 * d0;
-      }
-      reduce<A, 1, 1, 1>(S, a, b, c);
-      return S.oa[0];
-    };
-
-    if (bad) {
-      status = 5;
-    } else {
-      if (!build()) status = 4;
-      else {
-        builds = 1;
-        hcur = S.hash;
-        E = full_energy();
-        if (!isfinite(E)) status = 5;
-        else if (E <= (acc_t)P.e_tol) status = 0;
-      }
-    }
-    for (int u = tid; u < k * kRingInts; u += T) S.ring[u / kRingInts][u % kRingInts] = 0;
-    for (int u = tid; u < k * kBasis * kBasis; u += T) gram[u] = vec_t(0);
-    __syncthreads();
-
-    const int q_ = n / k, r_ = n % k;
-    bool fresh = false;  // k == 1: g / E of the previous accepted trial are current
-    int e_at = 0;        // sweep after which E was last evaluated
-    acc_t Ewin = E;      // FP32 phase: energy at the start of the stagnation window
-
-    // ---- 3. sweeps
-    while (status == 3 && iters < P.max_iter) {
-      ++iters;
-      sc_t gsum = 0;
-      int moved = 0;
-      for (int p = 0; p < k && status == 3; ++p) {
-        const int b = p * q_ + min(p, r_), e = b + q_ + (p < r_ ? 1 : 0);
-        // Verlet guarantee for the coming step
-        if (sc_t(2) * Dmax + step_max > two_skin) {
-          if (!anm_rebuild()) { status = 4; break; }
-          fresh = false;
-        }
-        int *ring = S.ring[p];  // [0] count, [1] stage, [2..] slots, [2 + KS] pending
-        vec_t *Gm = gram + (size_t)p * kBasis * kBasis;
-        const int count0 = ring[0], st = ring[1], pending = ring[2 + kMaxSlots];
-
-        // ---- pass A: batch energy (Eq. 7) and gradient, dots of g with every stored vector, and
-        // the dots of the pair written by this batch's previous step (its curvature is tested here)
-        acc_t aA = 0;
-        vec_t bA[NRA];
-#pragma unroll
-        for (int u = 0; u < NRA; ++u) bA[u] = 0;
-        if (fresh) { VV *t_ = g; g = gt; gt = t_; }
-        for (int pos = b + tid; pos < e; pos += T) {
-          PP xi = xw[pos];
-          xo[pos] = xi;
-          VV gi;
-          if (!fresh) {
-            vec_t gx = 0, gy = 0;
-            acc_t ei = 0;
-            for (int t = rp[pos]; t < rp[pos + 1]; ++t) {
-              int j = col[t];
-              vec_t fx, fy;
-              acc_t d = A::pair(xi, xw[j], fx, fy);
-              gx += fx; gy += fy;
-              if (j < b || j >= e || j < pos) ei += d * d;
-            }
-            vec_t fx, fy;
-            acc_t d0 = A::wall(xi, R, Rm1sq, fx, fy);
-            gx += fx; gy += fy;
-            aA += ei + d0 * d0;
-            gi.x = gx; gi.y = gy;
-            g[pos] = gi;
-          } else {
-            gi = g[pos];
-          }
-          bA[0] += gi.x * gi.x + gi.y * gi.y;
-          VV sp, yp;
-          if (pending) { sp = Sv[(int64_t)st * n + pos]; yp = Yv[(int64_t)st * n + pos]; }
-#pragma unroll
-          for (int a = 0; a < kMaxSlots; ++a) {
-            if (a < mm) {
-              const VV s_ = Sv[(int64_t)a * n + pos], y_ = Yv[(int64_t)a * n + pos];
-              bA[1 + a] += gi.x * s_.x + gi.y * s_.y;
-              bA[1 + KS + a] += gi.x * y_.x + gi.y * y_.y;
-              if (pending) {
-                bA[OP + a] += sp.x * s_.x + sp.y * s_.y;
-                bA[OP + KS + a] += sp.x * y_.x + sp.y * y_.y;
-                bA[OP + 2 * KS + a] += yp.x * s_.x + yp.y * s_.y;
-                bA[OP + 3 * KS + a] += yp.x * y_.x + yp.y * y_.y;
-              }
-            }
-          }
-          if (pending) {
-            bA[OP + 4 * KS + 0] += sp.x * sp.x + sp.y * sp.y;
-            bA[OP + 4 * KS + 1] += sp.x * yp.x + sp.y * yp.y;
-            bA[OP + 4 * KS + 2] += yp.x * yp.x + yp.y * yp.y;
-          }
-        }
-        reduce_many<A, NRA>(S, aA, bA);
-        const acc_t Ep = fresh ? E : S.oa[0];
-        const vec_t gg = S.ob[0];
-        const sc_t gnorm = sqrt((sc_t)gg);
-        gsum += gnorm;
-        fresh = false;
-        // the pending pair joins the memory when s'y > curv_eps |s| |y| (Gram rows, then the ring)
-        if (pending) {
-          const vec_t ss = S.ob[OP + 4 * KS], sy = S.ob[OP + 4 * KS + 1], yy = S.ob[OP + 4 * KS + 2];
-          const bool push = (sc_t)sy > curv_eps * sqrt((sc_t)ss) * sqrt((sc_t)yy) && P.m > 0;
-          if (push) {
-            if (tid < count0) {
-              int sl = ring[2 + tid];
-              Gm[st * kBasis + sl] = Gm[sl * kBasis + st] = S.ob[OP + sl];
-              Gm[st * kBasis + KS + sl] = Gm[(KS + sl) * kBasis + st] = S.ob[OP + KS + sl];
-              Gm[(KS + st) * kBasis + sl] = Gm[sl * kBasis + KS + st] = S.ob[OP + 2 * KS + sl];
-              Gm[(KS + st) * kBasis + KS + sl] = Gm[(KS + sl) * kBasis + KS + st] = S.ob[OP + 3 * KS + sl];
-            }
-            if (tid == 0) {
-              Gm[st * kBasis + st] = ss;
-              Gm[st * kBasis + KS + st] = Gm[(KS + st) * kBasis + st] = sy;
-              Gm[(KS + st) * kBasis + KS + st] = yy;
-            }
-          }
-          __syncthreads();
-          if (tid == 0) {
-            if (push) {
-              int c = ring[0];
-              if (c < P.m) {
-                ring[2 + c] = st;
-                ring[0] = c + 1;
-                int fr = 0;  // first slot not in the ring
-                for (; fr < mm; ++fr) {
-                  bool used = false;
-                  for (int u = 0; u <= c; ++u) used |= (ring[2 + u] == fr);
-                  if (!used) break;
-                }
-                ring[1] = fr;
-              } else {
-                int ev = ring[2];
-                for (int u = 0; u + 1 < c; ++u) ring[2 + u] = ring[3 + u];
-                ring[2 + c - 1] = st;
-                ring[1] = ev;
-              }
-            }
-            ring[2 + kMaxSlots] = 0;
-          }
-          __syncthreads();
-        }
-        const int count = ring[0];
-        if (!(gnorm > sc_t(0))) {
-          if (!isfinite((float)gnorm)) status = 5;
-          continue;
-        }
-
-        // ---- two-loop recursion on the Gram matrix (warp 0).  With ring positions c (oldest
-        // first), rho_c = 1 / s_c'y_c, the first loop is the back substitution
-        //   alpha_c = rho_c (s_c'g - sum_{d > c} alpha_d s_c'y_d),
-        // gamma = s'y / y'y of the newest pair, and the second loop the forward substitution
-        //   beta_c = rho_c (gamma (y_c'g - sum_d alpha_d y_c'y_d) + sum_{d < c} w_d y_c's_d),
-        // w_d = alpha_d - beta_d; then -H g = -gamma g + gamma sum_c alpha_c y_c - sum_c w_c s_c.
-        // Lane c holds row c; each substitution step is one broadcast.
-        if (warp == 0) {
-          const bool act = lane < count;
-          const int sl = act ? ring[2 + lane] : 0;
-          const vec_t rho = act ? vec_t(1) / Gm[sl * kBasis + KS + sl] : vec_t(0);
-          vec_t acc = act ? S.ob[1 + sl] : vec_t(0);
-          vec_t my_alpha = 0, my_w = 0, gam = 1;
-          for (int cc = count - 1; cc >= 0; --cc) {
-            const vec_t a = __shfl_sync(0xffffffffu, rho * acc, cc);
-            if (lane == cc) my_alpha = a;
-            const int slc = ring[2 + cc];
-            if (lane < cc) acc -= a * Gm[sl * kBasis + KS + slc];
-          }
-          if (count > 0) {
-            const int nw_ = ring[2 + count - 1];
-            gam = Gm[nw_ * kBasis + KS + nw_] / Gm[(KS + nw_) * kBasis + KS + nw_];
-          }
-          vec_t t = act ? S.ob[1 + KS + sl] : vec_t(0);
-          for (int dd = 0; dd < count; ++dd) {
-            const vec_t ad = __shfl_sync(0xffffffffu, my_alpha, dd);
-            const int sld = ring[2 + dd];
-            if (act) t -= ad * Gm[(KS + sl) * kBasis + KS + sld];
-          }
-          vec_t acc2 = gam * t;
-          for (int cc = 0; cc < count; ++cc) {
-            const vec_t bcc = __shfl_sync(0xffffffffu, rho * acc2, cc);
-            const vec_t w = __shfl_sync(0xffffffffu, my_alpha, cc) - bcc;
-            if (lane == cc) my_w = w;
-            const int slc = ring[2 + cc];
-            if (act && lane > cc) acc2 += w * Gm[slc * kBasis + KS + sl];
-          }
-          if (act) {
-            S.coef[sl] = -my_w;
-            S.coef[KS + sl] = gam * my_alpha;
-          }
-          const unsigned used = __reduce_or_sync(0xffffffffu, act ? (1u << sl) : 0u);
-          if (lane == 0) { S.coef[GI] = -gam; S.used = used; }
-        }
-        __syncthreads();
-
-        bool accepted = false;
-        acc_t Et = 0;
-        vec_t disp2 = 0;
-        for (int attempt = 0; attempt < 2 && !accepted; ++attempt) {
-          if (attempt == 1) {
-            if (ring[0] == 0) break;
-            __syncthreads();
-            if (tid == 0) { ring[0] = 0; S.used = 0u; }
-            ++resets;
-            for (int u = tid; u < kBasis; u += T) S.coef[u] = (u == GI) ? vec_t(-1) : vec_t(0);
-            __syncthreads();
-          }
-          // ---- pass B: direction, g'd and the largest per-circle move
-          for (int round = 0; round < 2; ++round) {
-            const unsigned used = S.used;
-            acc_t aB[1] = {0};
-            vec_t bB[1] = {0}, cB[1] = {0};
-            for (int pos = b + tid; pos < e; pos += T) {
-              VV gi = g[pos];
-              vec_t cg = S.coef[GI];
-              vec_t dx = cg * gi.x, dy = cg * gi.y;
-#pragma unroll
-              for (int a = 0; a < kMaxSlots; ++a) {
-                if (a < mm && ((used >> a) & 1u)) {
-                  const VV s_ = Sv[(int64_t)a * n + pos], y_ = Yv[(int64_t)a * n + pos];
-                  const vec_t cs = S.coef[a], cy = S.coef[KS + a];
-                  dx += cs * s_.x + cy * y_.x;
-                  dy += cs * s_.y + cy * y_.y;
-                }
-              }
-              VV dd; dd.x = dx; dd.y = dy;
-              dv[pos] = dd;
-              bB[0] += gi.x * dx + gi.y * dy;
-              cB[0] = max(cB[0], dx * dx + dy * dy);
-            }
-            reduce<A, 1, 1, 1>(S, aB, bB, cB);
-            if (S.ob[0] < vec_t(0) || round == 1) break;
-            // not a descent direction: drop the memory, take -g
-            if (tid == 0) { ring[0] = 0; S.used = 0u; }
-            if (used != 0u) ++resets;
-            for (int u = tid; u < kBasis; u += T) S.coef[u] = (u == GI) ? vec_t(-1) : vec_t(0);
-            __syncthreads();
-          }
-          const sc_t gd = (sc_t)S.ob[0];
-          const sc_t dmax = sqrt((sc_t)S.oc[0]);
-          if (!(gd < sc_t(0))) break;
-          sc_t al = (dmax > step_max) ? step_max / dmax : sc_t(1);
-          for (int tr = 0; tr < P.max_trials; ++tr) {
-            // ---- pass C: trial coordinates
-            for (int pos = b + tid; pos < e; pos += T) {
-              PP xo_ = xo[pos];
-              VV dd = dv[pos];
-              PP v;
-              v.x = xo_.x + (pos_t)(al * (sc_t)dd.x);
-              v.y = xo_.y + (pos_t)(al * (sc_t)dd.y);
-              xw[pos] = v;
-            }
-            __syncthreads();
-            // ---- pass D: trial batch energy and gradient, displacement since the build
-            acc_t aD = 0;
-            vec_t cD = 0;
-            for (int pos = b + tid; pos < e; pos += T) {
-              PP xi = xw[pos];
-              vec_t gx = 0, gy = 0;
-              acc_t ei = 0;
-              for (int t = rp[pos]; t < rp[pos + 1]; ++t) {
-                int j = col[t];
-                vec_t fx, fy;
-                acc_t d = A::pair(xi, xw[j], fx, fy);
-                gx += fx; gy += fy;
-                if (j < b || j >= e || j < pos) ei += d * d;
-              }
-              vec_t fx, fy;
-              acc_t d0 = A::wall(xi, R, Rm1sq, fx, fy);
-              gx += fx; gy += fy;
-              aD += ei + d0 * d0;
-              VV gg_; gg_.x = gx; gg_.y = gy;
-              gt[pos] = gg_;
-              PP x0 = xb[pos];
-              vec_t ex = (vec_t)(xi.x - x0.x), ey = (vec_t)(xi.y - x0.y);
-              cD = max(cD, ex * ex + ey * ey);
-            }
-            reduce_sum_max<A>(S, aD, cD);
-            ++trials;
-            Et = S.oa[0];
-            if (Et <= Ep + c1 * al * gd) {
-              accepted = true;
-              disp2 = S.oc[0];
-              break;
-            }
-            al *= sc_t(0.5);
-          }
-          if (!accepted) {
-            for (int pos = b + tid; pos < e; pos += T) xw[pos] = xo[pos];
-            __syncthreads();
-          }
-        }
-        if (!accepted) { ++stalls; continue; }
-        moved = 1;
-        Dmax = max(Dmax, (sc_t)sqrt((sc_t)disp2));
-
-        // ---- pass E: the secant pair s = x_new - x_old, y = g_new - g_old goes to the stage slot;
-        // its dots and its curvature test come with this batch's next step
-        {
-          const int stg = ring[1];
-          for (int pos = b + tid; pos < e; pos += T) {
-            PP xn = xw[pos], x0 = xo[pos];
-            VV s_; s_.x = (vec_t)(xn.x - x0.x); s_.y = (vec_t)(xn.y - x0.y);
-            VV gn = gt[pos], go = g[pos];
-            VV y_; y_.x = gn.x - go.x; y_.y = gn.y - go.y;
-            Sv[(int64_t)stg * n + pos] = s_;
-            Yv[(int64_t)stg * n + pos] = y_;
-          }
-          // every thread raises the flag: with one batch the next read comes without a barrier in
-          // between, and each thread then reads its own store (thread 0 clears the flag only after
-          // the next step's reduction barriers)
-          ring[2 + kMaxSlots] = 1;
-          if (k == 1) { fresh = true; E = Et; }
-        }
-      }
-      if (status != 3) break;
-      // ---- ANM after the sweep (Algorithm ANM)
-      if (P.anm) {
-        ++cnt;
-        if (cnt >= len) {
-          if (!anm_rebuild()) { status = 4; break; }
-        }
-      }
-      // the FP32 phase needs the total energy only for its stagnation check (its e_tol is out of
-      // binary32's reach); the FP64 phases test E <= e_tol after every sweep
-      const bool check_now = A::kId != 1 || P.stall_window <= 0 || iters % P.stall_window == 0;
-      if (check_now && !(k == 1 && fresh)) { E = full_energy(); e_at = iters; }
-      if (k == 1 && fresh) e_at = iters;
-      if (!isfinite(E)) { status = 5; break; }
-      if (E <= (acc_t)P.e_tol) { status = 0; break; }
-      if (gsum <= gsum_tol) { status = 1; break; }
-      if (!moved) { status = 2; break; }
-      // FP32 phase: binary32 has reached its resolution when E stops falling; hand over
-      if (A::kId == 1 && P.stall_window > 0 && iters % P.stall_window == 0) {
-        if (E > Ewin * (acc_t)(1.0 - P.stall_rel)) { status = 2; break; }
-        Ewin = E;
-      }
-      if (P.budget_ns > 0) {
-        if (tid == 0) S.flag = globaltimer_ns() - *P.t0 > P.budget_ns;
-        __syncthreads();
-        int late = S.flag;
-        __syncthreads();
-        if (late) { status = 6; break; }
-      }
-    }
-
-    if (status < 4 && e_at != iters) E = full_energy();  // the final energy of the run
-    // ---- 4. merge: scatter back to the caller's order
-    for (int pos = tid; pos < n; pos += T) {
-      int i = perm[pos];
-      PP v = xw[pos];
-      if (A::kId == 1) {
-        P.x32[D.off + i] = make_float2((float)v.x, (float)v.y);
-      } else {
-        P.x64[D.off + i] = make_double2((double)v.x, (double)v.y);
-        if (A::kId == 2) P.x32[D.off + i] = make_float2((float)v.x, (float)v.y);
-      }
-    }
-    if (tid == 0) {
-      if (A::kId == 1) {
-        O->iters32 = iters; O->status32 = status; O->E32 = (double)E; O->trials32 = trials;
-        O->iters = iters; O->status = status; O->E = (double)E; O->polished = 0;
-        O->builds = builds; O->changes = changes; O->trials = trials; O->resets = resets; O->stalls = stalls;
-      } else if (A::kId == 2) {
-        O->iters = O->iters32 + iters; O->status = status; O->E = (double)E; O->polished = 1;
-        O->builds += builds; O->changes += changes; O->trials += trials; O->resets += resets; O->stalls += stalls;
-      } else {
-        O->iters = iters; O->status = status; O->E = (double)E; O->polished = 0;
-        O->builds = builds; O->changes = changes; O->trials = trials; O->resets = resets; O->stalls = stalls;
-        O->iters32 = iters; O->trials32 = trials;
-      }
-    }
-    __syncthreads();
-  }
-}
-
-template <class A> cudaError_t set_smem(size_t bytes) {
-  return cudaFuncSetAttribute(descend_kernel<A, MaxT<A>::v>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-}
-
-}  // namespace
 
 __global__ void stamp_kernel(long long *t0) { *t0 = globaltimer_ns(); }
 
@@ -731,48 +25,31 @@ cudaError_t launch_stamp(long long *t0, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_descend(int arith, const DescendParams &p, int grid, int block, cudaStream_t s) {
+cudaError_t launch_descend(const DescendVariant &v, const DescendParams &p, int grid, int block, cudaStream_t s) {
   if (grid <= 0) return cudaSuccess;
-  const size_t sm = p.smem_bytes;
-  if (arith == 0) descend_kernel<Arith64, MaxT<Arith64>::v><<<grid, block, sm, s>>>(p);
-  else if (arith == 1) descend_kernel<Arith32, MaxT<Arith32>::v><<<grid, block, sm, s>>>(p);
-  else descend_kernel<ArithMix, MaxT<ArithMix>::v><<<grid, block, sm, s>>>(p);
-  return cudaGetLastError();
-}
-
-cudaError_t descend_prepare(int arith, size_t smem_bytes) {
-  if (arith == 0) return set_smem<Arith64>(smem_bytes);
-  if (arith == 1) return set_smem<Arith32>(smem_bytes);
-  return set_smem<ArithMix>(smem_bytes);
-}
-
-size_t descend_static_smem(int arith) {
-  if (arith == 0) return sizeof(Smem<Arith64>);
-  if (arith == 1) return sizeof(Smem<Arith32>);
-  return sizeof(Smem<ArithMix>);
-}
-
-cudaError_t descend_attributes(int arith, cudaFuncAttributes *attr) {
-  if (arith == 0) return cudaFuncGetAttributes(attr, descend_kernel<Arith64, MaxT<Arith64>::v>);
-  if (arith == 1) return cudaFuncGetAttributes(attr, descend_kernel<Arith32, MaxT<Arith32>::v>);
-  return cudaFuncGetAttributes(attr, descend_kernel<ArithMix, MaxT<ArithMix>::v>);
+  if (block > v.max_threads) return cudaErrorInvalidValue;
+  void *args[] = {(void *)&p};
+  return cudaLaunchKernel(v.fn, dim3(grid), dim3(block), args, p.smem_bytes, s);
 }
 
 int descend_max_block(int arith) { return arith == 1 ? 512 : 256; }
 
-cudaError_t descend_occupancy(int arith, int block, size_t smem, int *bps) {
-  if (arith == 0) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, descend_kernel<Arith64, MaxT<Arith64>::v>, block, smem);
-  if (arith == 1) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, descend_kernel<Arith32, MaxT<Arith32>::v>, block, smem);
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, descend_kernel<ArithMix, MaxT<ArithMix>::v>, block, smem);
+// Shared-memory bytes without a global fallback: the per-warp partials of the first reduction of
+// a batch step and the k batch rings.
+size_t descend_smem_mandatory(int arith, int k, int block) {
+  const size_t sc = arith == 0 ? 8 : 4;
+  auto al = [](size_t b) { return (b + 15) & ~size_t(15); };
+  return al(sc * (size_t)(block / 32) * kPA) + al(4 * (size_t)k * kRingInts);
 }
 
-// Shared-memory bytes the working set of an instance of n circles (k batches) asks for.
-size_t descend_smem_need(int arith, int n, int k, int ncx) {
+// Shared-memory bytes the working set of an instance of n circles (k batches) asks for, in the
+// order the kernel carves it.
+size_t descend_smem_need(int arith, int n, int k, int ncx, int block) {
   const size_t pos = arith == 1 ? 8 : 16, vec = arith == 0 ? 16 : 8, sc = arith == 0 ? 8 : 4;
   auto al = [](size_t b) { return (b + 15) & ~size_t(15); };
-  size_t b = al(pos * n) + 3 * al(vec * n) + al(4 * (size_t)(n + 1)) + al(2 * (size_t)(10 * n + 64)) + al(pos * n) +
-             al(sc * (size_t)k * kBasis * kBasis) + al(4 * (2 * (size_t)ncx * ncx + 2)) + 2 * al(4 * (size_t)n) +
-             al(pos * n);
+  size_t b = descend_smem_mandatory(arith, k, block) + al(sc * (size_t)k * kBasis * kBasis) + al(pos * n) +
+             al(4 * (size_t)(n + 1)) + al(2 * (size_t)(10 * n + 64)) + 3 * al(vec * n) + 2 * al(pos * n) +
+             al(4 * (2 * (size_t)ncx * ncx + 2)) + 2 * al(4 * (size_t)n);
   return b;
 }
 

@@ -82,13 +82,19 @@ cudaError_t launch_grid_descend(int arith, const DescendParams &p, int q, const 
                                 int block, cudaStream_t s);
 
 // Launchers (pecc_descend.cu).  arith: PECC_FP64 (plain), PECC_FP32 (bulk), PECC_FP32_POLISH64 (polish).
-cudaError_t launch_descend(int arith, const DescendParams &p, int grid, int block, cudaStream_t s);
-cudaError_t descend_attributes(int arith, cudaFuncAttributes *attr);
+// A compiled instance of the descent kernel: entry, launch bound (threads per block at most, and
+// the resident blocks per SM its register budget is sized for), static shared memory.
+struct DescendVariant {
+  const void *fn;
+  int max_threads, min_blocks;
+  size_t static_smem;
+};
+int descend_variants(int arith, const DescendVariant **v);  // largest register budget first
+int descend_variants32(const DescendVariant **v);
+cudaError_t launch_descend(const DescendVariant &v, const DescendParams &p, int grid, int block, cudaStream_t s);
 int descend_max_block(int arith);
-cudaError_t descend_occupancy(int arith, int block, size_t smem, int *blocks_per_sm);
-cudaError_t descend_prepare(int arith, size_t smem_bytes);
-size_t descend_static_smem(int arith);
-size_t descend_smem_need(int arith, int n, int k, int ncx);
+size_t descend_smem_need(int arith, int n, int k, int ncx, int block);
+size_t descend_smem_mandatory(int arith, int k, int block);
 
 // Standalone kernels (pecc_kernels.cu).
 struct StandaloneParams {
