@@ -47,9 +47,10 @@ size_t descend_smem_mandatory(int arith, int k, int block) {
 size_t descend_smem_need(int arith, int n, int k, int ncx, int block) {
   const size_t pos = arith == 1 ? 8 : 16, vec = arith == 0 ? 16 : 8, sc = arith == 0 ? 8 : 4;
   auto al = [](size_t b) { return (b + 15) & ~size_t(15); };
+  const size_t cells = 4 * (2 * (size_t)ncx * ncx + 2);
   size_t b = descend_smem_mandatory(arith, k, block) + al(sc * (size_t)k * kBasis * kBasis) + al(pos * n) +
-             al(4 * (size_t)(n + 1)) + al(2 * (size_t)(10 * n + 64)) + 3 * al(vec * n) + 2 * al(pos * n) +
-             al(4 * (2 * (size_t)ncx * ncx + 2)) + 2 * al(4 * (size_t)n);
+             al(4 * (size_t)(n + 1)) + al(2 * (size_t)(8 * n + 64)) + 3 * al(vec * n) + 2 * al(pos * n) +
+             (cells <= pos * (size_t)n ? 0 : al(cells));
   return b;
 }
 

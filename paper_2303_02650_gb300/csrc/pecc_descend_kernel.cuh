@@ -192,7 +192,7 @@ descend_kernel(DescendParams P) {
     PP *xw = cv.take<PP>(n, (PP *)P.xw + D.off);
     int32_t *rp = cv.take<int32_t>(n + 1, P.rp + D.rp_off);
     // neighbor indices are 16-bit inside the descent (instances of at most 65535 circles)
-    const int cap_s = min(D.cap, 10 * n + 64);
+    const int cap_s = min(D.cap, 8 * n + 64);  // about 5 neighbors per circle in practice
     uint16_t *col_s = cv.take<uint16_t>(cap_s, (uint16_t *)nullptr);
     uint16_t *const col_g = (uint16_t *)(P.col + D.col_off);  // 2 cap int32 = 4 cap uint16
     uint16_t *col = col_s ? col_s : col_g;
@@ -204,9 +204,16 @@ descend_kernel(DescendParams P) {
     PP *xb = cv.take<PP>(n, (PP *)P.xb + D.off);
     const CellGrid G = (A::kId == 1) ? CellGrid{D.R, D.inv_cs, (float)D.R, D.inv_f, D.ncx_f, true}
                                      : CellGrid{D.R, D.inv_cs, 0.f, 0.f, D.ncx, false};
-    int32_t *cells = cv.take<int32_t>(2 * (size_t)G.nc * G.nc + 2, P.cells + D.cell_off);
-    uint32_t *ckey = cv.take<uint32_t>(n, P.ckey + D.off);
-    int32_t *corder = cv.take<int32_t>(n, P.corder + D.off);
+    // The list builds' scratch lives in arrays that are dead while a build runs: the circles in
+    // cell order and their cell keys in the direction (8 n bytes at least), the cell table in the
+    // positions at the last build when it fits (they are rewritten right after every build).  The
+    // gradient arrays cannot serve: one-batch steps swap g and gt and carry a gradient across the
+    // build at the end of a sweep.
+    int32_t *corder = (int32_t *)dv;
+    uint32_t *ckey = (uint32_t *)dv + n;
+    const size_t ncells = 2 * (size_t)G.nc * G.nc + 2;
+    int32_t *cells = (ncells * sizeof(int32_t) <= (size_t)n * sizeof(PP)) ? (int32_t *)xb
+                                                                         : cv.take<int32_t>(ncells, P.cells + D.cell_off);
     VV *Sv = (VV *)P.S + (int64_t)mm * D.off;
     VV *Yv = (VV *)P.Y + (int64_t)mm * D.off;
     int32_t *perm = P.perm + D.off;
@@ -241,7 +248,6 @@ descend_kernel(DescendParams P) {
       else { float2 u = P.x32[D.off + i]; v.x = (pos_t)u.x; v.y = (pos_t)u.y; }
       bad |= !(isfinite((float)v.x) && isfinite((float)v.y));
       xw[p] = v;
-      xb[p] = v;
     }
     bad = __syncthreads_or(bad);
 
@@ -307,6 +313,7 @@ descend_kernel(DescendParams P) {
       if (!build()) status = 4;
       else {
         builds = 1;
+        for (int p = tid; p < n; p += T) xb[p] = xw[p];  // the cell table of the build used xb
         hcur = S.hash;
         E = full_energy();
         if (!isfinite(E)) status = 5;
