@@ -115,6 +115,11 @@ typedef struct {
     int32_t smem_per_block; /* bytes of dynamic shared memory per instance block at most (the rest
                                of the working set stays in global memory and the SM's L1 keeps the
                                room); 0 = the block's whole share of the SM */
+    double polish_stall_rel;      /* the FP64 polish ends (status STALLED) when E fell by less than
+                                     polish_stall_rel (relative) over polish_stall_window sweeps: a
+                                     polish that stagnates above zero energy is at a jammed local
+                                     minimum; 1e-2 */
+    int32_t polish_stall_window;  /* sweeps per stagnation check of the polish; 100 (0 = off) */
 } pecc_config;
 
 /* Fill *cfg with the defaults listed above (num_instances = 0, n = NULL). */

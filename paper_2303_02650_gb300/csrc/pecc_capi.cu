@@ -149,6 +149,8 @@ void pecc_config_default(pecc_config *c) {
   c->stall_rel = 1e-3;
   c->stall_window = 10;
   c->polish_k = 1;
+  c->polish_stall_rel = 1e-2;
+  c->polish_stall_window = 100;
 }
 
 static int default_k(int n) { return n < 300 ? 1 : (n < 500 ? 3 : 5); }
@@ -173,6 +175,8 @@ pecc_status pecc_create(const pecc_config *cfg, void *stream, pecc_ctx **out) {
   if (cfg->init_mode < 0 || cfg->init_mode > 1) return fail(nullptr, PECC_ERR_ARG, "bad init_mode");
   if (!(cfg->nbr_capacity >= 1.0)) return fail(nullptr, PECC_ERR_ARG, "nbr_capacity must be >= 1");
   if (cfg->stall_window < 0 || !(cfg->stall_rel >= 0.0)) return fail(nullptr, PECC_ERR_ARG, "bad stall rule");
+  if (cfg->polish_stall_window < 0 || !(cfg->polish_stall_rel >= 0.0))
+    return fail(nullptr, PECC_ERR_ARG, "bad polish stall rule");
   if (cfg->polish_k < 0 || cfg->polish_k > kMaxK) return fail(nullptr, PECC_ERR_ARG, "polish_k must be in 0..64");
   if (cfg->smem_per_block < 0) return fail(nullptr, PECC_ERR_ARG, "smem_per_block must be >= 0");
   if (cfg->block_threads != 0 && (cfg->block_threads < 32 || cfg->block_threads % 32 ||
@@ -593,8 +597,8 @@ static DescendParams dparams(pecc_ctx *c, int phase) {
   p.l_cut = f.l_cut; p.rebuild_disp = f.rebuild_disp; p.step_max = f.step_max;
   p.e_tol = f.e_tol; p.gsum_tol = f.gsum_tol; p.c1 = f.c1; p.curv_eps = f.curv_eps; p.polish_gate = f.polish_gate;
   p.m = f.lbfgs_m; p.max_iter = f.max_iter; p.max_trials = f.max_trials; p.anm = f.anm; p.partition = f.partition;
-  p.stall_rel = f.stall_rel;
-  p.stall_window = f.stall_window;
+  p.stall_rel = (phase == 2) ? f.polish_stall_rel : f.stall_rel;
+  p.stall_window = (phase == 2) ? f.polish_stall_window : f.stall_window;
   p.t0 = c->t0;
   p.budget_ns = f.time_budget_ns;
   p.k_override = (phase == 2) ? f.polish_k : 0;

@@ -674,8 +674,9 @@ descend_kernel(DescendParams P) {
       if (E <= (acc_t)P.e_tol) { status = 0; break; }
       if (gsum <= gsum_tol) { status = 1; break; }
       if (!moved) { status = 2; break; }
-      // FP32 phase: binary32 has reached its resolution when E stops falling; hand over
-      if (A::kId == 1 && P.stall_window > 0 && iters % P.stall_window == 0) {
+      // FP32 phase: binary32 has reached its resolution when E stops falling, hand over; polish: a
+      // run whose E stops falling above zero sits at a jammed local minimum
+      if (A::kId != 0 && P.stall_window > 0 && iters % P.stall_window == 0) {
         if (E > Ewin * (acc_t)(1.0 - P.stall_rel)) { status = 2; break; }
         Ewin = E;
       }

@@ -675,7 +675,8 @@ __global__ void __launch_bounds__(256, 1) descend_grid_kernel(DescendParams P, i
     if (E <= (acc_t)P.e_tol) { status = 0; break; }
     if (gsum <= gsum_tol) { status = 1; break; }
     if (!moved) { status = 2; break; }
-    if (A::kId == 1 && P.stall_window > 0 && iters % P.stall_window == 0) {
+    // stagnation: the FP32 phase hands over, the polish stops at a jammed local minimum
+    if (A::kId != 0 && P.stall_window > 0 && iters % P.stall_window == 0) {
       if (E > Ewin * (acc_t)(1.0 - P.stall_rel)) { status = 2; break; }
       Ewin = E;
     }

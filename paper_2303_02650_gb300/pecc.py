@@ -36,7 +36,8 @@ class Config(C.Structure):
                 ("feas_tol", C.c_double), ("nbr_capacity", C.c_double), ("time_budget_ns", C.c_int64),
                 ("block_threads", C.c_int32), ("blocks_per_sm", C.c_int32), ("stall_rel", C.c_double),
                 ("stall_window", C.c_int32), ("polish_k", C.c_int32),
-                ("smem_per_block", C.c_int32)]
+                ("smem_per_block", C.c_int32), ("polish_stall_rel", C.c_double),
+                ("polish_stall_window", C.c_int32)]
 
 
 _lib = None
