@@ -160,6 +160,18 @@ def algorithmic_bytes_descent(n, k, iters, trials, m, vec_bytes=8):
     return float(np.sum(n * iters * per_sweep) + np.sum(n / k * trials * 44.0))
 
 
+def combine_ranks(dist, ms, count, device):
+    """Whole-job figures of a multi-rank run: the slowest rank's time (max) and the total count
+    over ranks (sum).  The only collective of the bench; the descent itself exchanges nothing."""
+    import torch
+
+    t = torch.tensor([float(ms)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    c = torch.tensor([int(count)], device=device, dtype=torch.int64)
+    dist.all_reduce(c)
+    return float(t.item()), int(c.item())
+
+
 def run_ours(args, rank, world, local):
     import torch
 
@@ -261,12 +273,7 @@ def run_ours(args, rank, world, local):
     ms_total = e0.elapsed_time(e1)
     feasible = int(feas_sum.item())
     if dist:
-        t = torch.tensor([ms_total], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
-        f = torch.tensor([feasible], device="cuda", dtype=torch.int64)
-        dist.all_reduce(f)
-        feasible = int(f.item())
+        ms_total, feasible = combine_ranks(dist, ms_total, feasible, "cuda")
     value = feasible / (ms_total / 1e3)
     solved = sum(int(n.size) for _ in range(args.steps)) * world
 

@@ -314,6 +314,18 @@ pecc_status pecc_warm_start(pecc_ctx *ctx, pecc_mlp *mlp, int32_t rounds, int32_
 pecc_status pecc_check_feasible_noalloc(const double *xy_dev, int32_t n, double R, double l_cut, double tol,
                                         uint8_t *feasible_dev, double *max_overlap_dev, void *stream);
 
+/* Self-test of the bounded wait of the grid barrier that the whole-GPU descent of large instances
+ * uses (the wait is measured on %globaltimer; past its limit the waiting block raises an error
+ * flag that every block sees, and the descent ends with status 6).  Four blocks wait at a barrier
+ * that expects a fifth, so no arrival releases it; every wait must end by itself after
+ * timeout_ns.  Runs on the current device and the legacy default stream; synchronises.
+ *   timeout_ns        the wait limit to test (> 0, at most 10 s)
+ *   failed_host       host int32[1]: 1 when the barrier reported the failed wait, else 0
+ *   waited_ns_host    host int64[1]: how long block 0 waited
+ * Returns PECC_ERR_ARG for a bad argument, PECC_ERR_CUDA (message in pecc_last_error(NULL)) if
+ * the launch or a copy failed. */
+pecc_status pecc_selftest_grid_barrier(int64_t timeout_ns, int32_t *failed_host, int64_t *waited_ns_host);
+
 /* Text of the last error on this context (or of the last failed pecc_create when ctx is NULL). */
 const char *pecc_last_error(pecc_ctx *ctx);
 

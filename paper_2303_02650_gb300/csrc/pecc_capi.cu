@@ -346,6 +346,18 @@ pecc_status pecc_destroy(pecc_ctx *ctx) {
   return PECC_OK;
 }
 
+pecc_status pecc_selftest_grid_barrier(int64_t timeout_ns, int32_t *failed_host, int64_t *waited_ns_host) {
+  if (!failed_host || !waited_ns_host || timeout_ns <= 0 || timeout_ns > 10000000000ll)
+    return fail(nullptr, PECC_ERR_ARG, "pecc_selftest_grid_barrier: bad argument");
+  int f = 0;
+  long long w = 0;
+  cudaError_t e = selftest_grid_barrier((long long)timeout_ns, &f, &w);
+  if (e != cudaSuccess) return fail(nullptr, PECC_ERR_CUDA, "pecc_selftest_grid_barrier: %s", cudaGetErrorString(e));
+  *failed_host = f;
+  *waited_ns_host = w;
+  return PECC_OK;
+}
+
 const char *pecc_last_error(pecc_ctx *ctx) { return ctx ? ctx->err.c_str() : g_create_err.c_str(); }
 
 static void cell_grid(double R, double l_cut, int n, double *inv, int *nc, double margin = 1.0 / 1048576.0) {

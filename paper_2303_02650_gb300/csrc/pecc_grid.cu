@@ -29,8 +29,9 @@ constexpr long long kBarrierTimeoutNs = 2000000000ll;
 __device__ __forceinline__ unsigned ldv(const unsigned *p) { return *(volatile const unsigned *)p; }
 __device__ __forceinline__ int ldv(const int *p) { return *(volatile const int *)p; }
 
-// Grid barrier; false (for the whole block) once any block's wait has timed out.
-__device__ bool grid_sync(GridCtl *c) {
+// Grid barrier for `expected` arriving blocks; false (for the whole block) once any block's wait
+// has run past timeout_ns (measured on %globaltimer) and raised the shared error flag.
+__device__ bool grid_sync_n(GridCtl *c, unsigned expected, long long timeout_ns) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -38,7 +39,7 @@ __device__ bool grid_sync(GridCtl *c) {
     __threadfence();
     const unsigned arrived = atomicAdd(&c->count, 1u) + 1u;
     int good = 1;
-    if (arrived == gridDim.x) {
+    if (arrived == expected) {
       atomicExch(&c->count, 0u);
       __threadfence();
       atomicAdd(&c->gen, 1u);
@@ -46,7 +47,7 @@ __device__ bool grid_sync(GridCtl *c) {
       const long long t0 = globaltimer_ns();
       while (ldv(&c->gen) == g) {
         if (ldv(&c->err)) { good = 0; break; }
-        if (globaltimer_ns() - t0 > kBarrierTimeoutNs) { atomicExch(&c->err, 1); good = 0; break; }
+        if (globaltimer_ns() - t0 > timeout_ns) { atomicExch(&c->err, 1); good = 0; break; }
         __nanosleep(64);
       }
     }
@@ -56,6 +57,8 @@ __device__ bool grid_sync(GridCtl *c) {
   __syncthreads();
   return ok;
 }
+
+__device__ __forceinline__ bool grid_sync(GridCtl *c) { return grid_sync_n(c, gridDim.x, kBarrierTimeoutNs); }
 
 template <class A> struct GSmem {
   using vec_t = typename A::vec_t;
@@ -731,7 +734,39 @@ template <class A> cudaError_t coop_launch(const DescendParams &p, int q, const 
   return cudaLaunchCooperativeKernel((void *)descend_grid_kernel<A>, dim3(grid), dim3(block), args, 0, s);
 }
 
+// Self-test of the bounded wait: every block waits at a barrier that expects one block more than
+// the grid has, so no arrival releases it; each wait must end by its time limit with the error
+// flag raised.  Block 0 reports whether it saw the barrier fail and how long it waited.
+__global__ void barrier_selftest_kernel(GridCtl *c, long long timeout_ns, int *failed, long long *waited) {
+  const long long t0 = globaltimer_ns();
+  const bool ok = grid_sync_n(c, gridDim.x + 1u, timeout_ns);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    *failed = ok ? 0 : 1;
+    *waited = globaltimer_ns() - t0;
+  }
+}
+
 }  // namespace
+
+cudaError_t selftest_grid_barrier(long long timeout_ns, int *failed_host, long long *waited_host) {
+  GridCtl *c = nullptr;
+  int *f = nullptr;
+  long long *w = nullptr;
+  cudaError_t e = cudaMalloc(&c, sizeof(GridCtl));
+  if (e == cudaSuccess) e = cudaMalloc(&f, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&w, sizeof(long long));
+  if (e == cudaSuccess) e = cudaMemset(c, 0, sizeof(GridCtl));
+  if (e == cudaSuccess) {
+    barrier_selftest_kernel<<<4, 32>>>(c, timeout_ns, f, w);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(failed_host, f, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(waited_host, w, sizeof(long long), cudaMemcpyDeviceToHost);
+  cudaFree(c);
+  cudaFree(f);
+  cudaFree(w);
+  return e;
+}
 
 cudaError_t grid_descend_occupancy(int arith, int block, int *bps) {
   if (arith == 0) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, descend_grid_kernel<Arith64>, block, 0);

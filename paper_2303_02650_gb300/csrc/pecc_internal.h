@@ -78,6 +78,8 @@ struct GridBufs {
 };
 constexpr int kGridMinN = 16384;  // instances this large descend on the whole GPU
 cudaError_t grid_descend_occupancy(int arith, int block, int *blocks_per_sm);
+// Bounded-wait self-test of the grid barrier (synchronous, default stream).
+cudaError_t selftest_grid_barrier(long long timeout_ns, int *failed_host, long long *waited_host);
 cudaError_t launch_grid_descend(int arith, const DescendParams &p, int q, const GridBufs &g, GridCtl *c, int grid,
                                 int block, cudaStream_t s);
 

@@ -48,7 +48,7 @@ _EXPORTS = ["pecc_config_default", "pecc_create", "pecc_destroy", "pecc_set_radi
             "pecc_get_counters", "pecc_get_launch", "pecc_last_error", "pecc_get_stats", "pecc_phase_times",
             "pecc_check_feasible_noalloc", "pecc_mlp_num_params", "pecc_mlp_create", "pecc_mlp_destroy",
             "pecc_mlp_get_params", "pecc_mlp_set_params", "pecc_mlp_forward", "pecc_mlp_grad", "pecc_mlp_train_step",
-            "pecc_features", "pecc_targets", "pecc_warm_start", "pecc_autotune"]
+            "pecc_features", "pecc_targets", "pecc_warm_start", "pecc_autotune", "pecc_selftest_grid_barrier"]
 NOALLOC_MAX_N = 4096
 
 
@@ -94,6 +94,7 @@ def load(build_if_missing: bool = True):
         "pecc_get_stats": (st, [vp, vp]),
         "pecc_phase_times": (st, [vp, C.POINTER(C.c_float)]),
         "pecc_check_feasible_noalloc": (st, [vp, C.c_int32, C.c_double, C.c_double, C.c_double, vp, vp, vp]),
+        "pecc_selftest_grid_barrier": (st, [C.c_int64, C.POINTER(C.c_int32), C.POINTER(C.c_int64)]),
         "pecc_mlp_num_params": (C.c_int32, []),
         "pecc_mlp_create": (st, [C.c_uint64, vp, C.POINTER(vp)]),
         "pecc_mlp_destroy": (st, [vp]),
@@ -129,6 +130,16 @@ def _ptr(t):
     if t is None:
         return None
     return C.c_void_p(t.data_ptr())
+
+
+def selftest_grid_barrier(timeout_ns=50_000_000):
+    """pecc_selftest_grid_barrier: (failed, waited_ns) of a grid barrier that nothing releases."""
+    L = load()
+    f, w = C.c_int32(), C.c_int64()
+    rc = L.pecc_selftest_grid_barrier(int(timeout_ns), C.byref(f), C.byref(w))
+    if rc != 0:
+        raise PeccError(f"pecc_selftest_grid_barrier: {ERRORS.get(rc, rc)}: {L.pecc_last_error(None).decode()}")
+    return f.value, w.value
 
 
 def check_feasible_noalloc(xy, R, l_cut=2.5, tol=1e-9, stream=None):

@@ -65,3 +65,19 @@ def test_mixed_small_and_large_instances(orc):
         assert float(mo.cpu()[q]) == orc.max_overlap(x, float(R[q]))[0]
     assert int(iters.cpu()[1]) > 0
     assert feas.cpu().numpy().sum() >= 2
+
+
+def test_grid_barrier_wait_is_bounded(orc):
+    """The grid barrier of the whole-GPU descent never waits past its limit: at a barrier that
+    nothing releases, every block's wait ends by itself (%globaltimer), the error flag is seen,
+    and the device stays usable for the next descent."""
+    torch, pecc = need_gpu()
+    failed, waited = pecc.selftest_grid_barrier(50_000_000)
+    assert failed == 1
+    assert 50_000_000 <= waited < 2_000_000_000
+    n = np.array([300], dtype=np.int32)
+    R = np.array([synth.radius(300, 0.8)])
+    with _ctx(pecc, n, R, precision=0, max_iter=2) as c:
+        c.init_random(5)
+        iters, status = c.descend()
+        assert int(iters.cpu()[0]) == 2 and int(status.cpu()[0]) == 3

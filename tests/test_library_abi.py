@@ -65,3 +65,12 @@ def test_create_rejects_bad_arguments_without_gpu(libpath):
         h = ctypes.c_void_p()
         assert L.pecc_create(ctypes.byref(c), None, ctypes.byref(h)) == 1, field
         assert not h.value
+
+
+def test_barrier_selftest_rejects_bad_arguments_without_gpu(libpath):
+    from paper_2303_02650_gb300 import pecc
+
+    L = pecc.load()
+    f, w = ctypes.c_int32(), ctypes.c_int64()
+    for t in (0, -5, 20_000_000_000):
+        assert L.pecc_selftest_grid_barrier(t, ctypes.byref(f), ctypes.byref(w)) == 1
