@@ -149,15 +149,16 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def algorithmic_bytes_descent(n, k, iters, trials, m, vec_bytes=8):
-    """Algorithmic DRAM bytes of the first-phase descent kernel (per launch).
-    Per circle and sweep: one fused energy + gradient pass (read x 8 B, row pointer 4 B, about 6
-    neighbor indices 24 B, write g 8 B = 44 B), the quasi-Newton direction over the m stored
-    pairs (read 4 m vectors of vec_bytes), the new pair (write s, y: 2 vec_bytes).  Per line-search
-    trial: one fused pass over the batch's n/k circles (44 B each)."""
+def algorithmic_bytes_descent(n, k, iters, trials, m, vec_bytes=8, pos_bytes=8):
+    """Algorithmic DRAM bytes of a descent phase (per launch).
+    Per circle and sweep: one fused energy + gradient pass (read x pos_bytes, row pointer 4 B, about
+    6 neighbor indices 24 B, write g vec_bytes: 44 B in FP32), the quasi-Newton direction over the
+    m stored pairs (read 4 m vectors of vec_bytes), the new pair (write s, y: 2 vec_bytes).  Per
+    line-search trial: one fused pass over the batch's n/k circles."""
     n = n.astype(np.float64)
-    per_sweep = 44.0 + 4 * m * vec_bytes + 2 * vec_bytes
-    return float(np.sum(n * iters * per_sweep) + np.sum(n / k * trials * 44.0))
+    pass_b = pos_bytes + 4 + 24 + vec_bytes
+    per_sweep = pass_b + 4 * m * vec_bytes + 2 * vec_bytes
+    return float(np.sum(n * iters * per_sweep) + np.sum(n / k * trials * pass_b))
 
 
 def combine_ranks(dist, ms, count, device):
@@ -219,6 +220,7 @@ def run_ours(args, rank, world, local):
     big = bool(np.any(n >= 16384))
     feas_sum = torch.zeros((), dtype=torch.int64, device="cuda")
     phase_ms, phase_bytes, phase2_ms, split_ms = [], [], [], []
+    fused = prec == 2 and not big and bool(ctx.cfg.fuse_phases)
     it_all, st_all, tr_all = [], [], []
 
     def timed_step(s, ev, keep):
@@ -238,7 +240,10 @@ def run_ours(args, rank, world, local):
             return
         phase_ms.append(ms[0])
         phase2_ms.append(ms[1])
-        phase_bytes.append(algorithmic_bytes_descent(n, kvec, st[:, 8], st[:, 9], 10, 16 if prec == 0 else 8))
+        b = algorithmic_bytes_descent(n, kvec, st[:, 8], st[:, 9], 10, 16 if prec == 0 else 8, 16 if prec == 0 else 8)
+        if fused:  # the polish runs in the same kernel: one batch, binary64 coordinates
+            b += algorithmic_bytes_descent(n, np.ones_like(kvec), st[:, 0] - st[:, 8], st[:, 4] - st[:, 9], 10, 8, 16)
+        phase_bytes.append(b)
         it_all.append(st[:, 0])
         st_all.append(st[:, 1])
         tr_all.append(st[:, 4])
@@ -332,8 +337,9 @@ def run_ours(args, rank, world, local):
         "step_gaps_ms": gaps,
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                      "frac": round(achieved / hbm, 4), "traffic": None,
-                     "kernel": ("descend_grid_kernel" if big else "descend_kernel") +
-                               ("<Arith64>" if prec == 0 else "<Arith32> (FP32 bulk phase)"),
+                     "kernel": ("descend_fused_kernel (FP32 descent + FP64 polish per instance)" if fused else
+                                ("descend_grid_kernel" if big else "descend_kernel") +
+                                ("<Arith64>" if prec == 0 else "<Arith32> (FP32 bulk phase)")),
                      "peak_kind": peak_kind, "avg_launch_ms": round(dom_ms, 3),
                      "algorithmic_bytes_per_launch": dom_bytes,
                      "polish_kernel_ms": round(float(np.mean(phase2_ms)), 3)},

@@ -120,6 +120,10 @@ typedef struct {
                                      polish that stagnates above zero energy is at a jammed local
                                      minimum; 1e-2 */
     int32_t polish_stall_window;  /* sweeps per stagnation check of the polish; 100 (0 = off) */
+    int32_t fuse_phases;    /* PECC_FP32_POLISH64: 1 = each instance's FP32 descent and polish run
+                               back to back in one block of one kernel (long polishes overlap other
+                               instances' descents; pecc_phase_times then reports the fused kernel
+                               as the first phase and 0 for the polish), 0 = two kernels; 0 */
 } pecc_config;
 
 /* Fill *cfg with the defaults listed above (num_instances = 0, n = NULL). */

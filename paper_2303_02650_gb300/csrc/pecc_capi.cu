@@ -43,7 +43,8 @@ struct pecc_ctx {
   bool radius_set = false;
   int lists_prec = -1;  // precision of the standalone lists: 0 FP64, 1 FP32
   int block = 0, bps = 0, grid = 0, block_build = 256;
-  struct Launch { int block = 0, bps = 0, grid = 0, var = 0; size_t smem = 0; } lc[3];  // per arithmetic
+  // per arithmetic (0 FP64, 1 FP32, 2 polish) and 3 = FP32 descent + polish fused in one kernel
+  struct Launch { int block = 0, bps = 0, grid = 0, var = 0; size_t smem = 0; } lc[4];
   bool lc_ready = false;
   bool tuned = false;  // launch shapes chosen by pecc_autotune
   int tuned_block = 0, tuned_bps = 0;
@@ -151,6 +152,7 @@ void pecc_config_default(pecc_config *c) {
   c->polish_k = 1;
   c->polish_stall_rel = 1e-2;
   c->polish_stall_window = 100;
+  c->fuse_phases = 0;
 }
 
 static int default_k(int n) { return n < 300 ? 1 : (n < 500 ? 3 : 5); }
@@ -540,10 +542,12 @@ static pecc_status plan_launch(pecc_ctx *ctx, int arith, int block = 0, int bps_
   for (int q = 0; q < ctx->num; ++q) {
     const InstDesc &D = ctx->desc_h[q];
     if (D.big) continue;
-    int k = D.k;
-    if (arith == 2 && ctx->cfg.polish_k > 0) k = std::min(ctx->cfg.polish_k, D.k);
-    need = std::max(need, descend_smem_need(arith, D.n, k, arith == 1 ? D.ncx_f : D.ncx, blk));
-    mand = std::max(mand, descend_smem_mandatory(arith, k, blk));
+    for (int a = (arith == 3 ? 1 : arith); a <= (arith == 3 ? 2 : arith); ++a) {  // fused: both phases
+      int k = D.k;
+      if (a == 2 && ctx->cfg.polish_k > 0) k = std::min(ctx->cfg.polish_k, D.k);
+      need = std::max(need, descend_smem_need(a, D.n, k, a == 1 ? D.ncx_f : D.ncx, blk));
+      mand = std::max(mand, descend_smem_mandatory(a, k, blk));
+    }
   }
   if (bps_target <= 0) bps_target = ctx->cfg.blocks_per_sm;
   const bool fixed = bps_target > 0;  // else as many blocks per SM as fit
@@ -629,6 +633,14 @@ static cudaError_t enqueue_descend(pecc_ctx *c) {
     if ((e = cudaEventRecordWithFlags(c->ev[1], c->stream, cudaEventRecordExternal))) return e;
     return cudaEventRecordWithFlags(c->ev[2], c->stream, cudaEventRecordExternal);
   }
+  if (c->cfg.precision == PECC_FP32_POLISH64 && c->cfg.fuse_phases) {
+    DescendParams p32 = dparams(c, 1), p64 = dparams(c, 2);
+    p64.max_iter = c->cfg.polish_max_iter;
+    p32.smem_bytes = p64.smem_bytes = c->lc[3].smem;
+    if ((e = launch_descend_fused(variant_of(c, 3), p32, p64, c->lc[3].grid, c->lc[3].block, c->stream))) return e;
+    if ((e = cudaEventRecordWithFlags(c->ev[1], c->stream, cudaEventRecordExternal))) return e;
+    return cudaEventRecordWithFlags(c->ev[2], c->stream, cudaEventRecordExternal);
+  }
   if ((e = launch_descend(variant_of(c, 1), dparams(c, 1), c->lc[1].grid, c->lc[1].block, c->stream))) return e;
   if ((e = cudaEventRecordWithFlags(c->ev[1], c->stream, cudaEventRecordExternal))) return e;
   if (c->cfg.precision == PECC_FP32_POLISH64) {
@@ -651,6 +663,8 @@ pecc_status pecc_descend(pecc_ctx *ctx, int32_t *iters_dev, int32_t *status_dev)
     const int tb = ctx->tuned ? ctx->tuned_block : 0, tt = ctx->tuned ? ctx->tuned_bps : 0;
     if (pr == PECC_FP64) {
       if ((s = plan_launch(ctx, 0, tb, tt))) return s;
+    } else if (pr == PECC_FP32_POLISH64 && ctx->cfg.fuse_phases) {
+      if ((s = plan_launch(ctx, 3, tb > 0 ? std::min(tb, 256) : 0, tt))) return s;
     } else {
       if ((s = plan_launch(ctx, 1, tb, tt))) return s;
       if (pr == PECC_FP32_POLISH64 && (s = plan_launch(ctx, 2, tb > 0 ? std::min(tb, 256) : 0, tt))) return s;
@@ -718,6 +732,7 @@ pecc_status pecc_autotune(pecc_ctx *ctx, int32_t sweeps, uint64_t seed, int32_t 
   if (sweeps < 1) return fail(ctx, PECC_ERR_ARG, "sweeps must be >= 1");
   if (ctx->num == 0) return PECC_OK;
   const int arith = ctx->cfg.precision == PECC_FP64 ? 0 : 1;
+  const int plan_arith = (ctx->cfg.precision == PECC_FP32_POLISH64 && ctx->cfg.fuse_phases) ? 3 : arith;
   // keep the caller's coordinates (both copies, bit for bit) and restore them afterwards
   const size_t b64 = sizeof(double2) * (size_t)ctx->total, b32 = ctx->x32 ? sizeof(float2) * (size_t)ctx->total : 0;
   char *saved = nullptr;
@@ -739,7 +754,7 @@ pecc_status pecc_autotune(pecc_ctx *ctx, int32_t sweeps, uint64_t seed, int32_t 
   pecc_status err = PECC_OK;
   for (int bi = 0; bi < 3 && !err; ++bi) {
     for (int ti = 0; ti < 5 && !err; ++ti) {
-      if (blocks[bi] > descend_max_block(arith)) continue;
+      if (blocks[bi] > descend_max_block(plan_arith)) continue;  // shapes the planned kernel can run
       if ((err = plan_launch(ctx, arith, blocks[bi], targets[ti]))) break;
       if (ctx->lc[arith].bps < targets[ti]) continue;  // that many blocks do not fit an SM
       ctx->lc_ready = true;
@@ -809,7 +824,8 @@ pecc_status pecc_phase_times(pecc_ctx *ctx, float *ms_host) {
 
 pecc_status pecc_get_launch(pecc_ctx *ctx, int32_t *block_threads, int32_t *blocks_per_sm, int32_t *grid) {
   if (!ctx) return PECC_ERR_ARG;
-  const int a = ctx->cfg.precision == PECC_FP64 ? 0 : 1;
+  const int a = ctx->cfg.precision == PECC_FP64 ? 0
+                : (ctx->cfg.precision == PECC_FP32_POLISH64 && ctx->cfg.fuse_phases ? 3 : 1);
   if (block_threads) *block_threads = ctx->lc[a].block;
   if (blocks_per_sm) *blocks_per_sm = ctx->lc[a].bps;
   if (grid) *grid = ctx->lc[a].grid;

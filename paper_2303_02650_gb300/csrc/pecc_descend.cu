@@ -14,6 +14,7 @@ static const DescendVariant kVarMix[] = {descend_variant<ArithMix, 256, 2>(), de
 int descend_variants(int arith, const DescendVariant **v) {
   if (arith == 0) { *v = kVar64; return (int)(sizeof(kVar64) / sizeof(kVar64[0])); }
   if (arith == 1) return descend_variants32(v);
+  if (arith == 3) return descend_variants_fused(v);
   *v = kVarMix;
   return (int)(sizeof(kVarMix) / sizeof(kVarMix[0]));
 }

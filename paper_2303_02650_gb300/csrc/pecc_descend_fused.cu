@@ -1,0 +1,23 @@
+// pecc_descend_fused.cu -- the fused instances of the descent kernel: the FP32 descent and the FP64
+// polish of each instance back to back in one block (own translation unit, compiled in parallel).
+#include "pecc_descend_kernel.cuh"
+
+namespace pecc {
+
+// 128 registers (two 256-thread or four 128-thread blocks per SM) and 96 (five 128-thread blocks).
+static const DescendVariant kVarFused[] = {descend_fused_variant<256, 2>(), descend_fused_variant<128, 5>()};
+
+int descend_variants_fused(const DescendVariant **v) {
+  *v = kVarFused;
+  return (int)(sizeof(kVarFused) / sizeof(kVarFused[0]));
+}
+
+cudaError_t launch_descend_fused(const DescendVariant &v, const DescendParams &p32, const DescendParams &p64, int grid,
+                                 int block, cudaStream_t s) {
+  if (grid <= 0) return cudaSuccess;
+  if (block > v.max_threads) return cudaErrorInvalidValue;
+  void *args[] = {(void *)&p32, (void *)&p64};
+  return cudaLaunchKernel(v.fn, dim3(grid), dim3(block), args, p32.smem_bytes, s);
+}
+
+}  // namespace pecc

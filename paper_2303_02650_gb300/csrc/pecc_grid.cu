@@ -161,8 +161,8 @@ __global__ void __launch_bounds__(256, 1) descend_grid_kernel(DescendParams P, i
     }
   }
   const int k = (P.k_override > 0) ? min(P.k_override, D.k) : D.k;
-  PP *xw = (PP *)P.xw + D.off, *xb = (PP *)P.xb + D.off, *xo = (PP *)P.xo + D.off;
-  VV *g = (VV *)P.g + D.off, *gt = (VV *)P.gt + D.off, *dv = (VV *)P.d + D.off;
+  PP *xw = (PP *)((double2 *)P.xw + D.off), *xb = (PP *)((double2 *)P.xb + D.off), *xo = (PP *)((double2 *)P.xo + D.off);
+  VV *g = (VV *)((double2 *)P.g + D.off), *gt = (VV *)((double2 *)P.gt + D.off), *dv = (VV *)((double2 *)P.d + D.off);
   VV *Sv = (VV *)P.S + (int64_t)mm * D.off, *Yv = (VV *)P.Y + (int64_t)mm * D.off;
   int32_t *perm = P.perm + D.off;
   uint64_t *skey = P.skey + D.off;

@@ -93,6 +93,9 @@ struct DescendVariant {
 };
 int descend_variants(int arith, const DescendVariant **v);  // largest register budget first
 int descend_variants32(const DescendVariant **v);
+int descend_variants_fused(const DescendVariant **v);  // arith 3: FP32 descent + polish in one block
+cudaError_t launch_descend_fused(const DescendVariant &v, const DescendParams &p32, const DescendParams &p64, int grid,
+                                 int block, cudaStream_t s);
 cudaError_t launch_descend(const DescendVariant &v, const DescendParams &p, int grid, int block, cudaStream_t s);
 int descend_max_block(int arith);
 size_t descend_smem_need(int arith, int n, int k, int ncx, int block);

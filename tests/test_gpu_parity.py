@@ -309,6 +309,33 @@ def test_descend_launch_shapes(orc, block):
     assert abs(int(out["feasible"].sum()) - int(ref["feasible"].sum())) <= 5
 
 
+@pytest.mark.parametrize("num,bps,smem", [(21, 0, 0), (600, 1, 8192)])
+def test_fused_phases_equal_two_kernels(orc, num, bps, smem):
+    """The fused kernel (each instance's FP32 descent and polish back to back in one block) runs
+    the same arithmetic in the same order as the two-kernel path: with the same threads per block
+    the final coordinates, statuses and sweep counts are identical bit for bit.  The second case
+    puts about four instances on each block and caps shared memory at 8 KB, so the working sets
+    live in global memory while FP32 phases and polishes of different instances run at once."""
+    torch, pecc = need_gpu()
+    if num == 21:
+        n = np.array([120, 200, 299, 300, 420, 640, 1000] * 3, dtype=np.int32)
+        R = _radii(n, 0.80)
+    else:
+        n, R = synth.batch_manifest(num, seed=44)
+    outs = []
+    for fuse in (1, 0):
+        with _ctx(pecc, n, R, precision=2, block_threads=128, blocks_per_sm=bps, smem_per_block=smem,
+                  fuse_phases=fuse) as c:
+            c.init_random(17)
+            iters, status = c.descend()
+            outs.append((c.get_positions().cpu().numpy(), iters.cpu().numpy(), status.cpu().numpy(),
+                         c.get_stats().cpu().numpy(), c.get_energy().cpu().numpy()))
+            ms = c.phase_times()
+            assert (ms[1] < 0.05) == bool(fuse)  # fused: the polish event follows the kernel at once
+    for a, b in zip(outs[0], outs[1]):
+        np.testing.assert_array_equal(a, b)
+
+
 def test_autotune_restores_coordinates_and_descends(orc):
     """pecc_autotune times short descents at every launch shape, then hands the caller back its
     coordinates bit for bit; the descent that follows runs at the chosen shape with the same
