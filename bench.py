@@ -194,6 +194,8 @@ def run_ours(args, rank, world, local):
         shape = dict(block_threads=b, blocks_per_sm=t)
     if args.smem_kb:
         shape["smem_per_block"] = int(args.smem_kb * 1024)
+    if args.fuse >= 0:
+        shape["fuse_phases"] = args.fuse
     ctx = pecc.Context(n, precision=prec, **shape)
     ctx.set_radius(R)
     tuned = None
@@ -507,6 +509,8 @@ def main():
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shape")
+    ap.add_argument("--fuse", type=int, default=-1, choices=[-1, 0, 1],
+                    help="FP32 descent and polish in one kernel (1) or two (0); -1 = the library default")
     ap.add_argument("--smem-kb", type=float, default=0, help="dynamic shared memory per instance block at most (KB)")
     ap.add_argument("--launch", default="", help="fixed launch shape THREADSxBLOCKS_PER_SM (no autotune), e.g. 128x4")
     ap.add_argument("--instances", type=int, default=0, help="use only the first N instances (small profiling case)")
