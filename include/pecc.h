@@ -123,7 +123,7 @@ typedef struct {
     int32_t fuse_phases;    /* PECC_FP32_POLISH64: 1 = each instance's FP32 descent and polish run
                                back to back in one block of one kernel (long polishes overlap other
                                instances' descents; pecc_phase_times then reports the fused kernel
-                               as the first phase and 0 for the polish), 0 = two kernels; 0 */
+                               as the first phase and 0 for the polish), 0 = two kernels; 1 */
 } pecc_config;
 
 /* Fill *cfg with the defaults listed above (num_instances = 0, n = NULL). */

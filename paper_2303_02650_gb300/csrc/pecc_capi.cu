@@ -152,7 +152,7 @@ void pecc_config_default(pecc_config *c) {
   c->polish_k = 1;
   c->polish_stall_rel = 1e-2;
   c->polish_stall_window = 100;
-  c->fuse_phases = 0;
+  c->fuse_phases = 1;
 }
 
 static int default_k(int n) { return n < 300 ? 1 : (n < 500 ? 3 : 5); }
