@@ -171,10 +171,17 @@ pecc_status pecc_export_neighbors(pecc_ctx *ctx, int32_t *row_ptr_dev, int32_t *
  * circles of each instance stably sorted by key (local indices). */
 pecc_status pecc_export_cells(pecc_ctx *ctx, uint32_t *key_dev, int32_t *order_dev);
 
+/* Coordinates of an instance the energy + gradient call stages in shared memory at most
+ * (PECC_ENERGY_STAGE_BYTES / 8 circles in FP32, / 16 in FP64 and the mixed arithmetic). */
+#define PECC_ENERGY_STAGE_BYTES (96 * 1024)
+
 /* Energy (Eq. 5, neighbor-list form of Sec. 4.3) and gradient of every instance at the
  * current coordinates over the current lists: E_dev = device double[num_instances];
  * grad_dev = device float2[sum n] (FP32 contexts) or double2[sum n] (PECC_FP64).
- * One launch over all circles; the gradient is gathered (no atomics). */
+ * One block per instance with its coordinates staged in shared memory (one launch for all
+ * instances up to PECC_ENERGY_STAGE_BYTES of coordinates); larger instances take one thread
+ * per circle and a per-instance reduction.  The gradient is gathered (no atomics) and E is
+ * summed in a fixed order (deterministic). */
 pecc_status pecc_energy_grad(pecc_ctx *ctx, double *E_dev, void *grad_dev);
 
 /* Same, with an explicit arithmetic: eval = PECC_FP64 (double2 gradient), PECC_FP32

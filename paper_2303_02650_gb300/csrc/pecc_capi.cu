@@ -497,6 +497,25 @@ pecc_status pecc_export_cells(pecc_ctx *ctx, uint32_t *key_dev, int32_t *order_d
   return PECC_OK;
 }
 
+// Which energy + gradient kernels a call needs: the largest instance the block kernel stages, and
+// whether any instance is too large for it.
+static void energy_grad_split(const pecc_ctx *ctx, int eval, int *max_small_n, bool *any_large) {
+  const int lim = energy_stage_n(eval);
+  *max_small_n = 0;
+  *any_large = false;
+  for (int q = 0; q < ctx->num; ++q) {
+    if (ctx->n[q] <= lim) *max_small_n = std::max(*max_small_n, ctx->n[q]);
+    else *any_large = true;
+  }
+}
+
+static cudaError_t energy_grad_launch(pecc_ctx *ctx, const StandaloneParams &sp, int eval, double *E, void *grad) {
+  int ms = 0;
+  bool big = false;
+  energy_grad_split(ctx, eval, &ms, &big);
+  return launch_energy_grad(sp, eval, E, grad, ctx->ecirc, ms, big, ctx->stream);
+}
+
 pecc_status pecc_energy_grad_ex(pecc_ctx *ctx, int32_t eval, double *E_dev, void *grad_dev) {
   pecc_status s = need_radius(ctx);
   if (s) return s;
@@ -506,7 +525,7 @@ pecc_status pecc_energy_grad_ex(pecc_ctx *ctx, int32_t eval, double *E_dev, void
   if (ctx->total > 0 && (!E_dev || !grad_dev)) return fail(ctx, PECC_ERR_ARG, "NULL output");
   if (eval == PECC_FP32_POLISH64 && ctx->cfg.precision == PECC_FP64)
     return fail(ctx, PECC_ERR_ARG, "the mixed arithmetic needs an FP32 context");
-  CK(launch_energy_grad(sparams(ctx), eval, E_dev, grad_dev, ctx->ecirc, ctx->stream));
+  CK(energy_grad_launch(ctx, sparams(ctx), eval, E_dev, grad_dev));
   return PECC_OK;
 }
 
@@ -977,12 +996,12 @@ pecc_status pecc_warm_start(pecc_ctx *ctx, pecc_mlp *mlp, int32_t rounds, int32_
   StandaloneParams sp = sparams(ctx);
   for (int r = 0; r < rounds; ++r) {
     CK(launch_build(sp, 1, 1, nullptr, nullptr, ctx->block_build, ctx->stream));
-    CK(launch_energy_grad(sp, 1, ctx->Eb, ctx->g, ctx->ecirc, ctx->stream));
+    CK(energy_grad_launch(ctx, sp, 1, ctx->Eb, ctx->g));
     CK(mlp_features(sp, ctx->feat, ctx->stream));
     CK(mlp_forward(mlp->wb, mlp->params, ctx->feat, ctx->total, ctx->dout, mlp->sms, ctx->stream));
     CK(mlp_apply(sp, ctx->dout, ctx->backup, ctx->stream));
     CK(launch_build(sp, 1, 1, nullptr, nullptr, ctx->block_build, ctx->stream));
-    CK(launch_energy_grad(sp, 1, ctx->Ea, ctx->g, ctx->ecirc, ctx->stream));
+    CK(energy_grad_launch(ctx, sp, 1, ctx->Ea, ctx->g));
     CK(mlp_revert(sp, ctx->backup, ctx->Eb, ctx->Ea, accepted_dev, ctx->stream));
   }
   ctx->lists_prec = -1;

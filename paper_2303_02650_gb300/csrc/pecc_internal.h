@@ -7,6 +7,7 @@
 #include <algorithm>
 #include <cuda_bf16.h>
 
+#include "pecc.h"
 #include "pecc_dev.cuh"
 
 namespace pecc {
@@ -102,6 +103,9 @@ size_t descend_smem_need(int arith, int n, int k, int ncx, int block);
 size_t descend_smem_mandatory(int arith, int k, int block);
 
 // Standalone kernels (pecc_kernels.cu).
+// Largest instance whose coordinates the block energy + gradient kernel stages in shared memory.
+inline int energy_stage_n(int eval) { return (int)(PECC_ENERGY_STAGE_BYTES / (eval == 1 ? 8 : 16)); }
+
 struct StandaloneParams {
   const InstDesc *desc;
   InstOut *out;
@@ -129,7 +133,7 @@ cudaError_t launch_set_radius(InstDesc *desc, const double *R, int num, cudaStre
 cudaError_t launch_build(const StandaloneParams &p, int prec, int force, int32_t *rebuilt, int32_t *status,
                          int block, cudaStream_t s);
 cudaError_t launch_energy_grad(const StandaloneParams &p, int eval, double *E, void *grad, void *ecirc,
-                               cudaStream_t s);
+                               int max_small_n, bool any_large, cudaStream_t s);
 cudaError_t launch_feasible(const StandaloneParams &p, int from32, double tol, uint8_t *feasible,
                             double *max_overlap, int block, cudaStream_t s);
 cudaError_t launch_export_csr(const StandaloneParams &p, const int64_t *base, int32_t *row_ptr, int32_t *col,

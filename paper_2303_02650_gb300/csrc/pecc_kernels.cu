@@ -110,7 +110,7 @@ __global__ void build_kernel(StandaloneParams P, int force, int32_t *rebuilt, in
 //   g_i = sum_{j in Gamma(i)} -2 d_ij (c_i - c_j) / l_ij + 2 d_i0 c_i / |c_i|
 //   e_i = sum_{j in Gamma(i), j < i} d_ij^2 + d_i0^2      (so that E = sum_i e_i, Eq. 5)
 template <class A>
-__global__ void __launch_bounds__(256) energy_grad_kernel(StandaloneParams P, void *__restrict__ grad_,
+__global__ void __launch_bounds__(256) energy_grad_kernel(StandaloneParams P, int stage_n, void *__restrict__ grad_,
                                                           void *__restrict__ ecirc_) {
   using pos_t = typename A::pos_t;
   using vec_t = typename A::vec_t;
@@ -120,6 +120,7 @@ __global__ void __launch_bounds__(256) energy_grad_kernel(StandaloneParams P, vo
   int64_t gi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (gi >= P.total) return;
   const int q = __ldg(P.inst_of + gi);
+  if (P.desc[q].n <= stage_n) return;  // the block kernel's instance
   const int64_t off = P.desc[q].off;
   const int64_t col_off = P.desc[q].col_s_off;
   const double Rd = P.desc[q].R;
@@ -149,12 +150,73 @@ __global__ void __launch_bounds__(256) energy_grad_kernel(StandaloneParams P, vo
   ((acc_t *)ecirc_)[gi] = e;
 }
 
-// Per-instance sum of the per-circle energies (fixed order: deterministic).
+// One block per instance whose coordinates fit the staging limit (stage_n circles at most): the
+// coordinates are staged in shared memory by one coalesced read, so every neighbor gather is an
+// on-chip load; row pointers and lists stream through once, the gradient is written once, and the
+// energy is reduced in the block in a fixed order (deterministic) and written once.  Larger
+// instances are left to energy_grad_kernel + energy_reduce_kernel.
+template <class A>
+__global__ void __launch_bounds__(256) energy_grad_block_kernel(StandaloneParams P, int stage_n,
+                                                                void *__restrict__ grad_, double *E) {
+  using pos_t = typename A::pos_t;
+  using vec_t = typename A::vec_t;
+  using acc_t = typename A::acc_t;
+  using PP = v2<pos_t>;
+  using VV = v2<vec_t>;
+  extern __shared__ __align__(16) unsigned char stage[];
+  __shared__ acc_t red[32];
+  const int q = blockIdx.x;
+  const int n = P.desc[q].n;
+  if (n > stage_n) return;  // the per-circle kernels' instance (uniform across the block)
+  const int64_t off = P.desc[q].off;
+  const int64_t col_off = P.desc[q].col_s_off;
+  const double Rd = P.desc[q].R;
+  const acc_t R = (acc_t)Rd;
+  const acc_t Rm1sq = (acc_t)((Rd >= 1.0) ? (Rd - 1.0) * (Rd - 1.0) : -1.0);
+  const PP *x = (sizeof(pos_t) == 4) ? (const PP *)(P.x32 + off) : (const PP *)(P.x64 + off);
+  PP *xs = (PP *)stage;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) xs[i] = x[i];
+  __syncthreads();
+  const int32_t *rp = P.rp + off + q;
+  const int32_t *cl = P.col + col_off;
+  VV *grad = (VV *)grad_ + off;
+  acc_t e = 0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const PP xi = xs[i];
+    vec_t gx = 0, gy = 0;
+    const int lo = __ldg(rp + i), hi = __ldg(rp + i + 1);
+    for (int t = lo; t < hi; ++t) {
+      const int j = __ldg(cl + t);
+      vec_t fx, fy;
+      acc_t d = A::pair(xi, xs[j], fx, fy);
+      gx += fx; gy += fy;
+      if (j < i) e += d * d;
+    }
+    vec_t fx, fy;
+    acc_t d0 = A::wall(xi, R, Rm1sq, fx, fy);
+    gx += fx; gy += fy;
+    e += d0 * d0;
+    VV gv; gv.x = gx; gv.y = gy;
+    grad[i] = gv;
+  }
+  e = warp_sum(e);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = e;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    acc_t v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : acc_t(0);
+    v = warp_sum(v);
+    if (threadIdx.x == 0) E[q] = (double)v;
+  }
+}
+
+// Per-instance sum of the per-circle energies (fixed order: deterministic), for the instances the
+// block kernel left (more than stage_n circles).
 template <typename acc_t>
-__global__ void energy_reduce_kernel(StandaloneParams P, const acc_t *__restrict__ ecirc, double *E) {
+__global__ void energy_reduce_kernel(StandaloneParams P, int stage_n, const acc_t *__restrict__ ecirc, double *E) {
   __shared__ acc_t sh[32];
   const int q = blockIdx.x;
   const InstDesc D = P.desc[q];
+  if (D.n <= stage_n) return;
   acc_t s = 0;
   for (int i = threadIdx.x; i < D.n; i += blockDim.x) s += ecirc[D.off + i];
   s = warp_sum(s);
@@ -303,17 +365,36 @@ cudaError_t launch_build(const StandaloneParams &p, int prec, int force, int32_t
   return cudaGetLastError();
 }
 
+template <class A> static cudaError_t launch_eg_block(const StandaloneParams &p, int stage_n, size_t smem,
+                                                     void *grad, double *E, cudaStream_t s) {
+  cudaError_t e = cudaFuncSetAttribute(energy_grad_block_kernel<A>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  energy_grad_block_kernel<A><<<p.num, 256, smem, s>>>(p, stage_n, grad, E);
+  return cudaGetLastError();
+}
+
+// max_small_n: the largest instance of at most stage_n(eval) circles (0: none); any_large: some
+// instance has more.
 cudaError_t launch_energy_grad(const StandaloneParams &p, int eval, double *E, void *grad, void *ecirc,
-                               cudaStream_t s) {
-  if (p.total > 0) {
-    unsigned nb = blocks_for(p.total, 256);
-    if (eval == 0) energy_grad_kernel<Arith64><<<nb, 256, 0, s>>>(p, grad, ecirc);
-    else if (eval == 1) energy_grad_kernel<Arith32><<<nb, 256, 0, s>>>(p, grad, ecirc);
-    else energy_grad_kernel<ArithMix><<<nb, 256, 0, s>>>(p, grad, ecirc);
+                               int max_small_n, bool any_large, cudaStream_t s) {
+  if (p.num <= 0) return cudaSuccess;
+  const int stage_n = energy_stage_n(eval);
+  cudaError_t e = cudaSuccess;
+  if (max_small_n > 0) {
+    const size_t smem = (size_t)max_small_n * (eval == 1 ? sizeof(float2) : sizeof(double2));
+    if (eval == 0) e = launch_eg_block<Arith64>(p, stage_n, smem, grad, E, s);
+    else if (eval == 1) e = launch_eg_block<Arith32>(p, stage_n, smem, grad, E, s);
+    else e = launch_eg_block<ArithMix>(p, stage_n, smem, grad, E, s);
+    if (e != cudaSuccess) return e;
   }
-  if (p.num > 0) {
-    if (eval == 1) energy_reduce_kernel<float><<<p.num, 256, 0, s>>>(p, (const float *)ecirc, E);
-    else energy_reduce_kernel<double><<<p.num, 256, 0, s>>>(p, (const double *)ecirc, E);
+  if (any_large && p.total > 0) {
+    unsigned nb = blocks_for(p.total, 256);
+    if (eval == 0) energy_grad_kernel<Arith64><<<nb, 256, 0, s>>>(p, stage_n, grad, ecirc);
+    else if (eval == 1) energy_grad_kernel<Arith32><<<nb, 256, 0, s>>>(p, stage_n, grad, ecirc);
+    else energy_grad_kernel<ArithMix><<<nb, 256, 0, s>>>(p, stage_n, grad, ecirc);
+    if (eval == 1) energy_reduce_kernel<float><<<p.num, 256, 0, s>>>(p, stage_n, (const float *)ecirc, E);
+    else energy_reduce_kernel<double><<<p.num, 256, 0, s>>>(p, stage_n, (const double *)ecirc, E);
   }
   return cudaGetLastError();
 }

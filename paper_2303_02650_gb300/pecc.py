@@ -50,6 +50,7 @@ _EXPORTS = ["pecc_config_default", "pecc_create", "pecc_destroy", "pecc_set_radi
             "pecc_mlp_get_params", "pecc_mlp_set_params", "pecc_mlp_forward", "pecc_mlp_grad", "pecc_mlp_train_step",
             "pecc_features", "pecc_targets", "pecc_warm_start", "pecc_autotune", "pecc_selftest_grid_barrier"]
 NOALLOC_MAX_N = 4096
+ENERGY_STAGE_BYTES = 96 * 1024  # PECC_ENERGY_STAGE_BYTES
 
 
 def library_path() -> str:
