@@ -501,7 +501,7 @@ pecc_status pecc_export_cells(pecc_ctx *ctx, uint32_t *key_dev, int32_t *order_d
 // whether any instance is too large for it.
 static void energy_grad_split(const pecc_ctx *ctx, int eval, int *max_small_n, bool *any_large) {
   const int lim = energy_stage_n(eval);
-  *max_small_n = 0;
+  *max_small_n = -1;  // no instance for the block kernel
   *any_large = false;
   for (int q = 0; q < ctx->num; ++q) {
     if (ctx->n[q] <= lim) *max_small_n = std::max(*max_small_n, ctx->n[q]);

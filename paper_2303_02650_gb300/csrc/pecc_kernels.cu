@@ -374,15 +374,15 @@ template <class A> static cudaError_t launch_eg_block(const StandaloneParams &p,
   return cudaGetLastError();
 }
 
-// max_small_n: the largest instance of at most stage_n(eval) circles (0: none); any_large: some
-// instance has more.
+// max_small_n: the largest instance of at most stage_n(eval) circles (-1: none; instances of 0
+// circles get E = 0 from the block kernel); any_large: some instance has more.
 cudaError_t launch_energy_grad(const StandaloneParams &p, int eval, double *E, void *grad, void *ecirc,
                                int max_small_n, bool any_large, cudaStream_t s) {
   if (p.num <= 0) return cudaSuccess;
   const int stage_n = energy_stage_n(eval);
   cudaError_t e = cudaSuccess;
-  if (max_small_n > 0) {
-    const size_t smem = (size_t)max_small_n * (eval == 1 ? sizeof(float2) : sizeof(double2));
+  if (max_small_n >= 0) {
+    const size_t smem = std::max<size_t>(16, (size_t)max_small_n * (eval == 1 ? sizeof(float2) : sizeof(double2)));
     if (eval == 0) e = launch_eg_block<Arith64>(p, stage_n, smem, grad, E, s);
     else if (eval == 1) e = launch_eg_block<Arith32>(p, stage_n, smem, grad, E, s);
     else e = launch_eg_block<ArithMix>(p, stage_n, smem, grad, E, s);

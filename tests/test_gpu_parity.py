@@ -133,6 +133,23 @@ def test_energy_grad_fp64(orc):
     assert np.all(np.linalg.norm(g - gr, axis=1) <= 1e-12 * np.maximum(gn, 1e-300) + 1e-13)
 
 
+def test_energy_grad_staged_and_per_circle_paths(orc):
+    """Instances up to PECC_ENERGY_STAGE_BYTES of coordinates take the block kernel (coordinates
+    staged in shared memory), larger ones the per-circle kernel and its reduction; one call with
+    both kinds (7000 circles is past the FP64 limit of 6144) matches the oracle on every instance."""
+    torch, pecc = need_gpu()
+    n = np.array([7000, 300, 0, 50, 6144], dtype=np.int32)
+    R = _radii(n, 0.83)
+    with _ctx(pecc, n, R, precision=0) as c:
+        xy = _layout(c, torch, 12, 1.03)
+        c.rebuild_neighbors()
+        E, g = [t.cpu().numpy() for t in c.energy_grad()]
+    Er, gr = _oracle_eg(orc, xy, n, R)
+    np.testing.assert_allclose(E, Er, rtol=1e-12, atol=1e-300)
+    gn = np.linalg.norm(gr, axis=1)
+    assert np.all(np.linalg.norm(g - gr, axis=1) <= 1e-12 * np.maximum(gn, 1e-300) + 1e-13)
+
+
 def test_energy_grad_fp32(orc):
     """FP32: d = 2 - l carries an absolute error of about ulp(2) = 2.4e-7 per pair (and the
     wall depth about ulp(R)), so E is compared to 1e-5 relative plus 4 ulp32(2) * sum 2 d, and
