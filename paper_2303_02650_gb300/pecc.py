@@ -311,11 +311,15 @@ class Context:
         self._check(self._L.pecc_export_cells(self.h, _ptr(key), _ptr(order)), "pecc_export_cells")
         return key, order
 
-    def energy_grad(self, eval=None):
-        E = torch.empty(self.num, dtype=torch.float64, device=self.dev)
+    def energy_grad(self, eval=None, out=None):
+        """(E, g); out = (E, g) preallocated with the right dtypes reuses those tensors."""
         ev = (FP64 if self.precision == FP64 else FP32) if eval is None else eval
-        gdt = torch.float64 if ev == FP64 else torch.float32
-        g = torch.empty((self.total, 2), dtype=gdt, device=self.dev)
+        if out is None:
+            E = torch.empty(self.num, dtype=torch.float64, device=self.dev)
+            gdt = torch.float64 if ev == FP64 else torch.float32
+            g = torch.empty((self.total, 2), dtype=gdt, device=self.dev)
+        else:
+            E, g = out
         rc = self._L.pecc_energy_grad(self.h, _ptr(E), _ptr(g)) if eval is None else \
             self._L.pecc_energy_grad_ex(self.h, int(eval), _ptr(E), _ptr(g))
         self._check(rc, "pecc_energy_grad")
