@@ -35,7 +35,6 @@ struct pecc_ctx {
   int32_t *perm = nullptr, *meta = nullptr;
   uint64_t *skey = nullptr;
   int32_t *rp = nullptr, *col = nullptr, *rp_s = nullptr, *col_s = nullptr;
-  int32_t *eg_err = nullptr;  // raised by the energy kernel if a staging wait ran out
   uint32_t *ckey = nullptr, *ckey_s = nullptr;
   int32_t *corder = nullptr, *corder_s = nullptr, *cells = nullptr;
   int64_t *nnz = nullptr;
@@ -254,10 +253,8 @@ pecc_status pecc_create(const pecc_config *cfg, void *stream, pecc_ctx **out) {
   ALC(ctx->queue, int32_t, 4);
   ALC(ctx->t0, long long, 1);
   ALC(ctx->inst_of, int32_t, total);
-  // coordinates, standalone row pointers and lists get 16 B of tail padding: the energy kernel's
-  // bulk copies read whole 16-byte units
-  ALC(ctx->x64, double2, total + 1);
-  if (!fp64) ALC(ctx->x32, float2, total + 2);
+  ALC(ctx->x64, double2, total);
+  if (!fp64) ALC(ctx->x32, float2, total);
   void *p;
   ALC(p, double2, total); ctx->xw = p;
   ALC(p, double2, total); ctx->xb = p;
@@ -275,9 +272,8 @@ pecc_status pecc_create(const pecc_config *cfg, void *stream, pecc_ctx **out) {
   ALC(ctx->skey, uint64_t, total);
   ALC(ctx->rp, int32_t, rp_off);
   ALC(ctx->col, int32_t, col_off);
-  ALC(ctx->rp_s, int32_t, total + ctx->num + 4);
-  ALC(ctx->col_s, int32_t, col_s_off + 4);
-  ALC(ctx->eg_err, int32_t, 1);
+  ALC(ctx->rp_s, int32_t, total + ctx->num);
+  ALC(ctx->col_s, int32_t, col_s_off);
   ALC(ctx->ckey, uint32_t, total);
   ALC(ctx->ckey_s, uint32_t, total);
   ALC(ctx->corder, int32_t, total);
@@ -517,7 +513,7 @@ static cudaError_t energy_grad_launch(pecc_ctx *ctx, const StandaloneParams &sp,
   int ms = 0;
   bool big = false;
   energy_grad_split(ctx, eval, &ms, &big);
-  return launch_energy_grad(sp, eval, E, grad, ctx->ecirc, ms, big, ctx->num_sms, ctx->eg_err, ctx->stream);
+  return launch_energy_grad(sp, eval, E, grad, ctx->ecirc, ms, big, ctx->stream);
 }
 
 pecc_status pecc_energy_grad_ex(pecc_ctx *ctx, int32_t eval, double *E_dev, void *grad_dev) {

@@ -133,7 +133,7 @@ cudaError_t launch_set_radius(InstDesc *desc, const double *R, int num, cudaStre
 cudaError_t launch_build(const StandaloneParams &p, int prec, int force, int32_t *rebuilt, int32_t *status,
                          int block, cudaStream_t s);
 cudaError_t launch_energy_grad(const StandaloneParams &p, int eval, double *E, void *grad, void *ecirc,
-                               int max_small_n, bool any_large, int sms, int *err, cudaStream_t s);
+                               int max_small_n, bool any_large, cudaStream_t s);
 cudaError_t launch_feasible(const StandaloneParams &p, int from32, double tol, uint8_t *feasible,
                             double *max_overlap, int block, cudaStream_t s);
 cudaError_t launch_export_csr(const StandaloneParams &p, const int64_t *base, int32_t *row_ptr, int32_t *col,

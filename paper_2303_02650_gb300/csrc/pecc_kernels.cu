@@ -150,173 +150,62 @@ __global__ void __launch_bounds__(256) energy_grad_kernel(StandaloneParams P, in
   ((acc_t *)ecirc_)[gi] = e;
 }
 
-// ---- energy + gradient of the instances up to the staging limit: a persistent kernel that streams
-// each instance's coordinates, row pointers and lists into shared memory with bulk asynchronous
-// copies (cp.async.bulk, completion on an mbarrier), double-buffered: while the block computes
-// instance k from one buffer, instance k + grid is already on its way into the other.  Every
-// neighbor gather is then an on-chip load, and the copies keep DRAM busy between instances.
-__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
-__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity) {
-  unsigned ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// global -> shared bulk copy; both addresses 16-byte aligned, bytes a multiple of 16
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, uint64_t *bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                   smem_u32(dst)),
-               "l"(src), "r"(bytes), "r"(smem_u32(bar))
-               : "memory");
-}
-// the wait for a staged instance is bounded: past this many polls (far beyond any copy's time) the
-// block gives up, flags the error and leaves
-constexpr long long kStagePolls = 1ll << 24;
-
-struct EgSlot {
-  int q, n;      // instance (q >= num: none), circles
-  int mode;      // 0 staged, 1 read from global memory (does not fit the buffer), 2 not this kernel's
-  int xs, rs, cs;        // element shifts of x, row pointers and lists inside their staged copies
-  int roff, coff;        // byte offsets of the row-pointer and list copies in the buffer
-};
-
+// One block per instance whose coordinates fit the staging limit (stage_n circles at most): the
+// coordinates are staged in shared memory by one coalesced read, so every neighbor gather is an
+// on-chip load; row pointers and lists stream through once, the gradient is written once, and the
+// energy is reduced in the block in a fixed order (deterministic) and written once.  Larger
+// instances are left to energy_grad_kernel + energy_reduce_kernel.
 template <class A>
-__global__ void __launch_bounds__(512) energy_grad_stream_kernel(StandaloneParams P, int stage_n, int buf_bytes,
-                                                                 void *__restrict__ grad_, double *E, int *err) {
+__global__ void __launch_bounds__(256) energy_grad_block_kernel(StandaloneParams P, int stage_n,
+                                                                void *__restrict__ grad_, double *E) {
   using pos_t = typename A::pos_t;
   using vec_t = typename A::vec_t;
   using acc_t = typename A::acc_t;
   using PP = v2<pos_t>;
   using VV = v2<vec_t>;
-  extern __shared__ __align__(128) unsigned char dyn[];
-  __shared__ EgSlot slot[2];
-  __shared__ __align__(8) uint64_t mbar[2];
+  extern __shared__ __align__(16) unsigned char stage[];
   __shared__ acc_t red[32];
-  const int tid = threadIdx.x, T = blockDim.x;
-  const PP *xg = (sizeof(pos_t) == 4) ? (const PP *)P.x32 : (const PP *)P.x64;
-  if (tid == 0) {
-    mbar_init(&mbar[0], 1);
-    mbar_init(&mbar[1], 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  // thread 0: describe instance qi in slot b and start its copies when it fits the buffer
-  auto issue = [&](int qi, int b) {
-    EgSlot t{};
-    t.q = qi;
-    t.mode = 2;
-    if (qi < P.num) {
-      const InstDesc &D = P.desc[qi];
-      t.n = D.n;
-      if (D.n <= stage_n) {
-        const int n = D.n;
-        const int32_t *rpg = P.rp + D.off + qi;
-        const int nnz = n > 0 ? rpg[n] : 0;
-        const uintptr_t xb = (uintptr_t)(xg + D.off), rb = (uintptr_t)rpg, cb = (uintptr_t)(P.col + D.col_s_off);
-        const uintptr_t xl = xb & ~(uintptr_t)15, rl = rb & ~(uintptr_t)15, cl = cb & ~(uintptr_t)15;
-        const unsigned xbytes = (unsigned)(((xb + (uintptr_t)n * sizeof(PP) + 15) & ~(uintptr_t)15) - xl);
-        const unsigned rbytes = (unsigned)(((rb + 4 * (uintptr_t)(n + 1) + 15) & ~(uintptr_t)15) - rl);
-        const unsigned cbytes = (unsigned)(((cb + 4 * (uintptr_t)nnz + 15) & ~(uintptr_t)15) - cl);
-        t.xs = (int)((xb - xl) / sizeof(PP));
-        t.rs = (int)((rb - rl) / 4);
-        t.cs = (int)((cb - cl) / 4);
-        t.roff = (int)xbytes;
-        t.coff = (int)(xbytes + rbytes);
-        if (n > 0 && (size_t)xbytes + rbytes + cbytes <= (size_t)buf_bytes) {
-          t.mode = 0;
-          unsigned char *base = dyn + (size_t)b * buf_bytes;
-          mbar_expect_tx(&mbar[b], xbytes + rbytes + cbytes);
-          bulk_g2s(base, (const void *)xl, xbytes, &mbar[b]);
-          bulk_g2s(base + xbytes, (const void *)rl, rbytes, &mbar[b]);
-          if (cbytes > 0) bulk_g2s(base + xbytes + rbytes, (const void *)cl, cbytes, &mbar[b]);
-        } else {
-          t.mode = 1;
-        }
-      }
-    }
-    slot[b] = t;
-  };
-  if (tid == 0) issue(blockIdx.x, 0);
-  unsigned uses[2] = {0u, 0u};  // completed phases of each buffer's mbarrier (block-uniform)
-  int k = 0;
-  for (int qi = blockIdx.x; qi < P.num; qi += gridDim.x, ++k) {
-    const int b = k & 1;
-    __syncthreads();  // slot b is written; buffer b ^ 1 is no longer read
-    if (tid == 0) {
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      issue(qi + gridDim.x, b ^ 1);
-    }
-    const EgSlot t = slot[b];
-    if (t.mode == 2) continue;  // larger than the staging limit: the per-circle kernel's
-    const InstDesc &D = P.desc[t.q];
-    const int n = t.n;
-    const PP *xs;
-    const int32_t *rps, *cls;
-    if (t.mode == 0) {
-      const unsigned par = uses[b] & 1u;
-      long long it = 0;
-      bool done = mbar_try_wait(&mbar[b], par);
-      while (!done && ++it < kStagePolls) {
-        __nanosleep(32);
-        done = mbar_try_wait(&mbar[b], par);
-      }
-      uses[b]++;
-      if (!__syncthreads_and(done)) {  // the copy never completed: flag, give it one more bounded wait, leave
-        if (tid == 0) {
-          atomicExch(err, 1);
-          for (long long w = 0; w < kStagePolls && !mbar_try_wait(&mbar[b], par); ++w) __nanosleep(32);
-        }
-        __syncthreads();
-        return;
-      }
-      const unsigned char *base = dyn + (size_t)b * buf_bytes;
-      xs = (const PP *)base + t.xs;
-      rps = (const int32_t *)(base + t.roff) + t.rs;
-      cls = (const int32_t *)(base + t.coff) + t.cs;
-    } else {
-      xs = xg + D.off;
-      rps = P.rp + D.off + t.q;
-      cls = P.col + D.col_s_off;
-    }
-    const double Rd = D.R;
-    const acc_t R = (acc_t)Rd;
-    const acc_t Rm1sq = (acc_t)((Rd >= 1.0) ? (Rd - 1.0) * (Rd - 1.0) : -1.0);
-    VV *grad = (VV *)grad_ + D.off;
-    acc_t e = 0;
-    for (int i = tid; i < n; i += T) {
-      const PP xi = xs[i];
-      vec_t gx = 0, gy = 0;
-      const int lo = rps[i], hi = rps[i + 1];
-      for (int u = lo; u < hi; ++u) {
-        const int j = cls[u];
-        vec_t fx, fy;
-        acc_t d = A::pair(xi, xs[j], fx, fy);
-        gx += fx; gy += fy;
-        if (j < i) e += d * d;
-      }
+  const int q = blockIdx.x;
+  const int n = P.desc[q].n;
+  if (n > stage_n) return;  // the per-circle kernels' instance (uniform across the block)
+  const int64_t off = P.desc[q].off;
+  const int64_t col_off = P.desc[q].col_s_off;
+  const double Rd = P.desc[q].R;
+  const acc_t R = (acc_t)Rd;
+  const acc_t Rm1sq = (acc_t)((Rd >= 1.0) ? (Rd - 1.0) * (Rd - 1.0) : -1.0);
+  const PP *x = (sizeof(pos_t) == 4) ? (const PP *)(P.x32 + off) : (const PP *)(P.x64 + off);
+  PP *xs = (PP *)stage;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) xs[i] = x[i];
+  __syncthreads();
+  const int32_t *rp = P.rp + off + q;
+  const int32_t *cl = P.col + col_off;
+  VV *grad = (VV *)grad_ + off;
+  acc_t e = 0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const PP xi = xs[i];
+    vec_t gx = 0, gy = 0;
+    const int lo = __ldg(rp + i), hi = __ldg(rp + i + 1);
+    for (int t = lo; t < hi; ++t) {
+      const int j = __ldg(cl + t);
       vec_t fx, fy;
-      acc_t d0 = A::wall(xi, R, Rm1sq, fx, fy);
+      acc_t d = A::pair(xi, xs[j], fx, fy);
       gx += fx; gy += fy;
-      e += d0 * d0;
-      VV gv; gv.x = gx; gv.y = gy;
-      grad[i] = gv;
+      if (j < i) e += d * d;
     }
-    e = warp_sum(e);
-    if ((tid & 31) == 0) red[tid >> 5] = e;
-    __syncthreads();
-    if (tid < 32) {
-      acc_t v = tid < (T >> 5) ? red[tid] : acc_t(0);
-      v = warp_sum(v);
-      if (tid == 0) E[t.q] = (double)v;
-    }
+    vec_t fx, fy;
+    acc_t d0 = A::wall(xi, R, Rm1sq, fx, fy);
+    gx += fx; gy += fy;
+    e += d0 * d0;
+    VV gv; gv.x = gx; gv.y = gy;
+    grad[i] = gv;
+  }
+  e = warp_sum(e);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = e;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    acc_t v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : acc_t(0);
+    v = warp_sum(v);
+    if (threadIdx.x == 0) E[q] = (double)v;
   }
 }
 
@@ -476,36 +365,27 @@ cudaError_t launch_build(const StandaloneParams &p, int prec, int force, int32_t
   return cudaGetLastError();
 }
 
-template <class A> static cudaError_t launch_eg_stream(const StandaloneParams &p, int stage_n, int buf_bytes, int grid,
-                                                      void *grad, double *E, int *err, cudaStream_t s) {
-  const size_t smem = 2 * (size_t)buf_bytes;
-  cudaError_t e = cudaFuncSetAttribute(energy_grad_stream_kernel<A>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+template <class A> static cudaError_t launch_eg_block(const StandaloneParams &p, int stage_n, size_t smem,
+                                                     void *grad, double *E, cudaStream_t s) {
+  cudaError_t e = cudaFuncSetAttribute(energy_grad_block_kernel<A>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
-  energy_grad_stream_kernel<A><<<grid, 512, smem, s>>>(p, stage_n, buf_bytes, grad, E, err);
+  energy_grad_block_kernel<A><<<p.num, 256, smem, s>>>(p, stage_n, grad, E);
   return cudaGetLastError();
 }
 
 // max_small_n: the largest instance of at most stage_n(eval) circles (-1: none; instances of 0
-// circles get E = 0 from the streaming kernel); any_large: some instance has more.  sms: the
-// device's multiprocessors (two streaming blocks each); err: device int raised if a staging wait
-// ran out (the instance's E is then not written).
+// circles get E = 0 from the block kernel); any_large: some instance has more.
 cudaError_t launch_energy_grad(const StandaloneParams &p, int eval, double *E, void *grad, void *ecirc,
-                               int max_small_n, bool any_large, int sms, int *err, cudaStream_t s) {
+                               int max_small_n, bool any_large, cudaStream_t s) {
   if (p.num <= 0) return cudaSuccess;
   const int stage_n = energy_stage_n(eval);
   cudaError_t e = cudaSuccess;
   if (max_small_n >= 0) {
-    // a buffer holds the coordinates, row pointers and up to 8 list entries per circle of the
-    // largest instance (instances with longer lists read global memory); 16 B of alignment slack
-    // per copy
-    const size_t pos = eval == 1 ? sizeof(float2) : sizeof(double2);
-    size_t buf = (size_t)max_small_n * (pos + 4 + 32) + 64;
-    buf = std::min<size_t>((buf + 127) & ~size_t(127), 100 * 1024);
-    const int grid = std::max(1, std::min(p.num, 2 * sms));
-    if (eval == 0) e = launch_eg_stream<Arith64>(p, stage_n, (int)buf, grid, grad, E, err, s);
-    else if (eval == 1) e = launch_eg_stream<Arith32>(p, stage_n, (int)buf, grid, grad, E, err, s);
-    else e = launch_eg_stream<ArithMix>(p, stage_n, (int)buf, grid, grad, E, err, s);
+    const size_t smem = std::max<size_t>(16, (size_t)max_small_n * (eval == 1 ? sizeof(float2) : sizeof(double2)));
+    if (eval == 0) e = launch_eg_block<Arith64>(p, stage_n, smem, grad, E, s);
+    else if (eval == 1) e = launch_eg_block<Arith32>(p, stage_n, smem, grad, E, s);
+    else e = launch_eg_block<ArithMix>(p, stage_n, smem, grad, E, s);
     if (e != cudaSuccess) return e;
   }
   if (any_large && p.total > 0) {
