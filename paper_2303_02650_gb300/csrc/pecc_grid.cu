@@ -70,12 +70,20 @@ template <class A> struct GSmem {
   int32_t sh[40];
   long long iv[2];
   int flag;
+  int rbuf;  // partial buffer of the next grid_reduce (same in every block)
 };
 
-// Grid-wide reduction of NV values (kind 0: sum, 1: max); totals in S.tot[] of every block.
+// Grid-wide reduction of NV values (kind 0: sum, 1: max) with one grid barrier: every block writes
+// its partials to buffer S.rbuf of G.part, and after the barrier every block combines all blocks'
+// partials itself (warp q takes value q, its lanes stride over the blocks, then a fixed butterfly),
+// so every block holds bit-identical totals in S.tot[].  Consecutive reductions alternate the two
+// buffers: a block writes a buffer again only after the next reduction's barrier, which every
+// block passes after its reads of this one.
 template <class A, int NV, typename T>
 __device__ bool grid_reduce(GSmem<A> &S, const GridBufs &G, GridCtl *c, T (&v)[NV], const int (&kind)[NV]) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int buf = S.rbuf;
+  double *part = G.part + (size_t)buf * gridDim.x * kPart;
 #pragma unroll
   for (int q = 0; q < NV; ++q) {
     T s = kind[q] ? warp_max(v[q]) : warp_sum(v[q]);
@@ -85,21 +93,20 @@ __device__ bool grid_reduce(GSmem<A> &S, const GridBufs &G, GridCtl *c, T (&v)[N
   for (int q = threadIdx.x; q < NV; q += blockDim.x) {
     double s = S.wb[q];
     for (int u = 1; u < nw; ++u) s = kind[q] ? fmax(s, S.wb[u * kPart + q]) : s + S.wb[u * kPart + q];
-    G.part[(size_t)blockIdx.x * kPart + q] = s;
+    part[(size_t)blockIdx.x * kPart + q] = s;
   }
   if (!grid_sync(c)) return false;
-  if (blockIdx.x == 0) {
-    for (int q = threadIdx.x; q < NV; q += blockDim.x) {
-      double s = G.part[q];
-      for (int b = 1; b < (int)gridDim.x; ++b) {
-        const double x = *(volatile const double *)&G.part[(size_t)b * kPart + q];
-        s = kind[q] ? fmax(s, x) : s + x;
-      }
-      G.res[q] = s;
+  for (int q = w; q < NV; q += nw) {
+    double s = kind[q] ? -INFINITY : 0.0;
+    for (int b = lane; b < (int)gridDim.x; b += 32) {
+      const double x = __ldcg(part + (size_t)b * kPart + q);  // L2: another block wrote it
+      s = kind[q] ? fmax(s, x) : s + x;
     }
+    s = kind[q] ? warp_max(s) : warp_sum(s);
+    if (lane == 0) S.tot[q] = s;
   }
-  if (!grid_sync(c)) return false;
-  for (int q = threadIdx.x; q < NV; q += blockDim.x) S.tot[q] = *(volatile const double *)&G.res[q];
+  __syncthreads();
+  if (threadIdx.x == 0) S.rbuf = buf ^ 1;
   __syncthreads();
   return true;
 }
@@ -150,6 +157,8 @@ __global__ void __launch_bounds__(256, 1) descend_grid_kernel(DescendParams P, i
   const sc_t c1 = (sc_t)P.c1, step_max = (sc_t)P.step_max, two_skin = (sc_t)(2.0 * P.rebuild_disp);
   const sc_t gsum_tol = (sc_t)P.gsum_tol, curv_eps = (sc_t)P.curv_eps;
 
+  if (tid == 0) S.rbuf = 0;
+  __syncthreads();
   if (A::kId == 2) {  // the polish runs only on instances the FP32 descent left near zero energy
     if (!(O->E32 <= P.polish_gate) || O->status32 >= 4) {
       for (int i = gid; i < n; i += gstride) {
