@@ -579,29 +579,27 @@ __device__ __forceinline__ void descend_instance(const DescendParams &P, Smem<A,
         if (!(gd < sc_t(0))) break;
         sc_t al = (dmax > step_max) ? step_max / dmax : sc_t(1);
         for (int tr = 0; tr < P.max_trials; ++tr) {
-          // ---- pass D: trial coordinates x_o + al d, trial batch energy and gradient, displacement
-          // since the build.  A batch neighbor's trial position is recomputed from its start and
-          // direction (final since pass B's reduction; the same expression, so the same bits)
-          // instead of read back, so no barrier separates writing and reading trial coordinates.
-          auto trial = [&](int j) -> PP {
-            const PP xo_ = xo[j];
-            const VV dd = dv[j];
+          // ---- pass C: trial coordinates
+          for (int pos = b + tid; pos < e; pos += T) {
+            PP xo_ = xo[pos];
+            VV dd = dv[pos];
             PP v;
             v.x = xo_.x + (pos_t)(al * (sc_t)dd.x);
             v.y = xo_.y + (pos_t)(al * (sc_t)dd.y);
-            return v;
-          };
+            xw[pos] = v;
+          }
+          __syncthreads();
+          // ---- pass D: trial batch energy and gradient, displacement since the build
           acc_t aD = 0;
           vec_t cD = 0;
           for (int pos = b + tid; pos < e; pos += T) {
-            const PP xi = trial(pos);
-            xw[pos] = xi;
+            PP xi = xw[pos];
             vec_t gx = 0, gy = 0;
             acc_t ei = 0;
             for (int t = rp[pos]; t < rp[pos + 1]; ++t) {
               int j = col[t];
               vec_t fx, fy;
-              acc_t d = A::pair(xi, (j >= b && j < e) ? trial(j) : xw[j], fx, fy);
+              acc_t d = A::pair(xi, xw[j], fx, fy);
               gx += fx; gy += fy;
               if (j < b || j >= e || j < pos) ei += d * d;
             }

@@ -603,28 +603,25 @@ __global__ void __launch_bounds__(256, 1) descend_grid_kernel(DescendParams P, i
         if (!(gd < sc_t(0))) break;
         sc_t al = (dmax > step_max) ? step_max / dmax : sc_t(1);
         for (int tr = 0; tr < P.max_trials; ++tr) {
-          // trial coordinates x_o + al d.  A batch neighbor's trial position is recomputed from its
-          // start and direction (final since pass B's reduction; the same expression, so the same
-          // bits) instead of read back, so no grid barrier separates writing and reading them.
-          auto trial = [&](int j) -> PP {
-            const PP xo_ = xo[j];
-            const VV dd = dv[j];
+          for (int pos = b + gid; pos < e; pos += gstride) {
+            const PP xo_ = xo[pos];
+            const VV dd = dv[pos];
             PP v;
             v.x = xo_.x + (pos_t)(al * (sc_t)dd.x);
             v.y = xo_.y + (pos_t)(al * (sc_t)dd.y);
-            return v;
-          };
+            xw[pos] = v;
+          }
+          if (!grid_sync(ctl)) { status = 6; break; }
           double vD[2] = {0.0, 0.0};
           const int kindD[2] = {0, 1};
           for (int pos = b + gid; pos < e; pos += gstride) {
-            const PP xi = trial(pos);
-            xw[pos] = xi;
+            const PP xi = xw[pos];
             vec_t gx = 0, gy = 0;
             acc_t ei = 0;
             for (int t = rp[pos]; t < rp[pos + 1]; ++t) {
               const int j = col[t];
               vec_t fx, fy;
-              const acc_t d = A::pair(xi, (j >= b && j < e) ? trial(j) : xw[j], fx, fy);
+              const acc_t d = A::pair(xi, xw[j], fx, fy);
               gx += fx; gy += fy;
               if (j < b || j >= e || j < pos) ei += d * d;
             }
