@@ -292,7 +292,7 @@ pecc_status pecc_create(const pecc_config *cfg, void *stream, pecc_ctx **out) {
     ctx->ggrid = ctx->num_sms * occ;
     for (int q : ctx->big) { nmax_big = std::max(nmax_big, ctx->n[q]); kmax = std::max(kmax, ctx->k[q]); }
     ALC(ctx->gb.part, double, 2 * (size_t)ctx->ggrid * 72);  // two alternating partial buffers
-    ALC(ctx->gb.res, double, 72);
+    ALC(ctx->gb.res, double, 2 * 72 + 1);  // two alternating total buffers, then the time-budget flag
     ALC(ctx->gb.ipart, int32_t, ctx->ggrid);
     ALC(ctx->gb.bucket, int32_t, 2 * (size_t)(nmax_big / 4) + 4);
     ALC(ctx->gb.hash, unsigned long long, 1);

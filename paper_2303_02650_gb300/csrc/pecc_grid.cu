@@ -96,14 +96,39 @@ __device__ bool grid_reduce(GSmem<A> &S, const GridBufs &G, GridCtl *c, T (&v)[N
     part[(size_t)blockIdx.x * kPart + q] = s;
   }
   if (!grid_sync(c)) return false;
-  for (int q = w; q < NV; q += nw) {
-    double s = kind[q] ? -INFINITY : 0.0;
-    for (int b = lane; b < (int)gridDim.x; b += 32) {
-      const double x = __ldcg(part + (size_t)b * kPart + q);  // L2: another block wrote it
-      s = kind[q] ? fmax(s, x) : s + x;
+  if (NV <= 8) {
+    for (int q = w; q < NV; q += nw) {
+      double s = kind[q] ? -INFINITY : 0.0;
+      for (int b = lane; b < (int)gridDim.x; b += 32) {
+        const double x = __ldcg(part + (size_t)b * kPart + q);  // L2: another block wrote it
+        s = kind[q] ? fmax(s, x) : s + x;
+      }
+      s = kind[q] ? warp_max(s) : warp_sum(s);
+      if (lane == 0) S.tot[q] = s;
     }
-    s = kind[q] ? warp_max(s) : warp_sum(s);
-    if (lane == 0) S.tot[q] = s;
+  } else {
+    // many values: block q combines value q over all blocks and publishes it, then a second
+    // barrier, and every block reads the NV totals (instead of every block reading NV x grid
+    // partials)
+    double *res = G.res + (size_t)buf * kPart;
+    for (int q = blockIdx.x; q < NV; q += gridDim.x) {
+      double s = kind[q] ? -INFINITY : 0.0;
+      for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+        const double x = __ldcg(part + (size_t)b * kPart + q);
+        s = kind[q] ? fmax(s, x) : s + x;
+      }
+      s = kind[q] ? warp_max(s) : warp_sum(s);
+      if (lane == 0) S.wb[w] = s;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double t = S.wb[0];
+        for (int u = 1; u < nw; ++u) t = kind[q] ? fmax(t, S.wb[u]) : t + S.wb[u];
+        res[q] = t;
+      }
+      __syncthreads();
+    }
+    if (!grid_sync(c)) return false;
+    for (int q = threadIdx.x; q < NV; q += blockDim.x) S.tot[q] = __ldcg(res + q);
   }
   __syncthreads();
   if (threadIdx.x == 0) S.rbuf = buf ^ 1;
@@ -694,9 +719,9 @@ __global__ void __launch_bounds__(256, 1) descend_grid_kernel(DescendParams P, i
     }
     if (P.budget_ns > 0) {
       // every block must take the same decision: block 0 reads the clock, a barrier publishes it
-      if (gid == 0) G.res[kPart - 1] = (globaltimer_ns() - *P.t0 > P.budget_ns) ? 1.0 : 0.0;
+      if (gid == 0) G.res[2 * kPart] = (globaltimer_ns() - *P.t0 > P.budget_ns) ? 1.0 : 0.0;
       if (!grid_sync(ctl)) { status = 6; break; }
-      const bool late = *(volatile double *)&G.res[kPart - 1] > 0.5;
+      const bool late = *(volatile double *)&G.res[2 * kPart] > 0.5;
       if (!grid_sync(ctl)) { status = 6; break; }
       if (late) { status = 6; break; }
     }
