@@ -360,7 +360,9 @@ def run_ours(args, rank, world, local):
         "step_gaps_ms": gaps,
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                      "frac": round(achieved / hbm, 4),
-                     "traffic": (round(fused_traffic(dom_bytes)) if fused and fused_traffic(dom_bytes) else None),
+                     # the capture's ratio holds for the workload it was taken on (the batch)
+                     "traffic": (round(fused_traffic(dom_bytes)) if fused and args.workload == "c3" and
+                                 fused_traffic(dom_bytes) else None),
                      "kernel": ("descend_fused_kernel (FP32 descent + FP64 polish per instance)" if fused else
                                 ("descend_grid_kernel" if big else "descend_kernel") +
                                 ("<Arith64>" if prec == 0 else "<Arith32> (FP32 bulk phase)")),
