@@ -89,6 +89,8 @@ def lib():
             "orc_default_opts": (None, [_P(Opts)]),
             "orc_gbo": (C.c_int, [C.c_int, d, C.c_double, _P(Opts), _P(Result), d]),
             "orc_max_overlap": (C.c_double, [C.c_int, d, C.c_double, d, d]),
+            "orc_u_energy_grad": (C.c_double, [C.c_int, d, C.c_double, C.c_double, d]),
+            "orc_adjust_container": (C.c_int, [C.c_int, d, d, _P(Opts), C.c_double, C.c_int, _P(Result)]),
             "orc_solve_batch": (C.c_double, [C.c_int, i32, d, C.c_uint64, C.c_int, C.c_int, _P(Opts),
                                              C.c_double, C.c_int, d, i32, i32, d, d, _P(C.c_uint8)]),
         }
@@ -293,6 +295,28 @@ def gbo(xy, R, **kw) -> GboResult:
     lib().orc_gbo(n, _ptr(x, C.c_double), R, C.byref(o), C.byref(r), _ptr(trace, C.c_double))
     return GboResult(x, r.iters, STATUS[r.status], r.builds, r.changes, r.disp_builds, r.trials, r.resets,
                      r.stalls, r.E, r.gsum, trace[: r.iters + 1])
+
+
+def u_energy_grad(xy, R, lam):
+    """Eq. 12: U = E + lam R^2 and its gradient over z = (x, R) (brute-force lists): (U, g[2n + 1])."""
+    x = _f64(xy)
+    n = x.shape[0]
+    g = np.zeros(2 * n + 1)
+    U = lib().orc_u_energy_grad(n, _ptr(x, C.c_double), R, lam, _ptr(g, C.c_double))
+    return U, g
+
+
+def adjust_container(xy, R, lambda0=1e-4, rounds=35, **kw):
+    """Algorithm adjust_container (Sec. 4.2): returns (x*, R*, result); does not modify xy."""
+    o = default_opts(**kw)
+    x = _f64(xy).copy()
+    n = x.shape[0]
+    Rv = np.array([float(R)])
+    r = Result()
+    lib().orc_adjust_container(n, _ptr(x, C.c_double), _ptr(Rv, C.c_double), C.byref(o), float(lambda0), int(rounds),
+                               C.byref(r))
+    return x, float(Rv[0]), GboResult(x, r.iters, STATUS[r.status], r.builds, r.changes, r.disp_builds, r.trials,
+                                      r.resets, r.stalls, r.E, r.gsum, None)
 
 
 def max_overlap(xy, R):

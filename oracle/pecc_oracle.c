@@ -912,6 +912,183 @@ int orc_gbo(int n, double *xy, double R, const orc_opts *o, orc_result *res, dou
 }
 
 /* ------------------------------------------------------------------------ */
+/* Container adjustment (Sec. 4.2, Algorithm adjust_container, Eq. 12).      */
+/* ------------------------------------------------------------------------ */
+/*
+ * U(z, lambda) = E(x, R) + lambda R^2 over the lists and its gradient over z = (x, R):
+ * g[0 .. 2n) = dE/dx (grad_row), g[2n] = dU/dR = -2 sum_i d_i0 + 2 lambda R, since
+ * d(d_i0^2)/dR = -2 d_i0 for d_i0 = max(0, |c_i| + 1 - R).
+ */
+static double u_energy_grad(int n, const double *xy, double R, double lambda, const csr *G, double *g)
+{
+    ksum sd = {0.0, 0.0};
+    for (int i = 0; i < n; i++) {
+        grad_row(i, xy, R, G->row_ptr, G->col, &g[2 * i], &g[2 * i + 1], NULL);
+        ks_add(&sd, bound_depth(xy[2 * i], xy[2 * i + 1], R, NULL));
+    }
+    g[2 * n] = -2.0 * ks_get(&sd) + 2.0 * lambda * R;
+    return orc_energy_csr(n, xy, R, G->row_ptr, G->col) + lambda * R * R;
+}
+
+/* U and its gradient on the brute-force lists (for the tests): g[2n + 1]. */
+double orc_u_energy_grad(int n, const double *xy, double R, double lambda, double *g)
+{
+    csr G = {0};
+    G.cap = (int64_t)n * (n > 0 ? n : 1);
+    G.row_ptr = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n + 1));
+    G.col = (int32_t *)malloc(sizeof(int32_t) * (size_t)(G.cap > 0 ? G.cap : 1));
+    G.nnz = orc_neighbors_brute(n, xy, 2.0, 0, G.row_ptr, G.col, G.cap);
+    double U = u_energy_grad(n, xy, R, lambda, &G, g);
+    free(G.row_ptr);
+    free(G.col);
+    return U;
+}
+
+/*
+ * adjust_container: z = (x, R); for t = 1 .. rounds minimise U(z, lambda) by a
+ * limited-memory BFGS over all of z, then halve lambda (lambda starts at lambda0).  Each
+ * round starts a fresh memory (U changes with lambda) and runs the descent of GBO with
+ * one batch: Armijo search from alpha0 = min(1, step_max / max(max_i |d_i|, |d_R|)), the
+ * Verlet rule and ANM on the lists, a pair kept when s'y > curv_eps |s| |y|; a round ends
+ * when |g| <= gsum_tol (stationary), when no step is accepted (stalled) or after max_iter
+ * iterations.  In place on xy[2n] and *R; res sums the rounds' iterations, builds and
+ * trials; status and E (of the final layout and radius) are those after the last round.
+ */
+int orc_adjust_container(int n, double *xy, double *Rp, const orc_opts *o, double lambda0, int rounds,
+                         orc_result *res)
+{
+    memset(res, 0, sizeof(*res));
+    double R = *Rp;
+    if (n <= 0) {
+        res->status = ORC_CONVERGED;
+        return 0;
+    }
+    const int dim = 2 * n + 1;
+    csr G = {0}, Gt = {0};
+    G.cap = Gt.cap = (int64_t)n * 8 + 64;
+    G.row_ptr = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n + 1));
+    Gt.row_ptr = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n + 1));
+    G.col = (int32_t *)malloc(sizeof(int32_t) * (size_t)G.cap);
+    Gt.col = (int32_t *)malloc(sizeof(int32_t) * (size_t)Gt.cap);
+    csr_build(&G, n, xy, R, o);
+    res->builds = 1;
+    double *xb = (double *)malloc(sizeof(double) * 2 * (size_t)n);
+    memcpy(xb, xy, sizeof(double) * 2 * (size_t)n);
+    double D = 0.0;
+    int cnt = 0, len = 1;
+    size_t vb = sizeof(double) * (size_t)dim;
+    double *g = (double *)malloc(vb), *gn = (double *)malloc(vb), *d = (double *)malloc(vb);
+    double *zo = (double *)malloc(vb), *s = (double *)malloc(vb), *y = (double *)malloc(vb);
+    double *alpha = (double *)malloc(sizeof(double) * (size_t)(o->m > 0 ? o->m : 1));
+    lmem M;
+    lmem_init(&M, o->m, dim);
+    double lambda = lambda0;
+    int status = ORC_MAXITER;
+    for (int round = 0; round < rounds; round++) {
+        M.count = 0;
+        M.head = 0;
+        status = ORC_MAXITER;
+        for (int t = 0; t < o->max_iter; t++) {
+            if (2.0 * D + o->step_max > 2.0 * o->rebuild_disp) {
+                anm_rebuild(&G, &Gt, n, xy, R, o, &cnt, &len, xb, &D, res);
+                res->disp_builds++;
+            }
+            res->iters++;
+            double U0 = u_energy_grad(n, xy, R, lambda, &G, g);
+            double gnorm = sqrt(dot(g, g, dim));
+            if (!(gnorm > o->gsum_tol)) {
+                status = ORC_STATIONARY;
+                break;
+            }
+            memcpy(zo, xy, sizeof(double) * 2 * (size_t)n);
+            zo[2 * n] = R;
+            int accepted = 0;
+            for (int attempt = 0; attempt < 2 && !accepted; attempt++) {
+                if (attempt == 1) {
+                    if (M.count == 0) break;
+                    M.count = 0;
+                    M.head = 0;
+                    res->resets++;
+                }
+                two_loop(&M, g, d, alpha);
+                double gd = dot(g, d, dim);
+                if (!(gd < 0.0)) {
+                    if (M.count > 0) {
+                        M.count = 0;
+                        M.head = 0;
+                        res->resets++;
+                    }
+                    for (int i = 0; i < dim; i++) d[i] = -g[i];
+                    gd = -gnorm * gnorm;
+                }
+                double dmax = fabs(d[2 * n]);
+                for (int a = 0; a < n; a++) {
+                    double v = sqrt(d[2 * a] * d[2 * a] + d[2 * a + 1] * d[2 * a + 1]);
+                    if (v > dmax) dmax = v;
+                }
+                double al = (dmax > o->step_max) ? o->step_max / dmax : 1.0;
+                for (int tr = 0; tr < o->max_trials; tr++) {
+                    for (int i = 0; i < 2 * n; i++) xy[i] = zo[i] + al * d[i];
+                    R = zo[2 * n] + al * d[2 * n];
+                    double Ut = orc_energy_csr(n, xy, R, G.row_ptr, G.col) + lambda * R * R;
+                    res->trials++;
+                    if (Ut <= U0 + o->c1 * al * gd) {
+                        accepted = 1;
+                        break;
+                    }
+                    al *= 0.5;
+                }
+                if (!accepted) {
+                    memcpy(xy, zo, sizeof(double) * 2 * (size_t)n);
+                    R = zo[2 * n];
+                }
+            }
+            if (!accepted) {
+                res->stalls++;
+                status = ORC_STALLED;
+                break;
+            }
+            u_energy_grad(n, xy, R, lambda, &G, gn);
+            double dmv = 0.0;
+            for (int i = 0; i < n; i++) {
+                double ex = xy[2 * i] - xb[2 * i], ey = xy[2 * i + 1] - xb[2 * i + 1];
+                double v = sqrt(ex * ex + ey * ey);
+                if (v > dmv) dmv = v;
+            }
+            if (dmv > D) D = dmv;
+            for (int i = 0; i < 2 * n; i++) s[i] = xy[i] - zo[i];
+            s[2 * n] = R - zo[2 * n];
+            for (int i = 0; i < dim; i++) y[i] = gn[i] - g[i];
+            double sy = dot(s, y, dim);
+            double ns = sqrt(dot(s, s, dim)), ny = sqrt(dot(y, y, dim));
+            if (M.m > 0 && sy > o->curv_eps * ns * ny) lmem_push(&M, s, y, sy);
+            if (o->anm) {
+                cnt++;
+                if (cnt >= len) anm_rebuild(&G, &Gt, n, xy, R, o, &cnt, &len, xb, &D, res);
+            }
+        }
+        lambda *= 0.5;
+    }
+    res->status = status;
+    res->E = orc_energy_csr(n, xy, R, G.row_ptr, G.col);
+    *Rp = R;
+    free(G.row_ptr);
+    free(G.col);
+    free(Gt.row_ptr);
+    free(Gt.col);
+    free(xb);
+    lmem_free(&M);
+    free(g);
+    free(gn);
+    free(d);
+    free(zo);
+    free(s);
+    free(y);
+    free(alpha);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Feasibility (Eq. 1, Eq. 2): largest pair depth over all pairs and largest */
 /* boundary depth, brute force.  Returns the larger of the two.              */
 /* ------------------------------------------------------------------------ */
