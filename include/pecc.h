@@ -325,6 +325,24 @@ pecc_status pecc_warm_start(pecc_ctx *ctx, pecc_mlp *mlp, int32_t rounds, int32_
 pecc_status pecc_check_feasible_noalloc(const double *xy_dev, int32_t n, double R, double l_cut, double tol,
                                         uint8_t *feasible_dev, double *max_overlap_dev, void *stream);
 
+/* Container adjustment (Sec. 4.2, Algorithm adjust_container, Eq. 12): with z = (x, R) and
+ * U(z, lambda) = E(x, R) + lambda R^2, for each of `rounds` rounds a limited-memory BFGS (the
+ * descent's step, one batch, lbfgs_m pairs, a fresh memory each round, binary64) minimises U over
+ * all of z, then lambda is halved; the paper's schedule is lambda0 = 1e-4, rounds = 35.  A round
+ * ends when |grad U| <= gsum_tol, when no step is accepted, or after max_iter iterations.
+ *   R_dev       device double[num_instances]: the starting radii in, the adjusted radii out (the
+ *               context's own radii, those of pecc_set_radius, are left as they are)
+ *   iters_dev   device int32[num_instances]: quasi-Newton iterations over all rounds
+ *   status_dev  device int32[num_instances]: status of the last round (1 stationary, 2 stalled,
+ *               3 max_iter; 4: list capacity exceeded, or an instance of 16384 circles or more,
+ *               which this call does not adjust; 0 for an empty instance)
+ * Starts from the context's coordinates (those of the last descent, pecc_set_positions or
+ * pecc_init_random) and replaces them with the adjusted layout.  Stream-ordered, asynchronous;
+ * the first call allocates the binary64 secant pairs (lbfgs_m <= 10 slots per circle).
+ * Errors: PECC_ERR_ARG for NULL pointers, rounds < 0, lambda0 < 0 or not finite, lbfgs_m > 10. */
+pecc_status pecc_adjust_container(pecc_ctx *ctx, double *R_dev, double lambda0, int32_t rounds, int32_t *iters_dev,
+                                  int32_t *status_dev);
+
 /* Self-test of the bounded wait of the grid barrier that the whole-GPU descent of large instances
  * uses (the wait is measured on %globaltimer; past its limit the waiting block raises an error
  * flag that every block sees, and the descent ends with status 6).  Four blocks wait at a barrier

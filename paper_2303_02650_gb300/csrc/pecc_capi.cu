@@ -35,6 +35,7 @@ struct pecc_ctx {
   int32_t *perm = nullptr, *meta = nullptr;
   uint64_t *skey = nullptr;
   int32_t *rp = nullptr, *col = nullptr, *rp_s = nullptr, *col_s = nullptr;
+  double2 *adjS = nullptr, *adjY = nullptr;  // binary64 secant pairs of the container adjustment
   uint32_t *ckey = nullptr, *ckey_s = nullptr;
   int32_t *corder = nullptr, *corder_s = nullptr, *cells = nullptr;
   int64_t *nnz = nullptr;
@@ -250,7 +251,7 @@ pecc_status pecc_create(const pecc_config *cfg, void *stream, pecc_ctx **out) {
   ALC(ctx->desc, InstDesc, ctx->num);
   ALC(ctx->out, InstOut, ctx->num);
   ALC(ctx->order, int32_t, ctx->num);
-  ALC(ctx->queue, int32_t, 4);
+  ALC(ctx->queue, int32_t, 5);  // descent phases 0..3, container adjustment 4
   ALC(ctx->t0, long long, 1);
   ALC(ctx->inst_of, int32_t, total);
   ALC(ctx->x64, double2, total);
@@ -818,6 +819,42 @@ pecc_status pecc_autotune(pecc_ctx *ctx, int32_t sweeps, uint64_t seed, int32_t 
   if (ce != cudaSuccess) return fail(ctx, PECC_ERR_CUDA, "autotune restore: %s", cudaGetErrorString(ce));
   if (block_out) *block_out = best_b;
   if (bps_out) *bps_out = best_t;
+  return PECC_OK;
+}
+
+pecc_status pecc_adjust_container(pecc_ctx *ctx, double *R_dev, double lambda0, int32_t rounds, int32_t *iters_dev,
+                                  int32_t *status_dev) {
+  pecc_status s = need_radius(ctx);
+  if (s) return s;
+  if (ctx->num == 0) return PECC_OK;
+  if (!R_dev || !iters_dev || !status_dev) return fail(ctx, PECC_ERR_ARG, "pecc_adjust_container: NULL pointer");
+  if (rounds < 0 || !(lambda0 >= 0.0) || !std::isfinite(lambda0))
+    return fail(ctx, PECC_ERR_ARG, "pecc_adjust_container: rounds must be >= 0 and lambda0 finite and >= 0");
+  if (ctx->cfg.lbfgs_m > adjust_max_m()) return fail(ctx, PECC_ERR_ARG, "pecc_adjust_container: lbfgs_m too large");
+  const size_t slots = (size_t)adjust_max_m() * (size_t)std::max<int64_t>(ctx->total, 1);
+  if (!ctx->adjS) {
+    if ((s = dalloc<double2>(ctx, &ctx->adjS, slots))) return s;
+    if ((s = dalloc<double2>(ctx, &ctx->adjY, slots))) return s;
+  }
+  AdjustParams p{};
+  p.desc = ctx->desc;
+  p.num = ctx->num;
+  p.from32 = ctx->cfg.precision == PECC_FP32 ? 1 : 0;
+  p.x32 = ctx->x32;
+  p.x64 = ctx->x64;
+  p.R = R_dev;
+  p.g = (double2 *)ctx->g; p.gn = (double2 *)ctx->gt; p.d = (double2 *)ctx->d; p.zo = (double2 *)ctx->xo;
+  p.xb = (double2 *)ctx->xw; p.xs = (double2 *)ctx->xbuild;
+  p.S = ctx->adjS; p.Y = ctx->adjY;
+  p.rp = ctx->rp; p.col = ctx->col; p.ckey = ctx->ckey; p.corder = ctx->corder; p.cells = ctx->cells;
+  p.iters = iters_dev; p.status = status_dev; p.queue = ctx->queue + 4;
+  const pecc_config &f = ctx->cfg;
+  p.l_cut = f.l_cut; p.rebuild_disp = f.rebuild_disp; p.step_max = f.step_max; p.gsum_tol = f.gsum_tol;
+  p.c1 = f.c1; p.curv_eps = f.curv_eps; p.lambda0 = lambda0;
+  p.m = f.lbfgs_m; p.max_iter = f.max_iter; p.max_trials = f.max_trials; p.anm = f.anm; p.rounds = rounds;
+  CK(cudaMemsetAsync(ctx->queue + 4, 0, sizeof(int32_t), ctx->stream));
+  CK(launch_adjust(p, (int)std::min<int64_t>(ctx->num, (int64_t)ctx->num_sms * 4), ctx->stream));
+  ctx->lists_prec = -1;  // the standalone lists' reference coordinates served as scratch
   return PECC_OK;
 }
 

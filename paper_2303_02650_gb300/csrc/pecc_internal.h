@@ -103,6 +103,25 @@ size_t descend_smem_need(int arith, int n, int k, int ncx, int block);
 size_t descend_smem_mandatory(int arith, int k, int block);
 
 // Standalone kernels (pecc_kernels.cu).
+// Container adjustment (pecc_adjust.cu).  Per-circle double2 arrays are the context's scratch
+// (offset by the instance); S, Y: adjust_max_m() slots of double2 per circle.
+struct AdjustParams {
+  const InstDesc *desc;
+  int num, from32;
+  float2 *x32;
+  double2 *x64;
+  double *R;  // in/out, per instance
+  double2 *g, *gn, *d, *zo, *xb, *xs, *S, *Y;
+  int32_t *rp, *col;
+  uint32_t *ckey;
+  int32_t *corder, *cells;
+  int32_t *iters, *status, *queue;
+  double l_cut, rebuild_disp, step_max, gsum_tol, c1, curv_eps, lambda0;
+  int m, max_iter, max_trials, anm, rounds;
+};
+cudaError_t launch_adjust(const AdjustParams &p, int grid, cudaStream_t s);
+int adjust_max_m();
+
 // Largest instance whose coordinates the block energy + gradient kernel stages in shared memory.
 inline int energy_stage_n(int eval) { return (int)(PECC_ENERGY_STAGE_BYTES / (eval == 1 ? 8 : 16)); }
 

@@ -48,7 +48,8 @@ _EXPORTS = ["pecc_config_default", "pecc_create", "pecc_destroy", "pecc_set_radi
             "pecc_get_counters", "pecc_get_launch", "pecc_last_error", "pecc_get_stats", "pecc_phase_times",
             "pecc_check_feasible_noalloc", "pecc_mlp_num_params", "pecc_mlp_create", "pecc_mlp_destroy",
             "pecc_mlp_get_params", "pecc_mlp_set_params", "pecc_mlp_forward", "pecc_mlp_grad", "pecc_mlp_train_step",
-            "pecc_features", "pecc_targets", "pecc_warm_start", "pecc_autotune", "pecc_selftest_grid_barrier"]
+            "pecc_features", "pecc_targets", "pecc_warm_start", "pecc_autotune", "pecc_selftest_grid_barrier",
+            "pecc_adjust_container"]
 NOALLOC_MAX_N = 4096
 ENERGY_STAGE_BYTES = 96 * 1024  # PECC_ENERGY_STAGE_BYTES
 
@@ -96,6 +97,7 @@ def load(build_if_missing: bool = True):
         "pecc_phase_times": (st, [vp, C.POINTER(C.c_float)]),
         "pecc_check_feasible_noalloc": (st, [vp, C.c_int32, C.c_double, C.c_double, C.c_double, vp, vp, vp]),
         "pecc_selftest_grid_barrier": (st, [C.c_int64, C.POINTER(C.c_int32), C.POINTER(C.c_int64)]),
+        "pecc_adjust_container": (st, [vp, vp, C.c_double, C.c_int32, vp, vp]),
         "pecc_mlp_num_params": (C.c_int32, []),
         "pecc_mlp_create": (st, [C.c_uint64, vp, C.POINTER(vp)]),
         "pecc_mlp_destroy": (st, [vp]),
@@ -378,6 +380,16 @@ class Context:
         acc = torch.zeros(self.num, dtype=torch.int32, device=self.dev)
         self._check(self._L.pecc_warm_start(self.h, mlp.h, int(rounds), _ptr(acc)), "pecc_warm_start")
         return acc
+
+    def adjust_container(self, R, lambda0=1e-4, rounds=35):
+        """pecc_adjust_container: R (float64[num], device or host) -> (R*, iters, status) device
+        tensors; the context's coordinates become the adjusted layout."""
+        Rt = torch.as_tensor(R, dtype=torch.float64).to(self.dev).clone().contiguous()
+        iters = torch.empty(self.num, dtype=torch.int32, device=self.dev)
+        status = torch.empty(self.num, dtype=torch.int32, device=self.dev)
+        self._check(self._L.pecc_adjust_container(self.h, _ptr(Rt), float(lambda0), int(rounds), _ptr(iters),
+                                                  _ptr(status)), "pecc_adjust_container")
+        return Rt, iters, status
 
     def autotune(self, sweeps=40, seed=99):
         """pecc_autotune: pick threads per block and blocks per SM by timing short descents."""
