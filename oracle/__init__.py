@@ -57,6 +57,11 @@ class Result(C.Structure):
                 ("stalls", C.c_int), ("E", C.c_double), ("gsum", C.c_double)]
 
 
+class SedResult(C.Structure):
+    _fields_ = [("iters", C.c_int), ("status", C.c_int), ("descents", C.c_int), ("E0", C.c_double),
+                ("E", C.c_double)]
+
+
 def _P(t):
     return C.POINTER(t)
 
@@ -91,6 +96,11 @@ def lib():
             "orc_max_overlap": (C.c_double, [C.c_int, d, C.c_double, d, d]),
             "orc_u_energy_grad": (C.c_double, [C.c_int, d, C.c_double, C.c_double, d]),
             "orc_adjust_container": (C.c_int, [C.c_int, d, d, _P(Opts), C.c_double, C.c_int, _P(Result)]),
+            "orc_sed_J": (C.c_int, [C.c_double]),
+            "orc_sed_perturb": (None, [C.c_int, d, C.c_uint64, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, d]),
+            "orc_sed_select": (C.c_int, [C.c_int, d, C.c_double, C.c_uint64, C.c_int, C.c_int]),
+            "orc_sed": (C.c_int, [C.c_int, C.c_double, C.c_uint64, C.c_int, C.c_int, _P(Opts), C.c_int, C.c_int,
+                                  C.c_double, C.c_int, C.c_double, d, _P(SedResult), i32, i32, d, d]),
             "orc_solve_batch": (C.c_double, [C.c_int, i32, d, C.c_uint64, C.c_int, C.c_int, _P(Opts),
                                              C.c_double, C.c_int, d, i32, i32, d, d, _P(C.c_uint8)]),
         }
@@ -317,6 +327,58 @@ def adjust_container(xy, R, lambda0=1e-4, rounds=35, **kw):
                                C.byref(r))
     return x, float(Rv[0]), GboResult(x, r.iters, STATUS[r.status], r.builds, r.changes, r.disp_builds, r.trials,
                                       r.resets, r.stalls, r.E, r.gsum, None)
+
+
+def sed_J(E):
+    """J(E) = ceil(-log10 E) of Sec. 5.2 (2^30 for E <= 0)."""
+    return int(lib().orc_sed_J(float(E)))
+
+
+def sed_perturb(xy, seed, inst, it, j, shared=0, amp=0.8):
+    """The perturbation of Sec. 5.2 of layout xy: candidate j of SED iteration it."""
+    x = _f64(xy)
+    out = np.empty_like(x)
+    lib().orc_sed_perturb(x.shape[0], _ptr(x, C.c_double), int(seed), int(inst), int(it), int(j), int(shared),
+                          float(amp), _ptr(out, C.c_double))
+    return out
+
+
+def sed_select(E, Ex, seed, inst, it):
+    """The select operator of Eq. 18 over candidate energies E, operated solution energy Ex."""
+    e = _f64(E)
+    return int(lib().orc_sed_select(e.size, _ptr(e, C.c_double), float(Ex), int(seed), int(inst), int(it)))
+
+
+@dataclass
+class SedOut:
+    x: np.ndarray
+    E: float
+    E0: float
+    iters: int
+    status: str
+    descents: int
+    m: np.ndarray
+    sel: np.ndarray
+    Ex: np.ndarray
+    Eb: np.ndarray
+
+
+def sed(n, R, seed, inst=0, s_iter=500, max_cand=25, e_feas=1e-25, shared=0, amp=0.8, init_mode=0, **kw):
+    """Algorithm SED (Sec. 5.2) on one instance.  The GBO inside stops at e_tol = e_feas unless
+    e_tol is given."""
+    kw.setdefault("e_tol", e_feas)
+    o = default_opts(**kw)
+    x = np.zeros((int(n), 2))
+    r = SedResult()
+    mt = np.zeros(max(s_iter, 1), dtype=np.int32)
+    st = np.zeros(max(s_iter, 1), dtype=np.int32)
+    ex = np.zeros(max(s_iter, 1))
+    eb = np.zeros(max(s_iter, 1))
+    lib().orc_sed(int(n), float(R), int(seed), int(inst), int(init_mode), C.byref(o), int(s_iter), int(max_cand),
+                  float(e_feas), int(shared), float(amp), _ptr(x, C.c_double), C.byref(r), _ptr(mt, C.c_int32),
+                  _ptr(st, C.c_int32), _ptr(ex, C.c_double), _ptr(eb, C.c_double))
+    k = r.iters
+    return SedOut(x, r.E, r.E0, k, STATUS[r.status], r.descents, mt[:k], st[:k], ex[:k], eb[:k])
 
 
 def max_overlap(xy, R):

@@ -36,6 +36,8 @@
  *   dense BFGS      Eq. 10 / Eq. 11 applied as written, used by the tests to
  *                   pin the limited-memory two-loop recursion.
  *   feasibility     Eq. 1 / Eq. 2: maximum pair and boundary overlap depth.
+ *   adjustment      Sec. 4.2, Eq. 12 (container adjustment by L-BFGS over (x, R)).
+ *   SED             Sec. 5.2, Algorithm SED and the select operator of Eq. 18.
  */
 #include <math.h>
 #include <pthread.h>
@@ -1177,4 +1179,129 @@ double orc_solve_batch(int num, const int32_t *n, const double *R, uint64_t seed
     free(th);
     free(off);
     return (double)(t1.tv_sec - t0.tv_sec) + 1e-9 * (double)(t1.tv_nsec - t0.tv_nsec);
+}
+
+/* ------------------------------------------------------------------------ */
+/* SED (Sec. 5.2, Algorithm SED): solution-space exploring and descent at a */
+/* fixed container radius.  From the GBO minimum of a random layout, each    */
+/* iteration perturbs the operated solution x into m = max(1, J(E(x)))       */
+/* candidates, descends each by GBO, and replaces x by the select operator   */
+/* of Eq. 18; the best solution x* is kept, and the search stops once        */
+/* E(x*) <= e_feas (the paper: 1e-25) or after s_iter iterations.            */
+/* Random numbers: Philox4x32-10 with key = seed; candidate j of iteration   */
+/* it draws counter (i, it, inst, 2^31 + j) for circle i, the select draw    */
+/* counter (0, it, inst, 2^30) (the initial layout uses c3 = 0).             */
+/* ------------------------------------------------------------------------ */
+
+/* J(E) = ceil(-log10 E) (Sec. 5.2); +2^30 for E <= 0. */
+int orc_sed_J(double E)
+{
+    if (!(E > 0.0)) return 1 << 30;
+    return (int)ceil(-log10(E));
+}
+
+/* The perturbation of Sec. 5.2: x'_i = x_i + r, y'_i = y_i + r with r ~ U(-amp, amp), amp = 0.8.
+ * shared = 0: r drawn independently for x and for y; shared = 1: one r for both, as printed. */
+void orc_sed_perturb(int n, const double *xy, uint64_t seed, int inst, int it, int j, int shared, double amp,
+                     double *out)
+{
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    for (int i = 0; i < n; i++) {
+        uint32_t ctr[4] = {(uint32_t)i, (uint32_t)it, (uint32_t)inst, 0x80000000u | (uint32_t)j}, w[4];
+        orc_philox4x32_10(ctr, key, w);
+        double rx = amp * (2.0 * u53(w[0], w[1]) - 1.0);
+        double ry = shared ? rx : amp * (2.0 * u53(w[2], w[3]) - 1.0);
+        out[2 * i] = xy[2 * i] + rx;
+        out[2 * i + 1] = xy[2 * i + 1] + ry;
+    }
+}
+
+/* select (Eq. 18).  The candidate of least energy when that energy is below E(x) (the first of
+ * equal ones).  Otherwise a draw with probability softmax(J(y)): with w_j = exp(J_j - max J),
+ * the first j whose running sum w_0 + ... + w_j exceeds u (w_0 + ... + w_{m-1}), u uniform in
+ * [0, 1) from the select counter. */
+int orc_sed_select(int m, const double *E, double Ex, uint64_t seed, int inst, int it)
+{
+    if (m <= 1) return 0;
+    int best = 0;
+    for (int j = 1; j < m; j++)
+        if (E[j] < E[best]) best = j;
+    if (E[best] < Ex) return best;
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t ctr[4] = {0u, (uint32_t)it, (uint32_t)inst, 0x40000000u}, w[4];
+    orc_philox4x32_10(ctr, key, w);
+    double u = u53(w[0], w[1]);
+    int Jmax = orc_sed_J(E[0]);
+    for (int j = 1; j < m; j++) {
+        int J = orc_sed_J(E[j]);
+        if (J > Jmax) Jmax = J;
+    }
+    double tot = 0.0;
+    for (int j = 0; j < m; j++) tot += exp((double)(orc_sed_J(E[j]) - Jmax));
+    double target = u * tot, run = 0.0;
+    for (int j = 0; j < m; j++) {
+        run += exp((double)(orc_sed_J(E[j]) - Jmax));
+        if (target < run) return j;
+    }
+    return m - 1;
+}
+
+typedef struct {
+    int iters;     /* SED iterations performed */
+    int status;    /* 0: E(x*) <= e_feas; 3: s_iter iterations without reaching it */
+    int descents;  /* GBO calls, the initial one included */
+    double E0;     /* energy after the initial descent */
+    double E;      /* E(x*) */
+} orc_sed_result;
+
+/* SED on one instance.  xy_best receives x*.  Traces (length s_iter, may be NULL): per iteration
+ * the candidate count m, the selected candidate, E(x) after the selection and E(x*). */
+int orc_sed(int n, double R, uint64_t seed, int inst, int init_mode, const orc_opts *o, int s_iter, int max_cand,
+            double e_feas, int shared, double amp, double *xy_best, orc_sed_result *res, int32_t *m_trace,
+            int32_t *sel_trace, double *Ex_trace, double *Eb_trace)
+{
+    memset(res, 0, sizeof(*res));
+    size_t vb = sizeof(double) * 2 * (size_t)(n > 0 ? n : 1);
+    double *x = (double *)malloc(vb);
+    double *cand = (double *)malloc(vb * (size_t)(max_cand > 0 ? max_cand : 1));
+    double *Ec = (double *)malloc(sizeof(double) * (size_t)(max_cand > 0 ? max_cand : 1));
+    orc_result r;
+    orc_init_positions(n, R, seed, inst, init_mode, x);
+    orc_gbo(n, x, R, o, &r, NULL);
+    res->descents = 1;
+    double Ex = r.E, Eb = r.E;
+    res->E0 = r.E;
+    memcpy(xy_best, x, sizeof(double) * 2 * (size_t)n);
+    int it = 0;
+    for (; it < s_iter; it++) {
+        if (Eb <= e_feas) break;
+        int m = orc_sed_J(Ex);
+        if (m < 1) m = 1;
+        if (m > max_cand) m = max_cand;
+        for (int j = 0; j < m; j++) {
+            double *c = cand + (size_t)j * 2 * (size_t)n;
+            orc_sed_perturb(n, x, seed, inst, it, j, shared, amp, c);
+            orc_gbo(n, c, R, o, &r, NULL);
+            Ec[j] = r.E;
+            res->descents++;
+        }
+        int sel = orc_sed_select(m, Ec, Ex, seed, inst, it);
+        memcpy(x, cand + (size_t)sel * 2 * (size_t)n, sizeof(double) * 2 * (size_t)n);
+        Ex = Ec[sel];
+        if (Ex < Eb) {
+            Eb = Ex;
+            memcpy(xy_best, x, sizeof(double) * 2 * (size_t)n);
+        }
+        if (m_trace) m_trace[it] = m;
+        if (sel_trace) sel_trace[it] = sel;
+        if (Ex_trace) Ex_trace[it] = Ex;
+        if (Eb_trace) Eb_trace[it] = Eb;
+    }
+    res->iters = it;
+    res->E = Eb;
+    res->status = Eb <= e_feas ? ORC_CONVERGED : ORC_MAXITER;
+    free(x);
+    free(cand);
+    free(Ec);
+    return 0;
 }
