@@ -13,6 +13,12 @@ the FP64 feasibility check.  Workloads:
   c4      one instance n = 100000, u = 0.85; FP32, whole-GPU descent (pair-gradient evaluations/s)
   c5      learned form: the MLP trained on 10^6 descent steps (instance-sweeps) of the batch
           distribution, then 1024 fresh instances n ~ U{300..1000}: warm start + descent vs plain
+  sed     SED (Sec. 5.2) on the first 1024 instances of the c3 batch at their radii: the start
+          (random layout + descent) and 10 iterations of perturbed candidates (up to 25 per
+          instance), all candidates of all instances descending together; FP32 + FP64 polish
+  adjust  container adjustment (Sec. 4.2, Eq. 12) of the first 304 instances of the c3 batch (one
+          resident wave: two instance blocks per SM), each from the layout its FP32 + polish
+          descent reached; lambda0 = 1e-4, 35 rounds of up to 2000 iterations
 Prints one JSON line.  --impl reference times the FP64 CPU oracle on the same workload instead.
 """
 from __future__ import annotations
@@ -155,7 +161,7 @@ class Clocks:
 # traffic is that ratio times its algorithmic bytes.  The figure holds for the kernel sources it
 # was measured on: once their hash changes the bench reports traffic as null.
 FUSED_TRAFFIC = {"sources": ["pecc_descend_kernel.cuh", "pecc_dev.cuh", "pecc_descend_fused.cu"],
-                 "sha256_16": "33038463da9ddd82", "dram_per_algorithmic_byte": 8.109419e9 / 250.712128817e9}
+                 "sha256_16": "c2763b2650e16661", "dram_per_algorithmic_byte": 8.638912e9 / 250.712128817e9}
 
 
 def fused_traffic(alg_bytes):
@@ -180,6 +186,430 @@ def algorithmic_bytes_descent(n, k, iters, trials, m, vec_bytes=8, pos_bytes=8):
     pass_b = pos_bytes + 4 + 24 + vec_bytes
     per_sweep = pass_b + 4 * m * vec_bytes + 2 * vec_bytes
     return float(np.sum(n * iters * per_sweep) + np.sum(n / k * trials * pass_b))
+
+
+# one resident wave of the adjustment's instance blocks on 152 SMs (two 256-thread blocks per SM):
+# about 58 000 binary64 quasi-Newton iterations per instance, 13 s per step
+ADJUST_INSTANCES = 304
+
+
+def adjust_bytes(n, iters, trials, visits, nnz_per_circle):
+    """Algorithmic bytes of the container adjustment, binary64, summed over the instances and all
+    rounds.  Per circle and iteration: the gradient norm (read g), the start copy (read x, write
+    zo), the two-loop's copy-in and final pass (dv = g; read dv and g, write dv), the secant pair
+    (read x, zo, gn, g, xb; write s, y in place) and its store (read 2, write 2 vectors): 19
+    double2 = 304 B.  Per pair visited by the two-loop: s, y and dv read and dv written in each
+    loop, 128 B.  Per line-search trial: the trial point (read zo, dv; write x) and one energy +
+    gradient pass (x, two row pointers, the row's column indices, write the gradient):
+    88 + 4 D B for D list entries per circle."""
+    n = np.asarray(n, dtype=np.float64)
+    return float(np.sum(n * (304.0 * iters + 128.0 * visits + (88.0 + 4.0 * nnz_per_circle) * trials)))
+
+
+def adjust_flops(n, iters, trials, visits, nnz_per_circle):
+    """Algorithmic binary64 flops of the container adjustment (sqrt and division one flop each).
+    Per circle and iteration: gradient norm 4, direction scaling and g'd 6, secant pair
+    differences, three dots and the displacement 22: 32.  Per pair visited by the two-loop: a dot
+    and an axpy in each loop, 16.  Per line-search trial: the trial point 4, the wall term 12 and
+    per directed list entry 14 (differences 2, squared distance 3, sqrt, 2 - l, the division, the
+    factor, two products, two sums, half an energy term)."""
+    n = np.asarray(n, dtype=np.float64)
+    return float(np.sum(n * (32.0 * iters + 16.0 * visits + (16.0 + 14.0 * nnz_per_circle) * trials)))
+
+
+# binary64 peak of the GB300: 2 FMA per SM per clock (the 1.25 TFLOP/s of the data sheet at
+# 152 SMs and 2.07 GHz), 2 flops each
+FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
+
+
+def adjust_start(ctx, torch, seed):
+    """The workload's starting layouts: one FP32 + polish descent from the Philox draw (untimed)."""
+    ctx.init_random(seed)
+    ctx.descend()
+    torch.cuda.synchronize()
+    return ctx.get_positions().clone()
+
+
+def run_adjust(args, rank, world, local):
+    import torch
+
+    from paper_2303_02650_gb300 import pecc
+
+    torch.cuda.set_device(local)
+    n, R, _, desc = workload("c3")
+    count = args.instances or ADJUST_INSTANCES
+    n, R = n[:count], R[:count]
+    desc = f"the first {n.size} instances of the " + desc
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    lam0, rounds = 1e-4, 35
+    seed = args.seed + 1_000_003 * rank
+    ctx = pecc.Context(n, precision=pecc.FP32_POLISH64)
+    ctx.set_radius(R)
+    x0 = adjust_start(ctx, torch, seed)
+    feas0, mo0 = ctx.check_feasible(1e-9)
+    feas_before = int(feas0.sum().item())
+    if args.adjust_max_iter:  # profiling case: fewer iterations per round, same starting layouts
+        ctx.close()
+        ctx = pecc.Context(n, precision=pecc.FP32_POLISH64, max_iter=args.adjust_max_iter)
+        ctx.set_radius(R)
+    rounds = args.adjust_rounds or rounds
+    R0 = torch.as_tensor(R, dtype=torch.float64, device="cuda")
+    Rt = R0.clone()
+    iters = torch.empty(n.size, dtype=torch.int32, device="cuda")
+    status = torch.empty_like(iters)
+    stats = torch.empty((n.size, 2), dtype=torch.int32, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 1 GB > L2
+
+    def step(ev):
+        flush.fill_(1.0)  # the working set of 304 instances (about 90 MB) would fit in L2
+        ev[0].record()
+        ctx.set_positions(x0)
+        Rt.copy_(R0)
+        ev[1].record()
+        ctx.adjust_container(None, lambda0=lam0, rounds=rounds, out=(Rt, iters, status), stats=stats)
+        ev[2].record()
+
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        for w in range(args.warmup):
+            step([torch.cuda.Event(enable_timing=True) for _ in range(3)])
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        clk.mark_start()
+        e0.record()
+        for s in range(args.steps):
+            step(evs[s])
+        e1.record()
+        torch.cuda.synchronize()
+        clk.mark_end()
+    ms_total = e0.elapsed_time(e1)
+    adj_ms = [ev[1].elapsed_time(ev[2]) for ev in evs]
+    # every step adjusts the same layouts (one block per instance, reductions in a fixed order:
+    # the same result each time); feasibility is checked once, at the adjusted radii
+    Rs = Rt.cpu().numpy()
+    it = iters.cpu().numpy().astype(np.float64)
+    st = status.cpu().numpy()
+    sts = stats.cpu().numpy().astype(np.float64)
+    ctx.set_radius(Rs)
+    feas, mo = ctx.check_feasible(1e-9)
+    feasible = int(feas.sum().item()) * args.steps
+    ctx.rebuild_neighbors(force=True, eval=0)
+    nnz_pc = ctx.neighbor_count() / max(1, int(n.sum()))
+    ctx.set_radius(R)
+    if dist:
+        ms_total, feasible = combine_ranks(dist, ms_total, feasible, "cuda")
+    value = feasible / (ms_total / 1e3)
+    alg = adjust_bytes(n, it, sts[:, 0], sts[:, 1], nnz_pc)
+    flops = adjust_flops(n, it, sts[:, 0], sts[:, 1], nnz_pc)
+    dom_ms = float(np.mean(adj_ms))
+    hbm, peak_kind = peaks()
+    achieved = alg / (dom_ms / 1e3) / 1e9
+    gflops = flops / (dom_ms / 1e3) / 1e9
+
+    # end to end: the starting layouts and radii from pinned host memory, the adjusted radii and
+    # layouts back, copies inside the timed region
+    xh = x0.cpu().pin_memory()
+    Rh = torch.as_tensor(R, dtype=torch.float64).pin_memory()
+    Rout = torch.empty_like(Rh).pin_memory()
+    xout = torch.empty_like(xh).pin_memory()
+    xd = torch.empty_like(x0)
+    e2e_ms = 0.0
+    for s in range(args.steps + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        xd.copy_(xh, non_blocking=True)
+        Rt.copy_(Rh, non_blocking=True)
+        ctx.set_positions(xd)
+        ctx.adjust_container(None, lambda0=lam0, rounds=rounds, out=(Rt, iters, status))
+        Rout.copy_(Rt, non_blocking=True)
+        xout.copy_(ctx.get_positions(), non_blocking=True)
+        torch.cuda.synchronize()
+        if s > 0:  # the first is untimed (first use of the host path)
+            e2e_ms += (time.perf_counter() - t0) * 1e3
+    e2e_value = feasible / (e2e_ms / 1e3)
+    h2d = int(xh.numel()) * 8 + int(Rh.numel()) * 8
+    d2h = int(xout.numel()) * 8 + int(Rout.numel()) * 8
+    grow = Rs / R - 1.0
+    line = {
+        "metric": "container adjustments/s (instances feasible, overlap<=1e-9, at the adjusted radius)",
+        "value": round(value, 3), "unit": "adjusted feasible packings/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_total / args.steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (Philox-drawn layouts put through one FP32 + polish descent; seeded instance manifest)",
+        "config": {"workload": "adjust: container adjustment (Sec. 4.2, Eq. 12) of " + desc +
+                               ", each instance from the layout its FP32 + polish descent reached",
+                   "lambda0": lam0, "rounds": rounds, "lbfgs_m": 10,
+                   "max_iter_per_round": args.adjust_max_iter or 2000,
+                   "instances_per_step": int(n.size), "circles_per_step": int(n.sum()),
+                   "feasible_before": feas_before,
+                   "l2": "L2 flushed (1 GB written) before every step; the working set of the default 304 "
+                         "instances is about 90 MB",
+                   "parallelism": f"instances sharded over {world} GPU(s), no collective on the data path"},
+        "success_rate": round(feasible / (args.steps * n.size * world), 4),
+        "radius_growth": {"mean": float(np.mean(grow)), "min": float(np.min(grow)), "max": float(np.max(grow))},
+        "iters_mean": round(float(it.mean()), 1), "trials_mean": round(float(sts[:, 0].mean()), 1),
+        "status_counts": np.bincount(st, minlength=5).tolist(),
+        "roofline": {"bound": "alu", "achieved": round(gflops, 1), "peak": round(FP64_PEAK_GFLOPS, 1),
+                     "unit": "GFLOP/s (binary64)", "frac": round(gflops / FP64_PEAK_GFLOPS, 4), "traffic": None,
+                     "kernel": "adjust_kernel", "peak_kind": "derived: 152 SMs x 2 FP64 FMA/clk x 2.07 GHz",
+                     "avg_launch_ms": round(dom_ms, 3), "algorithmic_flops_per_launch": flops,
+                     "hbm_view": {"achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                                  "frac": round(achieved / hbm, 4), "peak_kind": peak_kind,
+                                  "algorithmic_bytes_per_launch": alg},
+                     "neighbor_entries_per_circle": round(nnz_pc, 3)},
+        "e2e": {"value": round(e2e_value, 3), "unit": "adjusted feasible packings/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": 2 * args.steps,
+        "clocks": clk.summary(),
+    }
+    ctx.close()
+    if rank == 0:
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline_adjust(args, n, R, lam0, rounds)
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def oracle_adjust_sample(n, R, seed, idx, lam0, rounds, cores):
+    """The oracle on instances idx: its own GBO from the same Philox draw (untimed), then its
+    container adjustment, timed over all threads; returns (seconds, feasible count)."""
+    import concurrent.futures as cf
+
+    import oracle
+
+    def start(q):
+        x = oracle.init_positions(int(n[q]), float(R[q]), seed, inst=int(q))
+        return oracle.gbo(x, float(R[q]), k=1 if n[q] < 300 else (3 if n[q] < 500 else 5)).x
+
+    def adj(a):
+        q, x = a
+        xs, Rs, _ = oracle.adjust_container(x, float(R[q]), lambda0=lam0, rounds=rounds)
+        return oracle.max_overlap(xs, Rs)[0] <= 1e-9
+
+    with cf.ThreadPoolExecutor(cores) as ex:  # the oracle's C calls run without the GIL
+        starts = list(ex.map(start, idx))
+        t0 = time.perf_counter()
+        ok = list(ex.map(adj, zip(idx, starts)))
+        t = time.perf_counter() - t0
+    return t, int(sum(ok))
+
+
+def cpu_baseline_adjust(args, n, R, lam0, rounds, budget_s=15.0):
+    import oracle
+
+    oracle.build()
+    cores = os.cpu_count() or 1
+    t1, _ = oracle_adjust_sample(n, R, args.seed, [0], lam0, rounds, 1)
+    count = int(max(1, min(n.size, budget_s * cores / max(t1, 1e-3))))
+    t, feas = oracle_adjust_sample(n, R, args.seed, list(range(count)), lam0, rounds, cores)
+    return {"value": round(feas / t, 3), "unit": "adjusted feasible packings/s", "cores": cores, "kind": "oracle",
+            "sample": f"first {count} of the {n.size} instances, each from the oracle's own FP64 GBO result "
+                      f"(untimed), {cores} threads", "seconds": round(t, 2),
+            "success_rate": round(feas / count, 4)}
+
+
+SED_INSTANCES, SED_ITERS = 1024, 10
+
+
+def run_sed(args, rank, world, local):
+    import torch
+
+    from paper_2303_02650_gb300 import pecc
+
+    torch.cuda.set_device(local)
+    n, R, _, desc = workload("c3")
+    count = args.instances or SED_INSTANCES
+    n, R = n[:count], R[:count]
+    iters = args.sed_iters or SED_ITERS
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    M = 25
+    sed = pecc.Sed(n, precision=pecc.FP32_POLISH64, max_candidates=M, s_iter=iters)
+    sed.set_radius(R)
+    chk = pecc.Context(n, precision=pecc.FP64)  # the feasibility check of x* (S10)
+    chk.set_radius(R)
+    seed0 = args.seed + 1_000_003 * rank
+    kvec = np.array([1 if v < 300 else (3 if v < 500 else 5) for v in n], dtype=np.float64)
+    slot_n = np.repeat(n, M)
+    slot_k = np.repeat(kvec, M)
+    xb = torch.empty((int(n.sum()), 2), dtype=torch.float64, device="cuda")
+    feas_sum = torch.zeros((), dtype=torch.int64, device="cuda")
+
+    def step(s, rec):
+        """One pass: start, `iters` iterations, x* read and checked.  rec: per-descent events,
+        stats and candidate counts (device tensors, read after the timed region)."""
+        sed.start(seed0 + s)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * (iters + 1))]
+        sts, ms_ = [], []
+        for t in range(iters + 1):
+            if t > 0:
+                sed.prepare()
+            ms_.append(sed.m_counts() if t > 0 else None)
+            ev[2 * t].record()
+            if t > 0:
+                sed.descend()
+            ev[2 * t + 1].record()
+            sts.append(sed.stats())
+            if t > 0:
+                sed.select()
+        st = sed.get()
+        chk.set_positions(st["xbest"])
+        feas, _ = chk.check_feasible(1e-9)
+        rec.append((ev, sts, ms_, st["status"], st["iters"]))
+        return feas
+
+    # the start's descent runs inside sed.start (before the first event pair); its statistics are
+    # the first entry of sts.  Warm-up steps run the same body.
+    warm = []
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    recs = []
+    with Clocks(local) as clk:
+        for w in range(args.warmup):
+            feas_sum += step(10_000 + w, warm).to(torch.int64).sum()
+        feas_sum.zero_()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        clk.mark_start()
+        e0.record()
+        for s in range(args.steps):
+            feas_sum += step(s, recs).to(torch.int64).sum()
+        e1.record()
+        torch.cuda.synchronize()
+        clk.mark_end()
+    ms_total = e0.elapsed_time(e1)
+    feasible = int(feas_sum.item())
+    if dist:
+        ms_total, feasible = combine_ranks(dist, ms_total, feasible, "cuda")
+    value = feasible / (ms_total / 1e3)
+    # the iterations' descents: algorithmic bytes of the active slots over the events around them
+    desc_ms, desc_bytes, cands, status = [], [], [], []
+    for ev, sts, ms_, stt, itt in recs:
+        for t in range(1, iters + 1):
+            m = ms_[t].cpu().numpy()
+            st = sts[t].cpu().numpy()
+            act = (np.arange(M)[None, :] < m[:, None]).ravel()
+            if not act.any():
+                continue
+            b = algorithmic_bytes_descent(slot_n[act], slot_k[act], st[act, 8], st[act, 9], 10, 8, 8)
+            b += algorithmic_bytes_descent(slot_n[act], np.ones(int(act.sum())), st[act, 0] - st[act, 8],
+                                           st[act, 4] - st[act, 9], 10, 8, 16)
+            desc_ms.append(ev[2 * t].elapsed_time(ev[2 * t + 1]))
+            desc_bytes.append(b)
+            cands.append(int(act.sum()))
+        status.append(stt.cpu().numpy())
+    hbm, peak_kind = peaks()
+    dms = float(np.sum(desc_ms))
+    achieved = float(np.sum(desc_bytes)) / (dms / 1e3) / 1e9 if dms > 0 else 0.0
+    sts_all = np.concatenate(status)
+    # a plain descent of the same instances and seeds for the success rate the search starts from
+    e2e_ms, e2e_feas = 0.0, 0
+    Rh = torch.as_tensor(R, dtype=torch.float64).pin_memory()
+    xh = torch.empty((int(n.sum()), 2), dtype=torch.float64).pin_memory()
+    Rd = torch.empty(n.size, dtype=torch.float64, device="cuda")
+    for s in range(args.steps + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        Rd.copy_(Rh, non_blocking=True)
+        sed.set_radius(Rd)
+        sed.start(seed0 + 70_000 + s)
+        sed.iterate(iters)
+        st = sed.get()
+        chk.set_positions(st["xbest"])
+        feas, _ = chk.check_feasible(1e-9)
+        xh.copy_(st["xbest"], non_blocking=True)
+        fh = feas.cpu()
+        if s > 0:
+            e2e_ms += (time.perf_counter() - t0) * 1e3
+            e2e_feas += int(fh.sum())
+    start_only = float(np.mean([np.mean(r[4].cpu().numpy() == 0) for r in recs]))
+    line = {
+        "metric": "feasible packings/s found by SED (overlap<=1e-9 at the given radius)",
+        "value": round(value, 3), "unit": "feasible packings/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_total / args.steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+        "data": "synthetic (Philox-drawn layouts and perturbations; seeded instance manifest)",
+        "config": {"workload": f"sed: SED (Sec. 5.2) on the first {n.size} instances of the " + desc,
+                   "sed_iterations": iters, "max_candidates": M, "e_feas": 1e-25, "amp": 0.8,
+                   "precision": "FP32 bulk + FP64 polish (each candidate)", "instances_per_step": int(n.size),
+                   "circles_per_step": int(n.sum()),
+                   "l2": "working set per step > 129 MB L2 (candidate slots of all instances); no flush",
+                   "launch": dict(zip(["block_threads", "blocks_per_sm", "grid"], sed.launch_shape())),
+                   "parallelism": f"instances sharded over {world} GPU(s), no collective on the data path"},
+        "success_rate": round(feasible / (args.steps * n.size * world), 4),
+        "done_without_iterations": round(start_only, 4),
+        "status_counts": np.bincount(sts_all, minlength=4).tolist(),
+        "candidate_descents_per_step": round(float(np.sum(cands)) / args.steps, 1),
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                     "frac": round(achieved / hbm, 4) if hbm else None, "traffic": None,
+                     "kernel": "descend_fused_kernel (candidate slots of the SED iterations)",
+                     "peak_kind": peak_kind, "avg_launch_ms": round(dms / max(1, len(desc_ms)), 3),
+                     "algorithmic_bytes_per_launch": float(np.mean(desc_bytes)) if desc_bytes else 0.0,
+                     "iteration_descent_ms_per_step": round(dms / args.steps, 3)},
+        "e2e": {"value": round(e2e_feas / (e2e_ms / 1e3), 3), "unit": "feasible packings/s",
+                "h2d_bytes_per_step": int(n.size) * 8, "d2h_bytes_per_step": int(n.sum()) * 16 + int(n.size)},
+        "gpu_launches": None,
+        "clocks": clk.summary(),
+    }
+    # our kernels per step: the start (init, prepare, list, stamp, descent, select) and its
+    # statistics; per iteration prepare, list, stamp, descent, statistics, select; then the status
+    # kernel of sed.get and the check (set_pos, feasible)
+    line["gpu_launches"] = args.steps * (7 + 6 * iters + 3)
+    sed.close()
+    chk.close()
+    if rank == 0:
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline_sed(args, n, R, iters)
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def oracle_sed_sample(n, R, seed, idx, iters, cores):
+    """The oracle's SED on instances idx (threads over instances): (seconds, feasible count)."""
+    import concurrent.futures as cf
+
+    import oracle
+
+    def one(q):
+        r = oracle.sed(int(n[q]), float(R[q]), seed, inst=int(q), s_iter=iters)
+        return oracle.max_overlap(r.x, float(R[q]))[0] <= 1e-9
+
+    with cf.ThreadPoolExecutor(cores) as ex:
+        t0 = time.perf_counter()
+        ok = list(ex.map(one, idx))
+        t = time.perf_counter() - t0
+    return t, int(sum(ok))
+
+
+def cpu_baseline_sed(args, n, R, iters, budget_s=20.0):
+    import oracle
+
+    oracle.build()
+    cores = os.cpu_count() or 1
+    count = min(n.size, 2 * cores)
+    t, feas = oracle_sed_sample(n, R, args.seed, list(range(count)), iters, cores)
+    if t < budget_s / 2 and count < n.size:
+        count2 = int(min(n.size, count * budget_s / max(t, 1e-3)))
+        t, feas = oracle_sed_sample(n, R, args.seed, list(range(count2)), iters, cores)
+        count = count2
+    return {"value": round(feas / t, 3), "unit": "feasible packings/s", "cores": cores, "kind": "oracle",
+            "sample": f"first {count} of the {n.size} instances, SED with {iters} iterations, plain FP64 GBO, "
+                      f"{cores} threads", "seconds": round(t, 2), "success_rate": round(feas / count, 4)}
 
 
 def combine_ranks(dist, ms, count, device):
@@ -463,6 +893,10 @@ def run_reference(args, rank, world):
     import oracle
 
     oracle.build()
+    if args.workload == "adjust":
+        return run_reference_adjust(args, world)
+    if args.workload == "sed":
+        return run_reference_sed(args, world)
     n, R, prec, desc = workload(args.workload)
     cores = os.cpu_count() or 1
     per_step = max(1, min(n.size, 2 * cores))
@@ -485,6 +919,62 @@ def run_reference(args, rank, world):
         "cpu_baseline": {"value": round(value, 3), "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": round(value, 3), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def run_reference_adjust(args, world):
+    n, R, _, desc = workload("c3")
+    n, R = n[:ADJUST_INSTANCES], R[:ADJUST_INSTANCES]
+    desc = f"the first {n.size} instances of the " + desc
+    cores = os.cpu_count() or 1
+    per_step = max(1, cores)
+    oracle_adjust_sample(n, R, args.seed, [0], 1e-4, 35, 1)  # warm-up
+    tot_t, tot_f = 0.0, 0
+    for s in range(args.steps):
+        idx = [(s * per_step + i) % n.size for i in range(per_step)]
+        t, f = oracle_adjust_sample(n, R, args.seed, idx, 1e-4, 35, cores)
+        tot_t += t
+        tot_f += f
+    value = tot_f / tot_t
+    unit = "adjusted feasible packings/s"
+    sample = f"{per_step} instances per step, each from the oracle's own FP64 GBO result (untimed), {cores} threads"
+    print(json.dumps({
+        "impl": "reference", "metric": "container adjustments/s (instances feasible, overlap<=1e-9, at the "
+                                       "adjusted radius)",
+        "value": round(value, 3), "unit": unit, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(tot_t * 1e3 / args.steps, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "adjust: container adjustment (Sec. 4.2, Eq. 12) of " + desc, "precision": "FP64 oracle"},
+        "cpu_baseline": {"value": round(value, 3), "unit": unit, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": round(value, 3), "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def run_reference_sed(args, world):
+    n, R, _, desc = workload("c3")
+    n, R = n[:SED_INSTANCES], R[:SED_INSTANCES]
+    iters = args.sed_iters or SED_ITERS
+    cores = os.cpu_count() or 1
+    per_step = max(1, cores)
+    oracle_sed_sample(n, R, args.seed, [0], iters, 1)  # warm-up
+    tot_t, tot_f = 0.0, 0
+    for s in range(args.steps):
+        idx = [(s * per_step + i) % n.size for i in range(per_step)]
+        t, f = oracle_sed_sample(n, R, args.seed, idx, iters, cores)
+        tot_t += t
+        tot_f += f
+    value = tot_f / tot_t
+    unit = "feasible packings/s"
+    sample = f"{per_step} instances per step, SED with {iters} iterations, plain FP64 GBO, {cores} threads"
+    print(json.dumps({
+        "impl": "reference", "metric": "feasible packings/s found by SED (overlap<=1e-9 at the given radius)",
+        "value": round(value, 3), "unit": unit, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(tot_t * 1e3 / args.steps, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"sed: SED (Sec. 5.2) on the first {n.size} instances of the " + desc,
+                   "precision": "FP64 oracle"},
+        "cpu_baseline": {"value": round(value, 3), "unit": unit, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": round(value, 3), "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
 
@@ -542,7 +1032,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c3", choices=["c3", "c3-fp64", "c2", "c2-fp64", "c1", "c4", "c5"])
+    ap.add_argument("--workload", default="c3", choices=["c3", "c3-fp64", "c2", "c2-fp64", "c1", "c4", "c5", "adjust", "sed"])
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shape")
@@ -551,6 +1041,10 @@ def main():
     ap.add_argument("--smem-kb", type=float, default=0, help="dynamic shared memory per instance block at most (KB)")
     ap.add_argument("--launch", default="", help="fixed launch shape THREADSxBLOCKS_PER_SM (no autotune), e.g. 128x4")
     ap.add_argument("--instances", type=int, default=0, help="use only the first N instances (small profiling case)")
+    ap.add_argument("--adjust-max-iter", type=int, default=0,
+                    help="adjust workload: iterations per round at most (profiling case; default 2000)")
+    ap.add_argument("--adjust-rounds", type=int, default=0, help="adjust workload: rounds (profiling case; default 35)")
+    ap.add_argument("--sed-iters", type=int, default=0, help="sed workload: SED iterations per step (default 10)")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
@@ -561,6 +1055,10 @@ def main():
         run_reference(args, rank, world)
     elif args.workload == "c5":
         run_learned(args, rank, world, local)
+    elif args.workload == "adjust":
+        run_adjust(args, rank, world, local)
+    elif args.workload == "sed":
+        run_sed(args, rank, world, local)
     else:
         run_ours(args, rank, world, local)
 

@@ -336,12 +336,14 @@ pecc_status pecc_check_feasible_noalloc(const double *xy_dev, int32_t n, double 
  *   status_dev  device int32[num_instances]: status of the last round (1 stationary, 2 stalled,
  *               3 max_iter; 4: list capacity exceeded, or an instance of 16384 circles or more,
  *               which this call does not adjust; 0 for an empty instance)
+ *   stats_dev   device int32[num_instances][2] or NULL: line-search trials (energy + gradient
+ *               evaluations) and stored pairs visited by the two-loop recursion, over all rounds
  * Starts from the context's coordinates (those of the last descent, pecc_set_positions or
  * pecc_init_random) and replaces them with the adjusted layout.  Stream-ordered, asynchronous;
  * the first call allocates the binary64 secant pairs (lbfgs_m <= 10 slots per circle).
  * Errors: PECC_ERR_ARG for NULL pointers, rounds < 0, lambda0 < 0 or not finite, lbfgs_m > 10. */
 pecc_status pecc_adjust_container(pecc_ctx *ctx, double *R_dev, double lambda0, int32_t rounds, int32_t *iters_dev,
-                                  int32_t *status_dev);
+                                  int32_t *status_dev, int32_t *stats_dev);
 
 /* Self-test of the bounded wait of the grid barrier that the whole-GPU descent of large instances
  * uses (the wait is measured on %globaltimer; past its limit the waiting block raises an error
@@ -357,6 +359,93 @@ pecc_status pecc_selftest_grid_barrier(int64_t timeout_ns, int32_t *failed_host,
 
 /* Text of the last error on this context (or of the last failed pecc_create when ctx is NULL). */
 const char *pecc_last_error(pecc_ctx *ctx);
+
+/* ====================================================================================== SED
+ * The solution-space exploring and descent heuristic (Sec. 5.2, Algorithm SED) over a batch of
+ * instances at fixed container radii.
+ *   Start:     x_q <- GBO(random_solution(n_q, R_q)); x*_q <- x_q.
+ *   Iteration: unless E(x*_q) <= e_feas, instance q perturbs x_q into
+ *              m_q = max(1, J(E(x_q))) candidates, with J(E) = ceil(-log10 E) and m_q capped at
+ *              max_candidates.  Each candidate moves every circle by r ~ U(-amp, amp) in x and
+ *              in y.  Each candidate is descended by GBO, then x_q <- select(U) (Eq. 18): the
+ *              least candidate energy if it is below E(x_q), otherwise a draw with probabilities
+ *              softmax(J(y)).  Finally x*_q <- x_q when E(x_q) < E(x*_q).
+ * All the candidates of all instances descend together: the object owns a descent context with
+ * max_candidates slots per instance.  Each iteration runs on the device without waiting for the
+ * host.  The random numbers are Philox4x32-10 keyed by the seed:
+ *   - initial layout of instance q: counter (i, attempt, q, 0), as pecc_init_random;
+ *   - candidate j of iteration it: counter (i, it, q, 2^31 + j) for circle i;
+ *   - select draw: counter (0, it, q, 2^30), u = 53 bits of the first two words in [0, 1).
+ * Energies E are the descent's (pecc_get_energy) in the context's arithmetic; x and x* are
+ * binary64.  Instances must have fewer than 16384 circles (one block per candidate). */
+typedef struct pecc_sed pecc_sed;
+
+typedef struct {
+  int32_t max_candidates; /* candidate slots per instance, 1..64 (25: every J while E > 1e-25) */
+  int32_t s_iter;         /* SED iterations at most (the paper: 500) */
+  double e_feas;          /* stop an instance once E(x*) <= e_feas (the paper: 1e-25) */
+  double amp;             /* perturbation half-width (the paper: 0.8) */
+  int32_t shared_r;       /* 1: one r for both coordinates of a circle (the formula as printed);
+                             0: independent draws for x and y (default) */
+  int32_t check_every;    /* pecc_sed_iterate reads the count of running instances every this
+                             many iterations (one host synchronisation each) */
+} pecc_sed_config;
+
+/* Defaults: 25 candidates, 500 iterations, e_feas 1e-25, amp 0.8, independent draws, check 8. */
+void pecc_sed_config_default(pecc_sed_config *c);
+
+/* cfg: the instances (num_instances, n) and the descent's settings, used for every candidate
+ * (e_tol is GBO's own energy stop: set it to e_feas to descend candidates as far as SED asks).
+ * stream: cudaStream_t or NULL.  Errors: PECC_ERR_ARG (bad configuration, n >= 16384),
+ * PECC_ERR_OOM; the message is in pecc_sed_last_error(NULL). */
+pecc_status pecc_sed_create(const pecc_config *cfg, const pecc_sed_config *sc, void *stream, pecc_sed **out);
+pecc_status pecc_sed_destroy(pecc_sed *sed);
+const char *pecc_sed_last_error(pecc_sed *sed);
+
+/* R_dev: device double[num_instances], finite and > 0.  Synchronises the stream. */
+pecc_status pecc_sed_set_radius(pecc_sed *sed, const double *R_dev);
+
+/* Lines 1-3 of Algorithm SED for every instance: random layouts (cfg.init_mode), their GBO, and
+ * x = x* = the result.  Resets the iteration counter to 0.  Asynchronous. */
+pecc_status pecc_sed_start(pecc_sed *sed, uint64_t seed);
+
+/* Replaces the start: x = x* = x_dev (device double[2 * sum n], interleaved), E(x) = E(x*) =
+ * Ex_dev (device double[num_instances]), iteration counter it, random numbers keyed by seed. */
+pecc_status pecc_sed_set_state(pecc_sed *sed, const double *x_dev, const double *Ex_dev, uint64_t seed, int32_t it);
+
+/* Up to max_iterations SED iterations, each stopping instances whose E(x*) <= e_feas, and never
+ * past s_iter in all.  Stops early once no instance is running.  The stream is synchronised every
+ * check_every iterations and at the end.  ran_host: iterations run; left_host: instances still
+ * running (either may be NULL). */
+pecc_status pecc_sed_iterate(pecc_sed *sed, int32_t max_iterations, int32_t *ran_host, int32_t *left_host);
+
+/* The three steps of one iteration, for tests and custom drivers:
+ *   prepare: m_q and the candidates;
+ *   descend: GBO of the active candidates;
+ *   select:  Eq. 18 and the record.  E_cand_dev is device double[num_instances * max_candidates]
+ *            (slot q * max_candidates + j) replacing the descent's energies, or NULL.
+ * select advances the iteration counter.  All asynchronous. */
+pecc_status pecc_sed_prepare(pecc_sed *sed);
+pecc_status pecc_sed_descend(pecc_sed *sed);
+pecc_status pecc_sed_select(pecc_sed *sed, const double *E_cand_dev);
+
+/* Read the state (device pointers; any may be NULL):
+ *   x_dev, xbest_dev  double[2 * sum n]    x and x*
+ *   Ex_dev, Eb_dev    double[num]          E(x) and E(x*)
+ *   iters_dev         int32[num]           SED iterations each instance ran
+ *   status_dev        int32[num]           0 once E(x*) <= e_feas, else 3
+ *   m_dev, sel_dev    int32[num]           the last iteration's candidate count (0: done before
+ *                                          it) and selected candidate
+ * cand_dev: double[2 * max_candidates * sum n]: the candidate slots, instance by instance (slot j
+ * of instance q at 2 * (max_candidates * off_q + j * n_q)), or NULL. */
+pecc_status pecc_sed_get(pecc_sed *sed, double *x_dev, double *xbest_dev, double *Ex_dev, double *Eb_dev,
+                         int32_t *iters_dev, int32_t *status_dev, int32_t *m_dev, int32_t *sel_dev, double *cand_dev);
+
+/* The candidate descent context (owned by sed: do not destroy it, nor change its radii or
+ * positions), for pecc_get_stats, pecc_phase_times, pecc_get_launch and pecc_get_energy of the
+ * last descent (slot q * max_candidates + j; slots not active in that descent keep older values).
+ * NULL if sed is NULL. */
+pecc_ctx *pecc_sed_context(pecc_sed *sed);
 
 #ifdef __cplusplus
 }

@@ -63,7 +63,10 @@ __global__ void __launch_bounds__(kAdjT) adjust_kernel(AdjustParams P) {
     double R = P.R[q];
     double2 *x = P.x64 + D.off;
     if (n == 0 || D.big) {
-      if (tid == 0) { P.iters[q] = 0; P.status[q] = n == 0 ? 0 : 4; }
+      if (tid == 0) {
+        P.iters[q] = 0; P.status[q] = n == 0 ? 0 : 4;
+        if (P.stats) { P.stats[2 * q] = 0; P.stats[2 * q + 1] = 0; }
+      }
       __syncthreads();
       continue;
     }
@@ -78,7 +81,7 @@ __global__ void __launch_bounds__(kAdjT) adjust_kernel(AdjustParams P) {
     uint32_t *ckey = P.ckey + D.off;
     int32_t *corder = P.corder + D.off, *cells = P.cells + D.cell_off;
 
-    int status = 3, iters = 0, cnt = 0, len = 1;
+    int status = 3, iters = 0, cnt = 0, len = 1, trials = 0, visits = 0;
     unsigned long long hcur = 0ull;
     double Dmax = 0.0;
     // list build with ANM bookkeeping; false on a capacity overflow
@@ -156,6 +159,7 @@ __global__ void __launch_bounds__(kAdjT) adjust_kernel(AdjustParams P) {
             head = 0;
           }
           // ---- two-loop recursion (Nocedal & Wright, Alg. 7.4) over the stored pairs; q in dv
+          visits += count;
           for (int i = tid; i < n; i += T) dv[i] = g[i];
           double qR = gR;
           for (int c = count - 1; c >= 0; --c) {
@@ -237,6 +241,7 @@ __global__ void __launch_bounds__(kAdjT) adjust_kernel(AdjustParams P) {
             }
             R = Ro + al * dR;
             __syncthreads();
+            ++trials;
             eval(gn, R, lam, Ut, gnR);
             if (Ut <= U0 + P.c1 * al * gd) { accepted = true; break; }
             al *= 0.5;
@@ -291,7 +296,10 @@ __global__ void __launch_bounds__(kAdjT) adjust_kernel(AdjustParams P) {
       const double2 v = x[i];
       if (P.x32) P.x32[D.off + i] = make_float2((float)v.x, (float)v.y);
     }
-    if (tid == 0) { P.R[q] = R; P.iters[q] = iters; P.status[q] = status; }
+    if (tid == 0) {
+      P.R[q] = R; P.iters[q] = iters; P.status[q] = status;
+      if (P.stats) { P.stats[2 * q] = trials; P.stats[2 * q + 1] = visits; }
+    }
     __syncthreads();
   }
 }

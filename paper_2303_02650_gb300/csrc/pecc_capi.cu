@@ -36,6 +36,7 @@ struct pecc_ctx {
   uint64_t *skey = nullptr;
   int32_t *rp = nullptr, *col = nullptr, *rp_s = nullptr, *col_s = nullptr;
   double2 *adjS = nullptr, *adjY = nullptr;  // binary64 secant pairs of the container adjustment
+  int32_t *num_dev = nullptr;  // set by an owning search (SED): the descent's instance count on the device
   uint32_t *ckey = nullptr, *ckey_s = nullptr;
   int32_t *corder = nullptr, *corder_s = nullptr, *cells = nullptr;
   int64_t *nnz = nullptr;
@@ -617,6 +618,7 @@ static DescendParams dparams(pecc_ctx *c, int phase) {
   p.desc = c->desc;
   p.out = c->out;
   p.num = c->num;
+  p.num_dev = c->num_dev;
   p.order = c->order;
   p.queue = c->queue + phase;
   p.x32 = c->x32;
@@ -823,7 +825,7 @@ pecc_status pecc_autotune(pecc_ctx *ctx, int32_t sweeps, uint64_t seed, int32_t 
 }
 
 pecc_status pecc_adjust_container(pecc_ctx *ctx, double *R_dev, double lambda0, int32_t rounds, int32_t *iters_dev,
-                                  int32_t *status_dev) {
+                                  int32_t *status_dev, int32_t *stats_dev) {
   pecc_status s = need_radius(ctx);
   if (s) return s;
   if (ctx->num == 0) return PECC_OK;
@@ -847,7 +849,7 @@ pecc_status pecc_adjust_container(pecc_ctx *ctx, double *R_dev, double lambda0, 
   p.xb = (double2 *)ctx->xw; p.xs = (double2 *)ctx->xbuild;
   p.S = ctx->adjS; p.Y = ctx->adjY;
   p.rp = ctx->rp; p.col = ctx->col; p.ckey = ctx->ckey; p.corder = ctx->corder; p.cells = ctx->cells;
-  p.iters = iters_dev; p.status = status_dev; p.queue = ctx->queue + 4;
+  p.iters = iters_dev; p.status = status_dev; p.queue = ctx->queue + 4; p.stats = stats_dev;
   const pecc_config &f = ctx->cfg;
   p.l_cut = f.l_cut; p.rebuild_disp = f.rebuild_disp; p.step_max = f.step_max; p.gsum_tol = f.gsum_tol;
   p.c1 = f.c1; p.curv_eps = f.curv_eps; p.lambda0 = lambda0;
@@ -1089,6 +1091,297 @@ pecc_status pecc_solve_host(pecc_ctx *ctx, const double *R_host, uint64_t seed, 
   if (feasible_host) CK(cudaMemcpyAsync(feasible_host, dfeas, ctx->num, cudaMemcpyDeviceToHost, ctx->stream));
   if (max_overlap_host) CK(cudaMemcpyAsync(max_overlap_host, dmo, sizeof(double) * ctx->num, cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
+  return PECC_OK;
+}
+
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ SED (Sec. 5.2)
+struct pecc_sed {
+  pecc_ctx *cand = nullptr;  // the candidate slots: instance q's slot j is descent instance q*M + j
+  pecc_sed_config sc{};
+  int num = 0, M = 0;
+  std::vector<int32_t> n;
+  std::vector<double> R;
+  int64_t total = 0;
+  cudaStream_t stream = nullptr;
+  std::vector<void *> allocs;
+  SedParams p{};
+  bool radius_set = false, started = false;
+  std::string err;
+};
+
+static pecc_status sfail(pecc_sed *s, pecc_status st, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (s) s->err = buf;
+  else g_create_err = buf;
+  return st;
+}
+
+#define SCK(call)                                                                               \
+  do {                                                                                          \
+    cudaError_t e_ = (call);                                                                    \
+    if (e_ != cudaSuccess) return sfail(sed, PECC_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+template <typename T> static pecc_status salloc(pecc_sed *sed, T **p, size_t count) {
+  void *v = nullptr;
+  const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+  cudaError_t e = cudaMalloc(&v, bytes);
+  if (e != cudaSuccess) return sfail(sed, PECC_ERR_OOM, "cudaMalloc(%zu bytes): %s", bytes, cudaGetErrorString(e));
+  sed->allocs.push_back(v);
+  *p = (T *)v;
+  return PECC_OK;
+}
+
+extern "C" {
+
+void pecc_sed_config_default(pecc_sed_config *c) {
+  std::memset(c, 0, sizeof *c);
+  c->max_candidates = 25;
+  c->s_iter = 500;
+  c->e_feas = 1e-25;
+  c->amp = 0.8;
+  c->shared_r = 0;
+  c->check_every = 8;
+}
+
+pecc_status pecc_sed_destroy(pecc_sed *sed) {
+  if (!sed) return PECC_OK;
+  cudaStreamSynchronize(sed->stream);
+  if (sed->cand) pecc_destroy(sed->cand);
+  for (void *v : sed->allocs) cudaFree(v);
+  delete sed;
+  return PECC_OK;
+}
+
+pecc_status pecc_sed_create(const pecc_config *cfg, const pecc_sed_config *sc, void *stream, pecc_sed **out) {
+  if (!out) return sfail(nullptr, PECC_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!cfg || !sc) return sfail(nullptr, PECC_ERR_ARG, "cfg or sed config is NULL");
+  if (sc->max_candidates < 1 || sc->max_candidates > 64)
+    return sfail(nullptr, PECC_ERR_ARG, "max_candidates must be in 1..64");
+  if (sc->s_iter < 0 || sc->check_every < 1) return sfail(nullptr, PECC_ERR_ARG, "s_iter >= 0 and check_every >= 1");
+  if (!(sc->amp >= 0.0) || !std::isfinite(sc->amp) || !(sc->e_feas >= 0.0))
+    return sfail(nullptr, PECC_ERR_ARG, "amp finite and >= 0, e_feas >= 0");
+  if (cfg->num_instances < 0 || (cfg->num_instances > 0 && !cfg->n))
+    return sfail(nullptr, PECC_ERR_ARG, "num_instances < 0 or n is NULL");
+  const int num = cfg->num_instances, M = sc->max_candidates;
+  if ((int64_t)num * M > (int64_t)1 << 30) return sfail(nullptr, PECC_ERR_ARG, "too many candidate slots");
+  for (int q = 0; q < num; ++q)
+    if (cfg->n[q] < 0 || cfg->n[q] >= kGridMinN)
+      return sfail(nullptr, PECC_ERR_ARG, "n[%d] must be in 0..%d (one block per candidate)", q, kGridMinN - 1);
+  pecc_sed *sed = new pecc_sed();
+  sed->sc = *sc;
+  sed->num = num;
+  sed->M = M;
+  sed->n.assign(cfg->n, cfg->n + num);
+  sed->stream = (cudaStream_t)stream;
+  for (int v : sed->n) sed->total += v;
+  auto bail = [&](pecc_status st) {
+    g_create_err = sed->err;
+    pecc_sed_destroy(sed);
+    return st;
+  };
+  std::vector<int32_t> cn((size_t)num * M);
+  for (int q = 0; q < num; ++q)
+    for (int j = 0; j < M; ++j) cn[(size_t)q * M + j] = sed->n[q];
+  pecc_config c2 = *cfg;
+  c2.num_instances = num * M;
+  c2.n = cn.data();
+  pecc_status st = pecc_create(&c2, stream, &sed->cand);
+  if (st) return bail(sfail(sed, st, "candidate context: %s", g_create_err.c_str()));
+  pecc_ctx *ctx = sed->cand;
+  SedParams &p = sed->p;
+  p.num = num;
+  p.M = M;
+  p.init_mode = cfg->init_mode;
+  p.shared_r = sc->shared_r ? 1 : 0;
+  p.from32 = cfg->precision == PECC_FP32 ? 1 : 0;
+  p.amp = sc->amp;
+  p.e_feas = sc->e_feas;
+  int32_t *nd = nullptr;
+  int64_t *off = nullptr;
+  double *Rd = nullptr;
+  if ((st = salloc(sed, &nd, num)) || (st = salloc(sed, &off, num + 1)) || (st = salloc(sed, &Rd, num)) ||
+      (st = salloc(sed, &p.x, sed->total)) || (st = salloc(sed, &p.xb, sed->total)) ||
+      (st = salloc(sed, &p.Ex, num)) || (st = salloc(sed, &p.Eb, num)) || (st = salloc(sed, &p.m, num)) ||
+      (st = salloc(sed, &p.sel, num)) || (st = salloc(sed, &p.done, num)) || (st = salloc(sed, &p.iters, num)) ||
+      (st = salloc(sed, &p.porder, num)) || (st = salloc(sed, &p.scan, num)) ||
+      (st = salloc(sed, &p.list, (size_t)num * M)) || (st = salloc(sed, &p.count, 1)) || (st = salloc(sed, &p.left, 1)) ||
+      (st = salloc(sed, &p.active, 1)))
+    return bail(st);
+  p.n = nd;
+  p.off = off;
+  p.R = Rd;
+  std::vector<int64_t> oh(num + 1, 0);
+  for (int q = 0; q < num; ++q) oh[q + 1] = oh[q] + sed->n[q];
+  std::vector<int32_t> po(num);
+  std::iota(po.begin(), po.end(), 0);
+  std::stable_sort(po.begin(), po.end(), [&](int a, int b) { return sed->n[a] > sed->n[b]; });
+  cudaStream_t s = sed->stream;
+  SCK(cudaMemcpyAsync(nd, sed->n.data(), sizeof(int32_t) * std::max(num, 0), cudaMemcpyHostToDevice, s));
+  SCK(cudaMemcpyAsync(off, oh.data(), sizeof(int64_t) * (num + 1), cudaMemcpyHostToDevice, s));
+  SCK(cudaMemcpyAsync(p.porder, po.data(), sizeof(int32_t) * std::max(num, 0), cudaMemcpyHostToDevice, s));
+  SCK(cudaMemsetAsync(p.iters, 0, sizeof(int32_t) * std::max(num, 1), s));
+  SCK(cudaMemsetAsync(p.done, 0, sizeof(int32_t) * std::max(num, 1), s));
+  SCK(cudaStreamSynchronize(s));
+  p.cdesc = ctx->desc;
+  p.cout = ctx->out;
+  p.c64 = ctx->x64;
+  p.c32 = ctx->x32;
+  // the descent processes the active slots the list step writes into its order array
+  p.list = ctx->order;
+  ctx->num_dev = p.count;
+  *out = sed;
+  return PECC_OK;
+}
+
+const char *pecc_sed_last_error(pecc_sed *sed) { return sed ? sed->err.c_str() : g_create_err.c_str(); }
+
+pecc_ctx *pecc_sed_context(pecc_sed *sed) { return sed ? sed->cand : nullptr; }
+
+pecc_status pecc_sed_set_radius(pecc_sed *sed, const double *R_dev) {
+  if (!sed) return PECC_ERR_ARG;
+  if (sed->num == 0) { sed->radius_set = true; return PECC_OK; }
+  if (!R_dev) return sfail(sed, PECC_ERR_ARG, "R_dev is NULL");
+  sed->R.resize(sed->num);
+  SCK(cudaMemcpyAsync(sed->R.data(), R_dev, sizeof(double) * sed->num, cudaMemcpyDeviceToHost, sed->stream));
+  SCK(cudaStreamSynchronize(sed->stream));
+  std::vector<double> R2((size_t)sed->num * sed->M);
+  for (int q = 0; q < sed->num; ++q)
+    for (int j = 0; j < sed->M; ++j) R2[(size_t)q * sed->M + j] = sed->R[q];
+  double *tmp = nullptr;
+  SCK(cudaMalloc(&tmp, sizeof(double) * R2.size()));
+  cudaError_t e = cudaMemcpyAsync(tmp, R2.data(), sizeof(double) * R2.size(), cudaMemcpyHostToDevice, sed->stream);
+  pecc_status st = e ? PECC_ERR_CUDA : pecc_set_radius(sed->cand, tmp);
+  cudaStreamSynchronize(sed->stream);
+  cudaFree(tmp);
+  if (e) return sfail(sed, PECC_ERR_CUDA, "upload radii: %s", cudaGetErrorString(e));
+  if (st) return sfail(sed, st, "%s", pecc_last_error(sed->cand));
+  SCK(cudaMemcpyAsync((double *)sed->p.R, R_dev, sizeof(double) * sed->num, cudaMemcpyDeviceToDevice, sed->stream));
+  sed->radius_set = true;
+  return PECC_OK;
+}
+
+static pecc_status sed_descend(pecc_sed *sed) {
+  pecc_status st = pecc_descend(sed->cand, nullptr, nullptr);
+  return st ? sfail(sed, st, "%s", pecc_last_error(sed->cand)) : PECC_OK;
+}
+
+pecc_status pecc_sed_start(pecc_sed *sed, uint64_t seed) {
+  if (!sed) return PECC_ERR_ARG;
+  if (!sed->radius_set) return sfail(sed, PECC_ERR_ARG, "pecc_sed_set_radius has not been called");
+  sed->p.seed = seed;
+  sed->p.it = 0;
+  sed->started = true;
+  if (sed->num == 0) return PECC_OK;
+  SCK(cudaMemsetAsync(sed->p.iters, 0, sizeof(int32_t) * sed->num, sed->stream));
+  SCK(launch_sed_init(sed->p, sed->stream));
+  SCK(launch_sed_prepare(sed->p, 1, sed->stream));
+  pecc_status st = sed_descend(sed);
+  if (st) return st;
+  SCK(launch_sed_select(sed->p, nullptr, 1, sed->stream));
+  return PECC_OK;
+}
+
+pecc_status pecc_sed_set_state(pecc_sed *sed, const double *x_dev, const double *Ex_dev, uint64_t seed, int32_t it) {
+  if (!sed) return PECC_ERR_ARG;
+  if (!sed->radius_set) return sfail(sed, PECC_ERR_ARG, "pecc_sed_set_radius has not been called");
+  if (it < 0) return sfail(sed, PECC_ERR_ARG, "it must be >= 0");
+  sed->p.seed = seed;
+  sed->p.it = it;
+  sed->started = true;
+  if (sed->num == 0) return PECC_OK;
+  if (!x_dev || !Ex_dev) return sfail(sed, PECC_ERR_ARG, "NULL state");
+  const size_t xb = sizeof(double2) * (size_t)sed->total;
+  SCK(cudaMemcpyAsync(sed->p.x, x_dev, xb, cudaMemcpyDeviceToDevice, sed->stream));
+  SCK(cudaMemcpyAsync(sed->p.xb, x_dev, xb, cudaMemcpyDeviceToDevice, sed->stream));
+  SCK(cudaMemcpyAsync(sed->p.Ex, Ex_dev, sizeof(double) * sed->num, cudaMemcpyDeviceToDevice, sed->stream));
+  SCK(cudaMemcpyAsync(sed->p.Eb, Ex_dev, sizeof(double) * sed->num, cudaMemcpyDeviceToDevice, sed->stream));
+  SCK(cudaMemsetAsync(sed->p.iters, 0, sizeof(int32_t) * sed->num, sed->stream));
+  SCK(cudaMemsetAsync(sed->p.done, 0, sizeof(int32_t) * sed->num, sed->stream));
+  return PECC_OK;
+}
+
+pecc_status pecc_sed_prepare(pecc_sed *sed) {
+  if (!sed) return PECC_ERR_ARG;
+  if (!sed->started) return sfail(sed, PECC_ERR_ARG, "pecc_sed_start or pecc_sed_set_state first");
+  SCK(launch_sed_prepare(sed->p, 0, sed->stream));
+  return PECC_OK;
+}
+
+pecc_status pecc_sed_descend(pecc_sed *sed) {
+  if (!sed) return PECC_ERR_ARG;
+  if (!sed->started) return sfail(sed, PECC_ERR_ARG, "pecc_sed_start or pecc_sed_set_state first");
+  return sed->num ? sed_descend(sed) : PECC_OK;
+}
+
+pecc_status pecc_sed_select(pecc_sed *sed, const double *E_cand_dev) {
+  if (!sed) return PECC_ERR_ARG;
+  if (!sed->started) return sfail(sed, PECC_ERR_ARG, "pecc_sed_start or pecc_sed_set_state first");
+  SCK(launch_sed_select(sed->p, E_cand_dev, 0, sed->stream));
+  sed->p.it += 1;
+  return PECC_OK;
+}
+
+pecc_status pecc_sed_get(pecc_sed *sed, double *x_dev, double *xbest_dev, double *Ex_dev, double *Eb_dev,
+                         int32_t *iters_dev, int32_t *status_dev, int32_t *m_dev, int32_t *sel_dev, double *cand_dev) {
+  if (!sed) return PECC_ERR_ARG;
+  if (sed->num == 0) return PECC_OK;
+  cudaStream_t s = sed->stream;
+  const size_t xb = sizeof(double2) * (size_t)sed->total, eb = sizeof(double) * sed->num, ib = sizeof(int32_t) * sed->num;
+  if (x_dev) SCK(cudaMemcpyAsync(x_dev, sed->p.x, xb, cudaMemcpyDeviceToDevice, s));
+  if (xbest_dev) SCK(cudaMemcpyAsync(xbest_dev, sed->p.xb, xb, cudaMemcpyDeviceToDevice, s));
+  if (Ex_dev) SCK(cudaMemcpyAsync(Ex_dev, sed->p.Ex, eb, cudaMemcpyDeviceToDevice, s));
+  if (Eb_dev) SCK(cudaMemcpyAsync(Eb_dev, sed->p.Eb, eb, cudaMemcpyDeviceToDevice, s));
+  if (iters_dev) SCK(cudaMemcpyAsync(iters_dev, sed->p.iters, ib, cudaMemcpyDeviceToDevice, s));
+  if (m_dev) SCK(cudaMemcpyAsync(m_dev, sed->p.m, ib, cudaMemcpyDeviceToDevice, s));
+  if (sel_dev) SCK(cudaMemcpyAsync(sel_dev, sed->p.sel, ib, cudaMemcpyDeviceToDevice, s));
+  if (status_dev) SCK(launch_sed_status(sed->p, status_dev, s));
+  if (cand_dev) {
+    pecc_status st = pecc_get_positions(sed->cand, cand_dev);
+    if (st) return sfail(sed, st, "%s", pecc_last_error(sed->cand));
+  }
+  return PECC_OK;
+}
+
+pecc_status pecc_sed_iterate(pecc_sed *sed, int32_t max_iterations, int32_t *ran_host, int32_t *left_host) {
+  if (!sed) return PECC_ERR_ARG;
+  if (!sed->started) return sfail(sed, PECC_ERR_ARG, "pecc_sed_start or pecc_sed_set_state first");
+  if (max_iterations < 0) return sfail(sed, PECC_ERR_ARG, "max_iterations must be >= 0");
+  int ran = 0;
+  int32_t left = 0;
+  if (sed->num > 0) {
+    // the instances not done yet: the list step counts those with candidates (the prepared
+    // candidates are drawn again, identically, by the first iteration below)
+    SCK(launch_sed_prepare(sed->p, 0, sed->stream));
+    SCK(cudaMemcpyAsync(&left, sed->p.active, sizeof(int32_t), cudaMemcpyDeviceToHost, sed->stream));
+    SCK(cudaStreamSynchronize(sed->stream));
+  }
+  while (left > 0 && ran < max_iterations && sed->p.it < sed->sc.s_iter) {
+    SCK(launch_sed_prepare(sed->p, 0, sed->stream));
+    pecc_status st = sed_descend(sed);
+    if (st) return st;
+    SCK(launch_sed_select(sed->p, nullptr, 0, sed->stream));
+    sed->p.it += 1;
+    ++ran;
+    if (ran % sed->sc.check_every == 0) {
+      SCK(cudaMemcpyAsync(&left, sed->p.left, sizeof(int32_t), cudaMemcpyDeviceToHost, sed->stream));
+      SCK(cudaStreamSynchronize(sed->stream));
+    }
+  }
+  if (ran > 0) {
+    SCK(cudaMemcpyAsync(&left, sed->p.left, sizeof(int32_t), cudaMemcpyDeviceToHost, sed->stream));
+    SCK(cudaStreamSynchronize(sed->stream));
+  }
+  if (ran_host) *ran_host = ran;
+  if (left_host) *left_host = left;
   return PECC_OK;
 }
 

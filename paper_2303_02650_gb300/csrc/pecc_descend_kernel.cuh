@@ -718,12 +718,13 @@ __global__ void __launch_bounds__(MAXT, MINB)
 descend_kernel(DescendParams P) {
   extern __shared__ __align__(16) unsigned char dsm[];
   __shared__ Smem<A, MAXT / 32> S;
+  const int num = P.num_dev ? *P.num_dev : P.num;
   for (;;) {
     if (threadIdx.x == 0) S.q = atomicAdd(P.queue, 1);
     __syncthreads();
     const int qi = S.q;
     __syncthreads();
-    if (qi >= P.num) break;
+    if (qi >= num) break;
     descend_instance<A, MAXT / 32>(P, S, dsm, P.order[qi]);
   }
 }
@@ -737,12 +738,13 @@ descend_fused_kernel(DescendParams P32, DescendParams P64) {
   extern __shared__ __align__(16) unsigned char dsm[];
   __shared__ Smem<Arith32, MAXT / 32> S32;
   __shared__ Smem<ArithMix, MAXT / 32> S64;
+  const int num = P32.num_dev ? *P32.num_dev : P32.num;
   for (;;) {
     if (threadIdx.x == 0) S32.q = atomicAdd(P32.queue, 1);
     __syncthreads();
     const int qi = S32.q;
     __syncthreads();
-    if (qi >= P32.num) break;
+    if (qi >= num) break;
     const int q = P32.order[qi];
     descend_instance<Arith32, MAXT / 32>(P32, S32, dsm, q);
     descend_instance<ArithMix, MAXT / 32>(P64, S64, dsm, q);

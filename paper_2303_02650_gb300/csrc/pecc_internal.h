@@ -37,6 +37,7 @@ struct DescendParams {
   const InstDesc *desc;
   InstOut *out;
   int num;
+  const int32_t *num_dev;  // if set: the instance count, read from device memory at launch (<= num)
   const int32_t *order;  // processing order of instances (largest first)
   int32_t *queue;        // work counter, zeroed before each launch
   float2 *x32;
@@ -116,10 +117,36 @@ struct AdjustParams {
   uint32_t *ckey;
   int32_t *corder, *cells;
   int32_t *iters, *status, *queue;
+  int32_t *stats;  // optional: per instance {line-search trials, two-loop pair visits}
   double l_cut, rebuild_disp, step_max, gsum_tol, c1, curv_eps, lambda0;
   int m, max_iter, max_trials, anm, rounds;
 };
 cudaError_t launch_adjust(const AdjustParams &p, int grid, cudaStream_t s);
+
+// SED over a batch (pecc_sed.cu).  Instance q: n[q] circles at off[q] of the operated (x) and best
+// (xb) layouts; candidate slot q*M + j of the descent context (cdesc, cout, c64, c32).
+struct SedParams {
+  int num, M, it, init_mode, shared_r, from32;
+  uint64_t seed;
+  double amp, e_feas;
+  const int32_t *n;
+  const int64_t *off;
+  const double *R;
+  double2 *x, *xb;
+  double *Ex, *Eb;
+  int32_t *m, *sel, *done, *iters, *porder, *scan, *list;
+  int32_t *count;   // active slots of this iteration (the descent's instance count)
+  int32_t *active;  // instances with candidates this iteration
+  int32_t *left;    // instances not done after this iteration's select
+  const InstDesc *cdesc;
+  const InstOut *cout;
+  double2 *c64;
+  float2 *c32;
+};
+cudaError_t launch_sed_init(const SedParams &p, cudaStream_t s);
+cudaError_t launch_sed_prepare(const SedParams &p, int start, cudaStream_t s);  // prepare + active list
+cudaError_t launch_sed_select(const SedParams &p, const double *Ecand, int start, cudaStream_t s);
+cudaError_t launch_sed_status(const SedParams &p, int32_t *status, cudaStream_t s);
 int adjust_max_m();
 
 // Largest instance whose coordinates the block energy + gradient kernel stages in shared memory.

@@ -40,6 +40,11 @@ class Config(C.Structure):
                 ("polish_stall_window", C.c_int32), ("fuse_phases", C.c_int32)]
 
 
+class SedConfig(C.Structure):
+    _fields_ = [("max_candidates", C.c_int32), ("s_iter", C.c_int32), ("e_feas", C.c_double), ("amp", C.c_double),
+                ("shared_r", C.c_int32), ("check_every", C.c_int32)]
+
+
 _lib = None
 _EXPORTS = ["pecc_config_default", "pecc_create", "pecc_destroy", "pecc_set_radius", "pecc_set_positions",
             "pecc_init_random", "pecc_get_positions", "pecc_rebuild_neighbors", "pecc_rebuild_neighbors_ex",
@@ -49,7 +54,9 @@ _EXPORTS = ["pecc_config_default", "pecc_create", "pecc_destroy", "pecc_set_radi
             "pecc_check_feasible_noalloc", "pecc_mlp_num_params", "pecc_mlp_create", "pecc_mlp_destroy",
             "pecc_mlp_get_params", "pecc_mlp_set_params", "pecc_mlp_forward", "pecc_mlp_grad", "pecc_mlp_train_step",
             "pecc_features", "pecc_targets", "pecc_warm_start", "pecc_autotune", "pecc_selftest_grid_barrier",
-            "pecc_adjust_container"]
+            "pecc_adjust_container", "pecc_sed_config_default", "pecc_sed_create", "pecc_sed_destroy",
+            "pecc_sed_last_error", "pecc_sed_set_radius", "pecc_sed_start", "pecc_sed_set_state", "pecc_sed_iterate",
+            "pecc_sed_prepare", "pecc_sed_descend", "pecc_sed_select", "pecc_sed_get", "pecc_sed_context"]
 NOALLOC_MAX_N = 4096
 ENERGY_STAGE_BYTES = 96 * 1024  # PECC_ENERGY_STAGE_BYTES
 
@@ -97,7 +104,7 @@ def load(build_if_missing: bool = True):
         "pecc_phase_times": (st, [vp, C.POINTER(C.c_float)]),
         "pecc_check_feasible_noalloc": (st, [vp, C.c_int32, C.c_double, C.c_double, C.c_double, vp, vp, vp]),
         "pecc_selftest_grid_barrier": (st, [C.c_int64, C.POINTER(C.c_int32), C.POINTER(C.c_int64)]),
-        "pecc_adjust_container": (st, [vp, vp, C.c_double, C.c_int32, vp, vp]),
+        "pecc_adjust_container": (st, [vp, vp, C.c_double, C.c_int32, vp, vp, vp]),
         "pecc_mlp_num_params": (C.c_int32, []),
         "pecc_mlp_create": (st, [C.c_uint64, vp, C.POINTER(vp)]),
         "pecc_mlp_destroy": (st, [vp]),
@@ -110,6 +117,19 @@ def load(build_if_missing: bool = True):
         "pecc_targets": (st, [vp, vp, vp]),
         "pecc_warm_start": (st, [vp, vp, C.c_int32, vp]),
         "pecc_autotune": (st, [vp, C.c_int32, C.c_uint64, i32p, i32p]),
+        "pecc_sed_config_default": (None, [C.POINTER(SedConfig)]),
+        "pecc_sed_create": (st, [C.POINTER(Config), C.POINTER(SedConfig), vp, C.POINTER(vp)]),
+        "pecc_sed_destroy": (st, [vp]),
+        "pecc_sed_last_error": (C.c_char_p, [vp]),
+        "pecc_sed_set_radius": (st, [vp, vp]),
+        "pecc_sed_start": (st, [vp, C.c_uint64]),
+        "pecc_sed_set_state": (st, [vp, vp, vp, C.c_uint64, C.c_int32]),
+        "pecc_sed_iterate": (st, [vp, C.c_int32, i32p, i32p]),
+        "pecc_sed_prepare": (st, [vp]),
+        "pecc_sed_descend": (st, [vp]),
+        "pecc_sed_select": (st, [vp, vp]),
+        "pecc_sed_get": (st, [vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]),
+        "pecc_sed_context": (vp, [vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -381,14 +401,20 @@ class Context:
         self._check(self._L.pecc_warm_start(self.h, mlp.h, int(rounds), _ptr(acc)), "pecc_warm_start")
         return acc
 
-    def adjust_container(self, R, lambda0=1e-4, rounds=35):
+    def adjust_container(self, R, lambda0=1e-4, rounds=35, out=None, stats=None):
         """pecc_adjust_container: R (float64[num], device or host) -> (R*, iters, status) device
-        tensors; the context's coordinates become the adjusted layout."""
-        Rt = torch.as_tensor(R, dtype=torch.float64).to(self.dev).clone().contiguous()
-        iters = torch.empty(self.num, dtype=torch.int32, device=self.dev)
-        status = torch.empty(self.num, dtype=torch.int32, device=self.dev)
+        tensors; the context's coordinates become the adjusted layout.  out: optional (R, iters,
+        status) device tensors to reuse (R is then adjusted in place); stats: optional device
+        int32[num, 2] receiving {line-search trials, two-loop pair visits}."""
+        if out is None:
+            Rt = torch.as_tensor(R, dtype=torch.float64).to(self.dev).clone().contiguous()
+            iters = torch.empty(self.num, dtype=torch.int32, device=self.dev)
+            status = torch.empty(self.num, dtype=torch.int32, device=self.dev)
+        else:
+            Rt, iters, status = out
         self._check(self._L.pecc_adjust_container(self.h, _ptr(Rt), float(lambda0), int(rounds), _ptr(iters),
-                                                  _ptr(status)), "pecc_adjust_container")
+                                                  _ptr(status), _ptr(stats) if stats is not None else None),
+                    "pecc_adjust_container")
         return Rt, iters, status
 
     def autotune(self, sweeps=40, seed=99):
@@ -417,3 +443,129 @@ class Context:
         self._check(self._L.pecc_solve_host(self.h, a(R), C.c_uint64(seed), a(xy), a(iters), a(status), a(feas),
                                             a(mo)), "pecc_solve_host")
         return dict(xy=xy, iters=iters, status=status, feasible=feas, max_overlap=mo)
+
+
+class Sed:
+    """One pecc_sed: Algorithm SED (Sec. 5.2) over a batch of instances; every candidate of every
+    instance descends in one batched descent.  cfg: the descent's settings (pecc_config fields;
+    e_tol defaults to e_feas); sed: pecc_sed_config fields."""
+
+    def __init__(self, n, stream=None, max_candidates=25, s_iter=500, e_feas=1e-25, amp=0.8, shared_r=0,
+                 check_every=8, **cfg):
+        import numpy as np
+
+        self._L = load()
+        self.n = np.ascontiguousarray(n, dtype=np.int32)
+        self.num = int(self.n.shape[0])
+        self.total = int(self.n.sum())
+        cfg.setdefault("e_tol", e_feas)
+        self.cfg = default_config(**cfg)
+        self.cfg.num_instances = self.num
+        self.cfg.n = self.n.ctypes.data_as(C.POINTER(C.c_int32))
+        self.sc = SedConfig()
+        self._L.pecc_sed_config_default(C.byref(self.sc))
+        self.sc.max_candidates, self.sc.s_iter, self.sc.e_feas = int(max_candidates), int(s_iter), float(e_feas)
+        self.sc.amp, self.sc.shared_r, self.sc.check_every = float(amp), int(shared_r), int(check_every)
+        self.M = int(max_candidates)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        h = C.c_void_p()
+        rc = self._L.pecc_sed_create(C.byref(self.cfg), C.byref(self.sc), C.c_void_p(stream.cuda_stream), C.byref(h))
+        if rc != 0:
+            raise PeccError(f"pecc_sed_create: {ERRORS.get(rc, rc)}: {self._L.pecc_sed_last_error(None).decode()}")
+        self.h = h
+        self.ctx_h = C.c_void_p(self._L.pecc_sed_context(h))
+        self.dev = torch.device("cuda", torch.cuda.current_device())
+
+    def _check(self, rc, what):
+        if rc != 0:
+            raise PeccError(f"{what}: {ERRORS.get(rc, rc)}: {self._L.pecc_sed_last_error(self.h).decode()}")
+
+    def _check_ctx(self, rc, what):
+        if rc != 0:
+            raise PeccError(f"{what}: {ERRORS.get(rc, rc)}: {self._L.pecc_last_error(self.ctx_h).decode()}")
+
+    def stats(self, out=None):
+        """pecc_get_stats of the candidate context's last descent: int32 [num * M, 10] by slot."""
+        st = torch.empty((self.num * self.M, 10), dtype=torch.int32, device=self.dev) if out is None else out
+        self._check_ctx(self._L.pecc_get_stats(self.ctx_h, _ptr(st)), "pecc_get_stats")
+        return st
+
+    def launch_shape(self):
+        b, t, g = C.c_int32(), C.c_int32(), C.c_int32()
+        self._check_ctx(self._L.pecc_get_launch(self.ctx_h, C.byref(b), C.byref(t), C.byref(g)), "pecc_get_launch")
+        return b.value, t.value, g.value
+
+    def m_counts(self, out=None):
+        """The last prepared candidate counts (device int32[num]), without a synchronisation."""
+        m = torch.empty(self.num, dtype=torch.int32, device=self.dev) if out is None else out
+        self._check(self._L.pecc_sed_get(self.h, None, None, None, None, None, None, _ptr(m), None, None),
+                    "pecc_sed_get")
+        return m
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._L.pecc_sed_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_radius(self, R):
+        R = torch.as_tensor(R, dtype=torch.float64, device=self.dev).contiguous()
+        self._check(self._L.pecc_sed_set_radius(self.h, _ptr(R)), "pecc_sed_set_radius")
+
+    def start(self, seed: int):
+        self._check(self._L.pecc_sed_start(self.h, C.c_uint64(seed)), "pecc_sed_start")
+
+    def set_state(self, x, Ex, seed: int, it: int = 0):
+        x = torch.as_tensor(x, dtype=torch.float64, device=self.dev).contiguous()
+        Ex = torch.as_tensor(Ex, dtype=torch.float64, device=self.dev).contiguous()
+        assert x.numel() == 2 * self.total and Ex.numel() == self.num
+        self._check(self._L.pecc_sed_set_state(self.h, _ptr(x), _ptr(Ex), C.c_uint64(seed), int(it)),
+                    "pecc_sed_set_state")
+
+    def iterate(self, max_iterations):
+        ran, left = C.c_int32(), C.c_int32()
+        self._check(self._L.pecc_sed_iterate(self.h, int(max_iterations), C.byref(ran), C.byref(left)),
+                    "pecc_sed_iterate")
+        return ran.value, left.value
+
+    def prepare(self):
+        self._check(self._L.pecc_sed_prepare(self.h), "pecc_sed_prepare")
+
+    def descend(self):
+        self._check(self._L.pecc_sed_descend(self.h), "pecc_sed_descend")
+
+    def select(self, E_cand=None):
+        E = None if E_cand is None else torch.as_tensor(E_cand, dtype=torch.float64, device=self.dev).contiguous()
+        if E is not None:
+            assert E.numel() == self.num * self.M
+        self._check(self._L.pecc_sed_select(self.h, _ptr(E)), "pecc_sed_select")
+
+    def get(self, candidates=False):
+        """The state as a dict of device tensors: x, xbest, Ex, Eb, iters, status, m, sel (and
+        cand, the candidate slots, when asked)."""
+        f64 = dict(dtype=torch.float64, device=self.dev)
+        i32 = dict(dtype=torch.int32, device=self.dev)
+        out = {"x": torch.empty((self.total, 2), **f64), "xbest": torch.empty((self.total, 2), **f64),
+               "Ex": torch.empty(self.num, **f64), "Eb": torch.empty(self.num, **f64),
+               "iters": torch.empty(self.num, **i32), "status": torch.empty(self.num, **i32),
+               "m": torch.empty(self.num, **i32), "sel": torch.empty(self.num, **i32)}
+        cand = torch.empty((self.M * self.total, 2), **f64) if candidates else None
+        self._check(self._L.pecc_sed_get(self.h, _ptr(out["x"]), _ptr(out["xbest"]), _ptr(out["Ex"]), _ptr(out["Eb"]),
+                                         _ptr(out["iters"]), _ptr(out["status"]), _ptr(out["m"]), _ptr(out["sel"]),
+                                         _ptr(cand)), "pecc_sed_get")
+        if candidates:
+            out["cand"] = cand
+        return out

@@ -86,10 +86,20 @@ def test_short_runs_match_the_oracle(orc, rounds, iters_per_round):
     R = np.array([synth.radius(int(v), 0.86) for v in n])
     xy = np.concatenate([orc.init_positions(int(v), float(r), 77, inst=q) for q, (v, r) in enumerate(zip(n, R))])
     lam = 0.05
-    x, Rs, iters, status = _adjust(pecc, torch, n, R, xy, lam, rounds, precision=0, max_iter=iters_per_round)
+    with pecc.Context(n, precision=0, max_iter=iters_per_round) as c:
+        c.set_radius(R)
+        c.set_positions(torch.from_numpy(xy))
+        stats = torch.zeros((n.size, 2), dtype=torch.int32, device="cuda")
+        Rs, iters, status = c.adjust_container(R, lambda0=lam, rounds=rounds, stats=stats)
+        torch.cuda.synchronize()
+        x = c.get_positions().cpu().numpy()
+        Rs, iters, stats = Rs.cpu().numpy(), iters.cpu().numpy(), stats.cpu().numpy()
     for q, (a, b) in enumerate(zip(split(xy, n), split(x, n))):
         xr, Rr, res = orc.adjust_container(a, float(R[q]), lambda0=lam, rounds=rounds, max_iter=iters_per_round)
         assert iters[q] == res.iters, q
+        assert stats[q, 0] == res.trials, q  # line-search trials
+        # pairs visited by the two-loop: at most min(iterations so far in the round, m) per iteration
+        assert 0 <= stats[q, 1] <= iters[q] * 10
         assert Rs[q] == pytest.approx(Rr, rel=1e-9, abs=0.0), q
         np.testing.assert_allclose(b, xr, rtol=0, atol=1e-9 * float(R[q]))
 
