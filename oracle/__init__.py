@@ -48,7 +48,7 @@ class Opts(C.Structure):
                 ("e_tol", C.c_double), ("gsum_tol", C.c_double), ("c1", C.c_double),
                 ("curv_eps", C.c_double), ("m", C.c_int), ("max_iter", C.c_int), ("k", C.c_int),
                 ("partition", C.c_int), ("max_trials", C.c_int), ("anm", C.c_int),
-                ("prec32_pred", C.c_int)]
+                ("prec32_pred", C.c_int), ("part_seed", C.c_uint64), ("part_inst", C.c_int)]
 
 
 class Result(C.Structure):
@@ -89,6 +89,7 @@ def lib():
             "orc_pseudo_angle": (C.c_double, [C.c_double, C.c_double]),
             "orc_default_k": (C.c_int, [C.c_int]),
             "orc_partition": (None, [C.c_int, d, C.c_int, C.c_int, i32, i32]),
+            "orc_partition_seeded": (None, [C.c_int, d, C.c_int, C.c_int, C.c_uint64, C.c_int, i32, i32]),
             "orc_lbfgs_direction": (None, [C.c_int, C.c_int, d, d, d, d]),
             "orc_dense_bfgs_direction": (None, [C.c_int, C.c_int, d, d, d, d]),
             "orc_default_opts": (None, [_P(Opts)]),
@@ -237,13 +238,15 @@ def default_k(n):
     return lib().orc_default_k(n)
 
 
-def partition(xy, k, mode=0):
-    """Sec. 4.1 partitions (0 sector, 1 annulus, 2 fence): (perm[n], bounds[k+1])."""
+def partition(xy, k, mode=0, seed=0, inst=0):
+    """Sec. 4.1 partitions (0 sector, 1 annulus, 2 fence, 3 random with Philox key seed and
+    instance word inst): (perm[n], bounds[k+1])."""
     xy = _f64(xy)
     n = xy.shape[0]
     perm = np.zeros(n, dtype=np.int32)
     bounds = np.zeros(k + 1, dtype=np.int32)
-    lib().orc_partition(n, _ptr(xy, C.c_double), k, mode, _ptr(perm, C.c_int32), _ptr(bounds, C.c_int32))
+    lib().orc_partition_seeded(n, _ptr(xy, C.c_double), k, mode, int(seed), int(inst), _ptr(perm, C.c_int32),
+                               _ptr(bounds, C.c_int32))
     return perm, bounds
 
 

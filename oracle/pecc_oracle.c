@@ -445,6 +445,10 @@ static void batch_grad(const double *xy, double R, const int32_t *row_ptr, const
 /* [0, 2 pi) (the printed arctan(y/x) is read as the full polar angle):       */
 /*   y >= 0: 1 - x / (|x| + |y|),  y < 0: 3 + x / (|x| + |y|),  origin: 0.    */
 /* Annulus key: sqrt(x^2 + y^2).  Fence key: x.                               */
+/* Random (mode 3): "partition all circles into k sets randomly" is read as a */
+/* uniformly random order cut into the same contiguous sizes; circle i's key  */
+/* is 53 bits of Philox4x32-10 counter (i, 0, inst, 3 * 2^30) under the      */
+/* partition seed (the order by (key, index) is a uniform permutation).       */
 /* Stable by (key, index); the first n mod k batches hold ceil(n/k) circles.  */
 /* ------------------------------------------------------------------------ */
 double orc_pseudo_angle(double x, double y)
@@ -475,14 +479,21 @@ int orc_default_k(int n)
     return 5;
 }
 
-/* perm[n]: circles in partition order; bounds[k+1]: batch p is perm[bounds[p]..bounds[p+1]). */
-void orc_partition(int n, const double *xy, int k, int mode, int32_t *perm, int32_t *bounds)
+/* perm[n]: circles in partition order; bounds[k+1]: batch p is perm[bounds[p]..bounds[p+1]).
+ * seed, inst: the random partition's Philox key and instance word (other modes ignore them). */
+void orc_partition_seeded(int n, const double *xy, int k, int mode, uint64_t seed, int inst, int32_t *perm,
+                          int32_t *bounds)
 {
     keyidx *a = (keyidx *)malloc(sizeof(keyidx) * (size_t)(n > 0 ? n : 1));
+    uint32_t pkey[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
     for (int i = 0; i < n; i++) {
         double x = xy[2 * i], y = xy[2 * i + 1];
         double key;
-        if (mode == 1)
+        if (mode == 3) {
+            uint32_t ctr[4] = {(uint32_t)i, 0u, (uint32_t)inst, 0xC0000000u}, w[4];
+            orc_philox4x32_10(ctr, pkey, w);
+            key = u53(w[0], w[1]);
+        } else if (mode == 1)
             key = sqrt(x * x + y * y);
         else if (mode == 2)
             key = x;
@@ -497,6 +508,11 @@ void orc_partition(int n, const double *xy, int k, int mode, int32_t *perm, int3
     int q = n / k, r = n % k;
     bounds[0] = 0;
     for (int p = 0; p < k; p++) bounds[p + 1] = bounds[p] + q + (p < r ? 1 : 0);
+}
+
+void orc_partition(int n, const double *xy, int k, int mode, int32_t *perm, int32_t *bounds)
+{
+    orc_partition_seeded(n, xy, k, mode, 0, 0, perm, bounds);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -653,10 +669,12 @@ typedef struct {
     int m;               /* memory pairs */
     int max_iter;        /* sweeps */
     int k;               /* batches (0: by n) */
-    int partition;       /* 0 sector, 1 annulus, 2 fence */
+    int partition;       /* 0 sector, 1 annulus, 2 fence, 3 random */
     int max_trials;      /* backtracking trials per search */
     int anm;             /* 1: ANM deferral rebuilds on */
     int prec32_pred;     /* neighbor predicate in binary32 */
+    uint64_t part_seed;  /* random partition (3): Philox key */
+    int part_inst;       /* random partition: the instance word of the counter */
 } orc_opts;
 
 typedef struct {
@@ -682,6 +700,8 @@ void orc_default_opts(orc_opts *o)
     o->max_trials = 30;
     o->anm = 1;
     o->prec32_pred = 0;
+    o->part_seed = 0;
+    o->part_inst = 0;
 }
 
 typedef struct {
@@ -751,7 +771,7 @@ int orc_gbo(int n, double *xy, double R, const orc_opts *o, orc_result *res, dou
     int32_t *perm = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
     int32_t *bounds = (int32_t *)malloc(sizeof(int32_t) * (size_t)(k + 1));
     int32_t *batch_of = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
-    orc_partition(n, xy, k, o->partition, perm, bounds);
+    orc_partition_seeded(n, xy, k, o->partition, o->part_seed, o->part_inst, perm, bounds);
     for (int p = 0; p < k; p++)
         for (int a = bounds[p]; a < bounds[p + 1]; a++) batch_of[perm[a]] = p;
 

@@ -35,6 +35,52 @@ def test_partition_sizes_and_keys(orc):
     assert np.array_equal(perm, np.argsort(xy[:, 0], kind="stable"))
 
 
+def test_random_partition_is_a_uniform_permutation(orc):
+    """Mode 3: sizes as the other partitions; the order ignores the positions; over seeds the
+    first batch of 4 circles cut in 2 + 2 is each of the 6 pairs equally often (chi-square), and
+    every circle lands in each batch equally often."""
+    scipy_stats = pytest.importorskip("scipy.stats")
+    xy = synth.random_layout(1003, 30.0, seed=3)
+    for k in [1, 3, 7]:
+        perm, bounds = orc.partition(xy, k, mode=3, seed=5, inst=2)
+        sizes = np.diff(bounds)
+        assert sorted(perm) == list(range(1003)) and sizes.max() - sizes.min() <= 1
+        assert np.all(sizes[: 1003 % k] == math.ceil(1003 / k))
+    p1, _ = orc.partition(xy, 3, mode=3, seed=5, inst=2)
+    p2, _ = orc.partition(-xy[::-1] * 0.5, 3, mode=3, seed=5, inst=2)  # other positions, same keys
+    assert np.array_equal(p1, p2)
+    p3, _ = orc.partition(xy, 3, mode=3, seed=5, inst=3)
+    p4, _ = orc.partition(xy, 3, mode=3, seed=6, inst=2)
+    assert not np.array_equal(p1, p3) and not np.array_equal(p1, p4)
+    x4 = np.zeros((4, 2))
+    pairs = {}
+    where = np.zeros((4, 2))
+    draws = 6000
+    for s in range(draws):
+        perm, bounds = orc.partition(x4, 2, mode=3, seed=s, inst=0)
+        first = tuple(sorted(perm[:2]))
+        pairs[first] = pairs.get(first, 0) + 1
+        for b in range(2):
+            for i in perm[bounds[b]:bounds[b + 1]]:
+                where[i, b] += 1
+    assert len(pairs) == 6
+    assert scipy_stats.chisquare(list(pairs.values())).pvalue > 1e-4
+    assert scipy_stats.chisquare(where.ravel()).pvalue > 1e-4
+
+
+def test_gbo_with_random_partition_descends(orc):
+    """GBO over random batches lowers E monotonically and, with one batch, takes the same steps as
+    any other partition (one batch holds every circle)."""
+    n, R = 120, synth.radius(120, 0.75)
+    x0 = orc.init_positions(n, R, 4)
+    r = orc.gbo(x0, R, k=4, partition=3, part_seed=9, max_iter=60)
+    assert np.all(np.diff(r.trace) <= 1e-15)
+    assert r.E < r.trace[0]
+    a = orc.gbo(x0, R, k=1, partition=3, part_seed=9, max_iter=20)
+    b = orc.gbo(x0, R, k=1, partition=0, max_iter=20)
+    assert a.E == pytest.approx(b.E, rel=1e-9)
+
+
 def test_two_loop_equals_dense_bfgs_update(orc):
     """The limited-memory direction equals -H g with H built by Eq. 11 (beta of Eq. 10)
     applied pair by pair to gamma I, for any number of stored pairs."""
