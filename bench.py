@@ -16,6 +16,9 @@ the FP64 feasibility check.  Workloads:
   sed     SED (Sec. 5.2) on the first 1024 instances of the c3 batch at their radii: the start
           (random layout + descent) and 10 iterations of perturbed candidates (up to 25 per
           instance), all candidates of all instances descending together; FP32 + FP64 polish
+  ksweep  the batch-number study of Sec. 6.5: for n = 300, 500, 1000 and k = 1, 2, 3, 5, 7, 10, 15
+          (sector; at n = 1000 also annulus, fence and random), 608 instances per setting at
+          u = 0.83 descend from random layouts; mean device time per instance against k
   adjust  container adjustment (Sec. 4.2, Eq. 12) of the first 304 instances of the c3 batch (one
           resident wave: two instance blocks per SM), each from the layout its FP32 + polish
           descent reached; lambda0 = 1e-4, 35 rounds of up to 2000 iterations
@@ -161,7 +164,7 @@ class Clocks:
 # traffic is that ratio times its algorithmic bytes.  The figure holds for the kernel sources it
 # was measured on: once their hash changes the bench reports traffic as null.
 FUSED_TRAFFIC = {"sources": ["pecc_descend_kernel.cuh", "pecc_dev.cuh", "pecc_descend_fused.cu"],
-                 "sha256_16": "c2763b2650e16661", "dram_per_algorithmic_byte": 8.638912e9 / 250.712128817e9}
+                 "sha256_16": "0499380df5b27243", "dram_per_algorithmic_byte": 8.459172e9 / 250.712128817e9}
 
 
 def fused_traffic(alg_bytes):
@@ -418,6 +421,121 @@ def cpu_baseline_adjust(args, n, R, lam0, rounds, budget_s=15.0):
 
 
 SED_INSTANCES, SED_ITERS = 1024, 10
+KSWEEP_N = (300, 500, 1000)
+KSWEEP_K = (1, 2, 3, 5, 7, 10, 15)
+KSWEEP_INSTANCES = 608
+PART_NAMES = {0: "sector", 1: "annulus", 2: "fence", 3: "random"}
+
+
+def run_ksweep(args, rank, world, local):
+    """The batch-number and partition study (Sec. 6.5, the table of optimal batch numbers and
+    the partition figure): FP32 + FP64 polish descents from random layouts at u = 0.83."""
+    import torch
+
+    from paper_2303_02650_gb300 import pecc
+
+    torch.cuda.set_device(local)
+    I = args.instances or KSWEEP_INSTANCES
+    settings = [(n, 0) for n in KSWEEP_N] + [(1000, p) for p in (1, 2, 3)]
+    table, all_ms = {}, []
+    dom = None
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 1 GB > L2
+    with Clocks(local) as clk:
+        clk.mark_start()
+        for n0, part in settings:
+            n = np.full(I, n0, dtype=np.int32)
+            R = np.full(I, synth.radius(n0, 0.83))
+            rows = []
+            for k in KSWEEP_K:
+                ctx = pecc.Context(n, precision=pecc.FP32_POLISH64, k_batches=k, partition=part,
+                                   partition_seed=args.seed + 17)
+                ctx.set_radius(R)
+                ms = []
+                for s in range(args.warmup + args.steps):
+                    ctx.init_random(args.seed + s)  # the same layouts for every k and partition
+                    flush.fill_(float(s))
+                    a = torch.cuda.Event(enable_timing=True)
+                    b = torch.cuda.Event(enable_timing=True)
+                    a.record()
+                    ctx.descend()
+                    b.record()
+                    feas, _ = ctx.check_feasible(1e-9)
+                    torch.cuda.synchronize()
+                    if s >= args.warmup:
+                        ms.append(a.elapsed_time(b))
+                        st = ctx.get_stats().cpu().numpy()
+                        last = (st, int(feas.sum().item()))
+                st, fz = last
+                t = float(np.mean(ms))
+                all_ms.append(t)
+                rows.append({"k": k, "ms_per_descent": round(t, 2), "us_per_instance": round(1e3 * t / I, 2),
+                             "iters_mean": round(float(st[:, 0].mean()), 1), "success": round(fz / I, 4)})
+                if n0 == 1000 and part == 0 and k == 5:
+                    kv = np.full(I, 5.0)
+                    b_ = algorithmic_bytes_descent(n, kv, st[:, 8], st[:, 9], 10, 8, 8)
+                    b_ += algorithmic_bytes_descent(n, np.ones(I), st[:, 0] - st[:, 8], st[:, 4] - st[:, 9], 10, 8, 16)
+                    dom = (t, b_)
+                ctx.close()
+            key = f"n={n0} {PART_NAMES[part]}"
+            t1 = rows[0]["ms_per_descent"]
+            best = min(rows, key=lambda r: r["ms_per_descent"])
+            table[key] = {"rows": rows, "k_opt": best["k"], "ratio_opt_to_k1": round(best["ms_per_descent"] / t1, 4)}
+        clk.mark_end()
+    hbm, peak_kind = peaks()
+    t, b_ = dom
+    achieved = b_ / (t / 1e3) / 1e9
+    ratio = table["n=1000 sector"]["ratio_opt_to_k1"]
+    line = {
+        "metric": "descent time at the best batch number over k = 1 (n = 1000, sector; Sec. 6.5 ratio)",
+        "value": ratio, "unit": "ratio T_opt / T_k1", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(float(np.sum(all_ms)), 3), "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic (Philox-drawn layouts)",
+        "config": {"workload": f"ksweep: {I} instances per setting, u = 0.83, n in {list(KSWEEP_N)} (sector) and "
+                               f"n = 1000 with annulus, fence, random; k in {list(KSWEEP_K)}",
+                   "precision": "FP32 bulk + FP64 polish",
+                   "l2": "L2 flushed (1 GB written) before every timed descent; the same layouts for every k"},
+        "ksweep": table,
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                     "frac": round(achieved / hbm, 4), "traffic": None,
+                     "kernel": "descend_fused_kernel (n = 1000, k = 5, sector)", "peak_kind": peak_kind,
+                     "avg_launch_ms": round(t, 3), "algorithmic_bytes_per_launch": b_},
+        "e2e": None,
+        "e2e_note": "a study of the descent kernel across settings; the end-to-end path is the batch workload's",
+        "gpu_launches": len(all_ms) * (args.warmup + args.steps) * 5,
+        "clocks": clk.summary(),
+    }
+    if rank == 0:
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline_ksweep(args)
+        print(json.dumps(line), flush=True)
+
+
+def cpu_baseline_ksweep(args, count=16):
+    """The oracle's GBO (plain FP64, L-BFGS) at n = 1000, k = 1 and k = 5 (sector) on the same
+    kind of random layouts: mean seconds per descent and their ratio."""
+    import concurrent.futures as cf
+
+    import oracle
+
+    oracle.build()
+    cores = os.cpu_count() or 1
+    R = synth.radius(1000, 0.83)
+
+    def one(a):
+        q, k = a
+        x = oracle.init_positions(1000, R, args.seed + 7, inst=q)
+        t0 = time.perf_counter()
+        oracle.gbo(x, R, k=k)
+        return time.perf_counter() - t0
+
+    out = {}
+    with cf.ThreadPoolExecutor(cores) as ex:
+        for k in (1, 5):
+            ts = list(ex.map(one, [(q, k) for q in range(count)]))
+            out[k] = float(np.mean(ts))
+    return {"value": round(out[5] / out[1], 4), "unit": "ratio T_k5 / T_k1", "cores": cores, "kind": "oracle",
+            "sample": f"{count} descents of n = 1000 at each of k = 1 and k = 5, {cores} threads",
+            "seconds_per_descent": {"k1": round(out[1], 3), "k5": round(out[5], 3)}}
 
 
 def run_sed(args, rank, world, local):
@@ -1032,7 +1150,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c3", choices=["c3", "c3-fp64", "c2", "c2-fp64", "c1", "c4", "c5", "adjust", "sed"])
+    ap.add_argument("--workload", default="c3", choices=["c3", "c3-fp64", "c2", "c2-fp64", "c1", "c4", "c5", "adjust", "sed", "ksweep"])
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shape")
@@ -1059,6 +1177,8 @@ def main():
         run_adjust(args, rank, world, local)
     elif args.workload == "sed":
         run_sed(args, rank, world, local)
+    elif args.workload == "ksweep":
+        run_ksweep(args, rank, world, local)
     else:
         run_ours(args, rank, world, local)
 

@@ -71,8 +71,9 @@ enum {
     PECC_FP32_POLISH64 = 2  /* FP32 bulk descent, then an FP64 polish descent */
 };
 
-/* Geometric partitions of Sec. 4.1. */
-enum { PECC_PART_SECTOR = 0, PECC_PART_ANNULUS = 1, PECC_PART_FENCE = 2 };
+/* Partitions of Sec. 4.1: the three geometric ones, and the random one (a uniform Philox-keyed
+ * order of the circles, cut into the same contiguous batch sizes). */
+enum { PECC_PART_SECTOR = 0, PECC_PART_ANNULUS = 1, PECC_PART_FENCE = 2, PECC_PART_RANDOM = 3 };
 
 /* Initial layout of Sec. 5.1. */
 enum { PECC_INIT_DISK = 0, PECC_INIT_SQUARE = 1 };
@@ -124,6 +125,8 @@ typedef struct {
                                back to back in one block of one kernel (long polishes overlap other
                                instances' descents; pecc_phase_times then reports the fused kernel
                                as the first phase and 0 for the polish), 0 = two kernels; 1 */
+    uint64_t partition_seed;  /* PECC_PART_RANDOM: the Philox key; circle i of instance q draws
+                                 counter (i, 0, q, 3 * 2^30); 0 */
 } pecc_config;
 
 /* Fill *cfg with the defaults listed above (num_instances = 0, n = NULL). */

@@ -175,7 +175,7 @@ pecc_status pecc_create(const pecc_config *cfg, void *stream, pecc_ctx **out) {
   if (cfg->max_iter < 0 || cfg->polish_max_iter < 0 || cfg->max_trials < 1)
     return fail(nullptr, PECC_ERR_ARG, "bad iteration limits");
   if (cfg->k_batches < 0 || cfg->k_batches > kMaxK) return fail(nullptr, PECC_ERR_ARG, "k_batches must be in 0..64");
-  if (cfg->partition < 0 || cfg->partition > 2) return fail(nullptr, PECC_ERR_ARG, "bad partition");
+  if (cfg->partition < 0 || cfg->partition > 3) return fail(nullptr, PECC_ERR_ARG, "bad partition");
   if (cfg->init_mode < 0 || cfg->init_mode > 1) return fail(nullptr, PECC_ERR_ARG, "bad init_mode");
   if (!(cfg->nbr_capacity >= 1.0)) return fail(nullptr, PECC_ERR_ARG, "nbr_capacity must be >= 1");
   if (cfg->stall_window < 0 || !(cfg->stall_rel >= 0.0)) return fail(nullptr, PECC_ERR_ARG, "bad stall rule");
@@ -635,6 +635,7 @@ static DescendParams dparams(pecc_ctx *c, int phase) {
   p.l_cut = f.l_cut; p.rebuild_disp = f.rebuild_disp; p.step_max = f.step_max;
   p.e_tol = f.e_tol; p.gsum_tol = f.gsum_tol; p.c1 = f.c1; p.curv_eps = f.curv_eps; p.polish_gate = f.polish_gate;
   p.m = f.lbfgs_m; p.max_iter = f.max_iter; p.max_trials = f.max_trials; p.anm = f.anm; p.partition = f.partition;
+  p.part_seed = f.partition_seed;
   p.stall_rel = (phase == 2) ? f.polish_stall_rel : f.stall_rel;
   p.stall_window = (phase == 2) ? f.polish_stall_window : f.stall_window;
   p.t0 = c->t0;

@@ -220,7 +220,7 @@ __device__ __forceinline__ void descend_instance(const DescendParams &P, Smem<A,
     double x, y;
     if (A::kId == 0) { double2 v = P.x64[D.off + i]; x = v.x; y = v.y; }
     else { float2 v = P.x32[D.off + i]; x = v.x; y = v.y; }
-    skey[i] = sortable(part_key(x, y, P.partition));
+    skey[i] = sortable(P.partition == 3 ? random_part_key(P.part_seed, i, q) : part_key(x, y, P.partition));
   }
   __syncthreads();
   for (int i = tid; i < n; i += T) {

@@ -350,6 +350,14 @@ __device__ __forceinline__ double part_key(double x, double y, int mode) {
   return (y >= 0.0) ? __dsub_rn(1.0, t) : __dadd_rn(3.0, t);
 }
 
+// Key of the random partition of Sec. 4.1 (mode 3): 53 bits of Philox4x32-10 counter
+// (i, 0, q, 3 * 2^30) under the partition seed; the order by (key, index) is a uniform permutation.
+__device__ __forceinline__ double random_part_key(uint64_t seed, int i, int q) {
+  const uint4 w = philox4x32_10(make_uint4((uint32_t)i, 0u, (uint32_t)q, 0xC0000000u),
+                                make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+  return u53(w.x, w.y);
+}
+
 // ------------------------------------------------------- pair arithmetic ---
 // pair(): for circles a (the row owner) and b, returns the overlap depth d >= 0
 // (0 when l >= 2) and the gradient contribution to a: -2 d (a - b) / l.

@@ -220,7 +220,7 @@ __global__ void __launch_bounds__(256, 1) descend_grid_kernel(DescendParams P, i
       double x, y;
       if (A::kId == 0) { double2 v = P.x64[D.off + i]; x = v.x; y = v.y; }
       else { float2 v = P.x32[D.off + i]; x = v.x; y = v.y; }
-      const double key = part_key(x, y, P.partition);
+      const double key = P.partition == 3 ? random_part_key(P.part_seed, i, q) : part_key(x, y, P.partition);
       skey[i] = sortable(key);
       kmax = fmax(kmax, key);
       kmin_neg = fmax(kmin_neg, -key);

@@ -54,6 +54,7 @@ struct DescendParams {
   int32_t *meta;
   double l_cut, rebuild_disp, step_max, e_tol, gsum_tol, c1, curv_eps, polish_gate;
   int m, max_iter, max_trials, anm, partition;
+  uint64_t part_seed;     // random partition (3): Philox key
   double stall_rel;       // FP32 phase: stop when E fell by less than this over stall_window sweeps
   int stall_window;
   const long long *t0;    // %globaltimer at the start of the call (written by stamp_kernel)

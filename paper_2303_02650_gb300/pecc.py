@@ -14,7 +14,7 @@ import torch
 from . import build as _build
 
 FP64, FP32, FP32_POLISH64 = 0, 1, 2
-PART_SECTOR, PART_ANNULUS, PART_FENCE = 0, 1, 2
+PART_SECTOR, PART_ANNULUS, PART_FENCE, PART_RANDOM = 0, 1, 2, 3
 INIT_DISK, INIT_SQUARE = 0, 1
 STATUS = {0: "converged", 1: "stationary", 2: "stalled", 3: "max_iter", 4: "nbr_overflow", 5: "nonfinite",
           6: "timeout"}
@@ -37,7 +37,7 @@ class Config(C.Structure):
                 ("block_threads", C.c_int32), ("blocks_per_sm", C.c_int32), ("stall_rel", C.c_double),
                 ("stall_window", C.c_int32), ("polish_k", C.c_int32),
                 ("smem_per_block", C.c_int32), ("polish_stall_rel", C.c_double),
-                ("polish_stall_window", C.c_int32), ("fuse_phases", C.c_int32)]
+                ("polish_stall_window", C.c_int32), ("fuse_phases", C.c_int32), ("partition_seed", C.c_uint64)]
 
 
 class SedConfig(C.Structure):

@@ -265,6 +265,27 @@ def test_descend_short_runs_fp64(orc, k, sweeps):
         assert E[q] == pytest.approx(r.E, rel=1e-9)
 
 
+@pytest.mark.parametrize("part,k,sweeps", [(3, 3, 2), (3, 5, 3), (1, 3, 2), (2, 4, 2)])
+def test_descend_short_runs_other_partitions_fp64(orc, part, k, sweeps):
+    """The annulus, fence and random partitions of Sec. 4.1 (random: Philox-keyed order under
+    partition_seed, instance word q): a few binary64 sweeps follow the oracle's to 1e-9."""
+    torch, pecc = need_gpu()
+    n = np.array([300, 257, 640], dtype=np.int32)
+    R = _radii(n, 0.8)
+    with _ctx(pecc, n, R, precision=0, k_batches=k, max_iter=sweeps, partition=part, partition_seed=4242) as c:
+        c.init_random(33)
+        x0 = c.get_positions().cpu().numpy()
+        iters, status = c.descend()
+        x1 = c.get_positions().cpu().numpy()
+        E = c.get_energy().cpu().numpy()
+        iters = iters.cpu().numpy()
+    for q, (a, b) in enumerate(zip(split(x0, n), split(x1, n))):
+        r = orc.gbo(a, float(R[q]), k=k, max_iter=sweeps, partition=part, part_seed=4242, part_inst=q)
+        assert iters[q] == r.iters
+        np.testing.assert_allclose(b, r.x, rtol=0, atol=1e-9 * float(R[q]))
+        assert E[q] == pytest.approx(r.E, rel=1e-9)
+
+
 def _solve(pecc, torch, n, R, seed, **kw):
     with _ctx(pecc, n, R, **kw) as c:
         c.init_random(seed)

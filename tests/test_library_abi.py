@@ -58,7 +58,7 @@ def test_create_rejects_bad_arguments_without_gpu(libpath):
 
     L = pecc.load()
     n = (ctypes.c_int32 * 1)(10)
-    for field, bad in [("l_cut", 2.0), ("lbfgs_m", 11), ("k_batches", 65), ("partition", 3), ("step_max", 0.6)]:
+    for field, bad in [("l_cut", 2.0), ("lbfgs_m", 11), ("k_batches", 65), ("partition", 4), ("step_max", 0.6)]:
         c = pecc.default_config(**{field: bad})
         c.num_instances = 1
         c.n = ctypes.cast(n, ctypes.POINTER(ctypes.c_int32))
