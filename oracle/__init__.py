@@ -48,7 +48,7 @@ class Opts(C.Structure):
                 ("e_tol", C.c_double), ("gsum_tol", C.c_double), ("c1", C.c_double),
                 ("curv_eps", C.c_double), ("m", C.c_int), ("max_iter", C.c_int), ("k", C.c_int),
                 ("partition", C.c_int), ("max_trials", C.c_int), ("anm", C.c_int),
-                ("prec32_pred", C.c_int), ("part_seed", C.c_uint64), ("part_inst", C.c_int)]
+                ("prec32_pred", C.c_int), ("part_seed", C.c_uint64), ("part_inst", C.c_int), ("dense", C.c_int)]
 
 
 class Result(C.Structure):
@@ -97,6 +97,7 @@ def lib():
             "orc_max_overlap": (C.c_double, [C.c_int, d, C.c_double, d, d]),
             "orc_u_energy_grad": (C.c_double, [C.c_int, d, C.c_double, C.c_double, d]),
             "orc_adjust_container": (C.c_int, [C.c_int, d, d, _P(Opts), C.c_double, C.c_int, _P(Result)]),
+            "orc_bfgs_update": (None, [C.c_int, d, d, d]),
             "orc_sed_J": (C.c_int, [C.c_double]),
             "orc_sed_perturb": (None, [C.c_int, d, C.c_uint64, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, d]),
             "orc_sed_select": (C.c_int, [C.c_int, d, C.c_double, C.c_uint64, C.c_int, C.c_int]),
@@ -330,6 +331,13 @@ def adjust_container(xy, R, lambda0=1e-4, rounds=35, **kw):
                                C.byref(r))
     return x, float(Rv[0]), GboResult(x, r.iters, STATUS[r.status], r.builds, r.changes, r.disp_builds, r.trials,
                                       r.resets, r.stalls, r.E, r.gsum, None)
+
+
+def bfgs_update(H, s, y):
+    """Eq. 11 applied once to H (returns the updated copy), as the dense descent applies it."""
+    Hc = _f64(H).copy()
+    lib().orc_bfgs_update(Hc.shape[0], _ptr(Hc, C.c_double), _ptr(_f64(s), C.c_double), _ptr(_f64(y), C.c_double))
+    return Hc
 
 
 def sed_J(E):

@@ -675,6 +675,7 @@ typedef struct {
     int prec32_pred;     /* neighbor predicate in binary32 */
     uint64_t part_seed;  /* random partition (3): Philox key */
     int part_inst;       /* random partition: the instance word of the counter */
+    int dense;           /* 1: per-batch BFGS with an explicit inverse Hessian (Eq. 10, Eq. 11) */
 } orc_opts;
 
 typedef struct {
@@ -702,6 +703,94 @@ void orc_default_opts(orc_opts *o)
     o->prec32_pred = 0;
     o->part_seed = 0;
     o->part_inst = 0;
+    o->dense = 0;
+}
+
+/* The explicit inverse-Hessian approximation of one batch (Eq. 8, Eq. 10, Eq. 11).  It starts as
+ * I (the first step is a gradient step); before the first update it is rescaled to
+ * (s'y / y'y) I from that first pair, the usual initial scaling of BFGS; each accepted pair with
+ * enough curvature then applies Eq. 11, expanded as the symmetric rank-two change
+ *   H+ = H - rho (Hy) s' - rho s (Hy)' + (rho^2 y'Hy + rho) s s',  rho = 1 / (y's).
+ * A reset returns it to I. */
+typedef struct {
+    int dim, fresh;
+    double *H, *Hy;
+} dmem;
+
+static void dmem_reset(dmem *M)
+{
+    memset(M->H, 0, sizeof(double) * (size_t)M->dim * (size_t)M->dim);
+    for (int i = 0; i < M->dim; i++) M->H[(size_t)i * M->dim + i] = 1.0;
+    M->fresh = 1;
+}
+
+static void dmem_init(dmem *M, int dim)
+{
+    M->dim = dim;
+    M->H = (double *)malloc(sizeof(double) * (size_t)(dim > 0 ? dim : 1) * (size_t)(dim > 0 ? dim : 1));
+    M->Hy = (double *)malloc(sizeof(double) * (size_t)(dim > 0 ? dim : 1));
+    dmem_reset(M);
+}
+
+static void dmem_free(dmem *M)
+{
+    free(M->H);
+    free(M->Hy);
+}
+
+static void dmem_update(dmem *M, const double *s, const double *y, double sy, double yy);
+
+/* One update of Eq. 11 on a caller's H (n x n, row major, already scaled): the same code the
+ * dense descent runs, for the tests. */
+void orc_bfgs_update(int n, double *H, const double *s, const double *y)
+{
+    double sy = 0.0, yy = 0.0;
+    for (int i = 0; i < n; i++) {
+        sy += s[i] * y[i];
+        yy += y[i] * y[i];
+    }
+    dmem M;
+    M.dim = n;
+    M.fresh = 0;
+    M.H = H;
+    M.Hy = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    dmem_update(&M, s, y, sy, yy);
+    free(M.Hy);
+}
+
+/* d = -H g */
+static void dmem_direction(const dmem *M, const double *g, double *d)
+{
+    for (int r = 0; r < M->dim; r++) {
+        double v = 0.0;
+        const double *h = M->H + (size_t)r * M->dim;
+        for (int c = 0; c < M->dim; c++) v += h[c] * g[c];
+        d[r] = -v;
+    }
+}
+
+static void dmem_update(dmem *M, const double *s, const double *y, double sy, double yy)
+{
+    const int n = M->dim;
+    if (M->fresh) {
+        const double gam = sy / yy;
+        memset(M->H, 0, sizeof(double) * (size_t)n * (size_t)n);
+        for (int i = 0; i < n; i++) M->H[(size_t)i * n + i] = gam;
+        M->fresh = 0;
+    }
+    double yHy = 0.0;
+    for (int r = 0; r < n; r++) {
+        double v = 0.0;
+        const double *h = M->H + (size_t)r * n;
+        for (int c = 0; c < n; c++) v += h[c] * y[c];
+        M->Hy[r] = v;
+        yHy += y[r] * v;
+    }
+    const double rho = 1.0 / sy, cs = rho * rho * yHy + rho;
+    for (int r = 0; r < n; r++) {
+        double *h = M->H + (size_t)r * n;
+        for (int c = 0; c < n; c++) h[c] += -rho * (M->Hy[r] * s[c] + s[r] * M->Hy[c]) + cs * s[r] * s[c];
+    }
 }
 
 typedef struct {
@@ -792,6 +881,11 @@ int orc_gbo(int n, double *xy, double R, const orc_opts *o, orc_result *res, dou
     int maxnb = bounds[1] - bounds[0];
     lmem *mem = (lmem *)malloc(sizeof(lmem) * (size_t)k);
     for (int p = 0; p < k; p++) lmem_init(&mem[p], o->m, 2 * (bounds[p + 1] - bounds[p]));
+    dmem *dm = NULL;
+    if (o->dense) {
+        dm = (dmem *)malloc(sizeof(dmem) * (size_t)k);
+        for (int p = 0; p < k; p++) dmem_init(&dm[p], 2 * (bounds[p + 1] - bounds[p]));
+    }
     size_t vb = sizeof(double) * 2 * (size_t)maxnb;
     double *g = (double *)malloc(vb), *gn = (double *)malloc(vb), *d = (double *)malloc(vb);
     double *xo = (double *)malloc(vb), *s = (double *)malloc(vb), *y = (double *)malloc(vb);
@@ -827,17 +921,23 @@ int orc_gbo(int n, double *xy, double R, const orc_opts *o, orc_result *res, dou
                 xo[2 * a + 1] = xy[2 * mb[a] + 1];
             }
             int accepted = 0;
+            dmem *DM = dm ? &dm[p] : NULL;
             for (int attempt = 0; attempt < 2 && !accepted; attempt++) {
                 if (attempt == 1) {
-                    if (M->count == 0) break;
+                    if (DM ? DM->fresh : M->count == 0) break;
+                    if (DM) dmem_reset(DM);
                     M->count = 0;
                     M->head = 0;
                     res->resets++;
                 }
-                two_loop(M, g, d, alpha);
+                if (DM)
+                    dmem_direction(DM, g, d);
+                else
+                    two_loop(M, g, d, alpha);
                 double gd = dot(g, d, dim);
                 if (!(gd < 0.0)) {
-                    if (M->count > 0) {
+                    if (DM ? !DM->fresh : M->count > 0) {
+                        if (DM) dmem_reset(DM);
                         M->count = 0;
                         M->head = 0;
                         res->resets++;
@@ -890,7 +990,11 @@ int orc_gbo(int n, double *xy, double R, const orc_opts *o, orc_result *res, dou
             for (int i = 0; i < dim; i++) y[i] = gn[i] - g[i];
             double sy = dot(s, y, dim);
             double ns = sqrt(dot(s, s, dim)), ny = sqrt(dot(y, y, dim));
-            if (M->m > 0 && sy > o->curv_eps * ns * ny) lmem_push(M, s, y, sy);
+            if (DM) {
+                if (sy > o->curv_eps * ns * ny) dmem_update(DM, s, y, sy, ny * ny);
+            } else if (M->m > 0 && sy > o->curv_eps * ns * ny) {
+                lmem_push(M, s, y, sy);
+            }
         }
         /* ANM, called once per sweep (Algorithm GBO). */
         if (o->anm) {
@@ -923,6 +1027,10 @@ int orc_gbo(int n, double *xy, double R, const orc_opts *o, orc_result *res, dou
     free(xb);
     for (int p = 0; p < k; p++) lmem_free(&mem[p]);
     free(mem);
+    if (dm) {
+        for (int p = 0; p < k; p++) dmem_free(&dm[p]);
+        free(dm);
+    }
     free(g);
     free(gn);
     free(d);
