@@ -424,6 +424,8 @@ SED_INSTANCES, SED_ITERS = 1024, 10
 KSWEEP_N = (300, 500, 1000)
 KSWEEP_K = (1, 2, 3, 5, 7, 10, 15)
 KSWEEP_INSTANCES = 608
+KSWEEP_DENSE_N = (500, 1000)
+KSWEEP_DENSE_INSTANCES = 304
 PART_NAMES = {0: "sector", 1: "annulus", 2: "fence", 3: "random"}
 
 
@@ -435,8 +437,10 @@ def run_ksweep(args, rank, world, local):
     from paper_2303_02650_gb300 import pecc
 
     torch.cuda.set_device(local)
-    I = args.instances or KSWEEP_INSTANCES
-    settings = [(n, 0) for n in KSWEEP_N] + [(1000, p) for p in (1, 2, 3)]
+    dense = bool(args.dense)
+    I = args.instances or (KSWEEP_DENSE_INSTANCES if dense else KSWEEP_INSTANCES)
+    settings = [(n, 0) for n in KSWEEP_DENSE_N] if dense else [(n, 0) for n in KSWEEP_N] + [(1000, p) for p in (1, 2, 3)]
+    form = dict(precision=pecc.FP64, qn_dense=1) if dense else dict(precision=pecc.FP32_POLISH64)
     table, all_ms = {}, []
     dom = None
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 1 GB > L2
@@ -447,8 +451,7 @@ def run_ksweep(args, rank, world, local):
             R = np.full(I, synth.radius(n0, 0.83))
             rows = []
             for k in KSWEEP_K:
-                ctx = pecc.Context(n, precision=pecc.FP32_POLISH64, k_batches=k, partition=part,
-                                   partition_seed=args.seed + 17)
+                ctx = pecc.Context(n, k_batches=k, partition=part, partition_seed=args.seed + 17, **form)
                 ctx.set_radius(R)
                 ms = []
                 for s in range(args.warmup + args.steps):
@@ -471,9 +474,14 @@ def run_ksweep(args, rank, world, local):
                 rows.append({"k": k, "ms_per_descent": round(t, 2), "us_per_instance": round(1e3 * t / I, 2),
                              "iters_mean": round(float(st[:, 0].mean()), 1), "success": round(fz / I, 4)})
                 if n0 == 1000 and part == 0 and k == 5:
-                    kv = np.full(I, 5.0)
-                    b_ = algorithmic_bytes_descent(n, kv, st[:, 8], st[:, 9], 10, 8, 8)
-                    b_ += algorithmic_bytes_descent(n, np.ones(I), st[:, 0] - st[:, 8], st[:, 4] - st[:, 9], 10, 8, 16)
+                    if dense:  # per batch step: the two products with H and its rewrite, 4 N^2 words
+                        nb = 1000 // 5
+                        b_ = float(I) * float(st[:, 0].mean()) * 5 * 4 * (2 * nb) ** 2 * 8
+                    else:
+                        kv = np.full(I, 5.0)
+                        b_ = algorithmic_bytes_descent(n, kv, st[:, 8], st[:, 9], 10, 8, 8)
+                        b_ += algorithmic_bytes_descent(n, np.ones(I), st[:, 0] - st[:, 8], st[:, 4] - st[:, 9], 10, 8,
+                                                        16)
                     dom = (t, b_)
                 ctx.close()
             key = f"n={n0} {PART_NAMES[part]}"
@@ -486,18 +494,23 @@ def run_ksweep(args, rank, world, local):
     achieved = b_ / (t / 1e3) / 1e9
     ratio = table["n=1000 sector"]["ratio_opt_to_k1"]
     line = {
-        "metric": "descent time at the best batch number over k = 1 (n = 1000, sector; Sec. 6.5 ratio)",
+        "metric": "descent time at the best batch number over k = 1 (n = 1000, sector; Sec. 6.5 ratio)" +
+                  (", explicit per-batch inverse Hessian (Eq. 11)" if dense else ""),
         "value": ratio, "unit": "ratio T_opt / T_k1", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(float(np.sum(all_ms)), 3), "higher_is_better": False, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic (Philox-drawn layouts)",
-        "config": {"workload": f"ksweep: {I} instances per setting, u = 0.83, n in {list(KSWEEP_N)} (sector) and "
-                               f"n = 1000 with annulus, fence, random; k in {list(KSWEEP_K)}",
-                   "precision": "FP32 bulk + FP64 polish",
+        "vs_baseline": None, "dtype": "f64" if dense else "f32+f64", "data": "synthetic (Philox-drawn layouts)",
+        "config": {"workload": (f"ksweep --dense: {I} instances per setting, u = 0.83, n in {list(KSWEEP_DENSE_N)} "
+                                f"(sector), k in {list(KSWEEP_K)}, explicit inverse Hessian per batch (Eq. 10, Eq. 11)"
+                                if dense else
+                                f"ksweep: {I} instances per setting, u = 0.83, n in {list(KSWEEP_N)} (sector) and "
+                                f"n = 1000 with annulus, fence, random; k in {list(KSWEEP_K)}"),
+                   "precision": "binary64, dense BFGS" if dense else "FP32 bulk + FP64 polish",
                    "l2": "L2 flushed (1 GB written) before every timed descent; the same layouts for every k"},
         "ksweep": table,
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                      "frac": round(achieved / hbm, 4), "traffic": None,
-                     "kernel": "descend_fused_kernel (n = 1000, k = 5, sector)", "peak_kind": peak_kind,
+                     "kernel": ("dense_kernel" if dense else "descend_fused_kernel") + " (n = 1000, k = 5, sector)",
+                     "peak_kind": peak_kind,
                      "avg_launch_ms": round(t, 3), "algorithmic_bytes_per_launch": b_},
         "e2e": None,
         "e2e_note": "a study of the descent kernel across settings; the end-to-end path is the batch workload's",
@@ -506,13 +519,14 @@ def run_ksweep(args, rank, world, local):
     }
     if rank == 0:
         if not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline_ksweep(args)
+            line["cpu_baseline"] = cpu_baseline_ksweep(args, dense=dense)
         print(json.dumps(line), flush=True)
 
 
-def cpu_baseline_ksweep(args, count=16):
-    """The oracle's GBO (plain FP64, L-BFGS) at n = 1000, k = 1 and k = 5 (sector) on the same
-    kind of random layouts: mean seconds per descent and their ratio."""
+def cpu_baseline_ksweep(args, count=16, dense=False):
+    """The oracle's GBO (plain FP64; L-BFGS, or the explicit inverse Hessian with dense) at
+    n = 1000, k = 1 and k = 5 (sector) on the same kind of random layouts: mean seconds per
+    descent and their ratio."""
     import concurrent.futures as cf
 
     import oracle
@@ -525,7 +539,7 @@ def cpu_baseline_ksweep(args, count=16):
         q, k = a
         x = oracle.init_positions(1000, R, args.seed + 7, inst=q)
         t0 = time.perf_counter()
-        oracle.gbo(x, R, k=k)
+        oracle.gbo(x, R, k=k, dense=int(dense))
         return time.perf_counter() - t0
 
     out = {}
@@ -534,7 +548,8 @@ def cpu_baseline_ksweep(args, count=16):
             ts = list(ex.map(one, [(q, k) for q in range(count)]))
             out[k] = float(np.mean(ts))
     return {"value": round(out[5] / out[1], 4), "unit": "ratio T_k5 / T_k1", "cores": cores, "kind": "oracle",
-            "sample": f"{count} descents of n = 1000 at each of k = 1 and k = 5, {cores} threads",
+            "sample": f"{count} descents of n = 1000 at each of k = 1 and k = 5, {cores} threads" +
+                      (", explicit inverse Hessian" if dense else ", L-BFGS"),
             "seconds_per_descent": {"k1": round(out[1], 3), "k5": round(out[5], 3)}}
 
 
@@ -1163,6 +1178,8 @@ def main():
                     help="adjust workload: iterations per round at most (profiling case; default 2000)")
     ap.add_argument("--adjust-rounds", type=int, default=0, help="adjust workload: rounds (profiling case; default 35)")
     ap.add_argument("--sed-iters", type=int, default=0, help="sed workload: SED iterations per step (default 10)")
+    ap.add_argument("--dense", action="store_true",
+                    help="ksweep workload: the explicit per-batch inverse Hessian (Eq. 11), binary64")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

@@ -127,6 +127,12 @@ typedef struct {
                                as the first phase and 0 for the polish), 0 = two kernels; 1 */
     uint64_t partition_seed;  /* PECC_PART_RANDOM: the Philox key; circle i of instance q draws
                                  counter (i, 0, q, 3 * 2^30); 0 */
+    int32_t qn_dense;       /* 1: each batch keeps its inverse Hessian H_p explicitly and updates
+                               it by Eq. 11 (the paper's BFGS; H_p starts as I and is rescaled to
+                               (s'y / y'y) I before its first update), in place of the m secant
+                               pairs.  Needs PECC_FP64 and instances below 16384 circles; the
+                               first pecc_descend allocates sum over batches of (2 |B_p|)^2
+                               doubles (32 MB for n = 1000, k = 1).  lbfgs_m is then unused; 0 */
 } pecc_config;
 
 /* Fill *cfg with the defaults listed above (num_instances = 0, n = NULL). */

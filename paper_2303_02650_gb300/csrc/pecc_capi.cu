@@ -37,6 +37,9 @@ struct pecc_ctx {
   int32_t *rp = nullptr, *col = nullptr, *rp_s = nullptr, *col_s = nullptr;
   double2 *adjS = nullptr, *adjY = nullptr;  // binary64 secant pairs of the container adjustment
   int32_t *num_dev = nullptr;  // set by an owning search (SED): the descent's instance count on the device
+  double *denseH = nullptr;    // qn_dense: the inverse Hessians of every batch (allocated on first use)
+  int64_t *dense_hoff = nullptr;
+  bool dense_ran = false;
   uint32_t *ckey = nullptr, *ckey_s = nullptr;
   int32_t *corder = nullptr, *corder_s = nullptr, *cells = nullptr;
   int64_t *nnz = nullptr;
@@ -183,6 +186,9 @@ pecc_status pecc_create(const pecc_config *cfg, void *stream, pecc_ctx **out) {
     return fail(nullptr, PECC_ERR_ARG, "bad polish stall rule");
   if (cfg->polish_k < 0 || cfg->polish_k > kMaxK) return fail(nullptr, PECC_ERR_ARG, "polish_k must be in 0..64");
   if (cfg->smem_per_block < 0) return fail(nullptr, PECC_ERR_ARG, "smem_per_block must be >= 0");
+  if (cfg->qn_dense != 0 && cfg->qn_dense != 1) return fail(nullptr, PECC_ERR_ARG, "qn_dense must be 0 or 1");
+  if (cfg->qn_dense && cfg->precision != PECC_FP64)
+    return fail(nullptr, PECC_ERR_ARG, "qn_dense needs precision PECC_FP64");
   if (cfg->block_threads != 0 && (cfg->block_threads < 32 || cfg->block_threads % 32 ||
                                   cfg->block_threads > descend_max_block(cfg->precision == PECC_FP64 ? 0 : 1)))
     return fail(nullptr, PECC_ERR_ARG, "block_threads must be a multiple of 32 within the kernel's limit");
@@ -674,10 +680,53 @@ static cudaError_t enqueue_descend(pecc_ctx *c) {
   return cudaEventRecordWithFlags(c->ev[2], c->stream, cudaEventRecordExternal);
 }
 
+static pecc_status descend_dense(pecc_ctx *ctx, int32_t *iters_dev, int32_t *status_dev) {
+  for (int q = 0; q < ctx->num; ++q)
+    if (ctx->desc_h[q].big) return fail(ctx, PECC_ERR_ARG, "qn_dense: instance %d has 16384 circles or more", q);
+  if (!ctx->denseH) {
+    std::vector<int64_t> off(ctx->num);
+    int64_t words = 0;
+    for (int q = 0; q < ctx->num; ++q) {
+      off[q] = words;
+      words += dense_h_words(ctx->n[q], ctx->k[q]);
+    }
+    pecc_status s;
+    if ((s = dalloc<double>(ctx, &ctx->denseH, (size_t)std::max<int64_t>(words, 1)))) return s;
+    if ((s = dalloc<int64_t>(ctx, &ctx->dense_hoff, ctx->num))) return s;
+    CK(cudaMemcpyAsync(ctx->dense_hoff, off.data(), sizeof(int64_t) * ctx->num, cudaMemcpyHostToDevice, ctx->stream));
+  }
+  DenseParams p{};
+  p.desc = ctx->desc; p.out = ctx->out; p.num = ctx->num; p.order = ctx->order; p.queue = ctx->queue;
+  p.x = ctx->x64;
+  p.g = (double2 *)ctx->g; p.gn = (double2 *)ctx->gt; p.d = (double2 *)ctx->d; p.xo = (double2 *)ctx->xo;
+  p.xb = (double2 *)ctx->xb; p.xs = (double2 *)ctx->xbuild; p.hy = (double2 *)ctx->xw;
+  p.skey = ctx->skey; p.perm = ctx->perm; p.batch_of = (int32_t *)ctx->ckey_s;
+  p.rp = ctx->rp; p.col = ctx->col; p.ckey = ctx->ckey; p.corder = ctx->corder; p.cells = ctx->cells;
+  p.H = ctx->denseH; p.h_off = ctx->dense_hoff;
+  const pecc_config &f = ctx->cfg;
+  p.l_cut = f.l_cut; p.rebuild_disp = f.rebuild_disp; p.step_max = f.step_max; p.e_tol = f.e_tol;
+  p.gsum_tol = f.gsum_tol; p.c1 = f.c1; p.curv_eps = f.curv_eps;
+  p.max_iter = f.max_iter; p.max_trials = f.max_trials; p.anm = f.anm; p.partition = f.partition;
+  p.part_seed = f.partition_seed;
+  if (!ctx->ev[0])
+    for (int i = 0; i < 4; ++i) CK(cudaEventCreate(&ctx->ev[i]));
+  CK(cudaMemsetAsync(ctx->queue, 0, sizeof(int32_t), ctx->stream));
+  CK(cudaEventRecord(ctx->ev[0], ctx->stream));
+  CK(launch_dense(p, (int)std::min<int64_t>(ctx->num, (int64_t)ctx->num_sms * 2), ctx->stream));
+  CK(cudaEventRecord(ctx->ev[1], ctx->stream));
+  CK(cudaEventRecord(ctx->ev[2], ctx->stream));
+  ctx->dense_ran = true;
+  ctx->lists_prec = -1;
+  if (iters_dev || status_dev)
+    CK(launch_outputs(ctx->out, ctx->num, iters_dev, status_dev, nullptr, nullptr, nullptr, nullptr, ctx->stream));
+  return PECC_OK;
+}
+
 pecc_status pecc_descend(pecc_ctx *ctx, int32_t *iters_dev, int32_t *status_dev) {
   pecc_status s = need_radius(ctx);
   if (s) return s;
   if (ctx->num == 0) return PECC_OK;
+  if (ctx->cfg.qn_dense) return descend_dense(ctx, iters_dev, status_dev);
   for (int q = 0; q < ctx->num; ++q)
     if (ctx->n[q] > 65535 && !ctx->desc_h[q].big)
       return fail(ctx, PECC_ERR_ARG, "pecc_descend: instance %d has more than 65535 circles", q);
@@ -869,7 +918,7 @@ pecc_status pecc_get_stats(pecc_ctx *ctx, int32_t *stats_dev) {
 
 pecc_status pecc_phase_times(pecc_ctx *ctx, float *ms_host) {
   if (!ctx || !ms_host) return PECC_ERR_ARG;
-  if (!ctx->graph) return fail(ctx, PECC_ERR_ARG, "pecc_descend has not run");
+  if (!ctx->graph && !ctx->dense_ran) return fail(ctx, PECC_ERR_ARG, "pecc_descend has not run");
   CK(cudaEventSynchronize(ctx->ev[2]));
   float a = 0.f, b = 0.f, c = 0.f;
   CK(cudaEventElapsedTime(&a, ctx->ev[0], ctx->ev[1]));

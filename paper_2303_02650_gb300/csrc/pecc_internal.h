@@ -124,6 +124,28 @@ struct AdjustParams {
 };
 cudaError_t launch_adjust(const AdjustParams &p, int grid, cudaStream_t s);
 
+// GBO with the explicit inverse Hessian per batch (pecc_dense.cu); binary64, per-circle scratch of
+// the context (double2 each), H of instance q at H + h_off[q].
+struct DenseParams {
+  const InstDesc *desc;
+  InstOut *out;
+  int num;
+  const int32_t *order;
+  int32_t *queue;
+  double2 *x, *g, *gn, *d, *xo, *xb, *xs, *hy;
+  uint64_t *skey;
+  int32_t *perm, *batch_of, *rp, *col;
+  uint32_t *ckey;
+  int32_t *corder, *cells;
+  double *H;
+  const int64_t *h_off;
+  double l_cut, rebuild_disp, step_max, e_tol, gsum_tol, c1, curv_eps;
+  int max_iter, max_trials, anm, partition;
+  uint64_t part_seed;
+};
+cudaError_t launch_dense(const DenseParams &p, int grid, cudaStream_t s);
+int64_t dense_h_words(int n, int k);
+
 // SED over a batch (pecc_sed.cu).  Instance q: n[q] circles at off[q] of the operated (x) and best
 // (xb) layouts; candidate slot q*M + j of the descent context (cdesc, cout, c64, c32).
 struct SedParams {

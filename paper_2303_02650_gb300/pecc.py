@@ -37,7 +37,8 @@ class Config(C.Structure):
                 ("block_threads", C.c_int32), ("blocks_per_sm", C.c_int32), ("stall_rel", C.c_double),
                 ("stall_window", C.c_int32), ("polish_k", C.c_int32),
                 ("smem_per_block", C.c_int32), ("polish_stall_rel", C.c_double),
-                ("polish_stall_window", C.c_int32), ("fuse_phases", C.c_int32), ("partition_seed", C.c_uint64)]
+                ("polish_stall_window", C.c_int32), ("fuse_phases", C.c_int32), ("partition_seed", C.c_uint64),
+                ("qn_dense", C.c_int32)]
 
 
 class SedConfig(C.Structure):
