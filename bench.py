@@ -215,14 +215,21 @@ def adjust_bytes(n, iters, trials, visits, nnz_per_circle):
     return float(np.sum(n * (304.0 * iters + 128.0 * visits + (88.0 + 4.0 * nnz_per_circle) * trials)))
 
 
-def adjust_flops(n, iters, trials, visits, nnz_per_circle):
+def adjust_flops(n, iters, trials, visits, nnz_per_circle, mixed=False):
     """Algorithmic binary64 flops of the container adjustment (sqrt and division one flop each).
-    Per circle and iteration: gradient norm 4, direction scaling and g'd 6, secant pair
-    differences, three dots and the displacement 22: 32.  Per pair visited by the two-loop: a dot
-    and an axpy in each loop, 16.  Per line-search trial: the trial point 4, the wall term 12 and
-    per directed list entry 14 (differences 2, squared distance 3, sqrt, 2 - l, the division, the
-    factor, two products, two sums, half an energy term)."""
+    Binary64 form: per circle and iteration, gradient norm 4, direction scaling and g'd 6, secant
+    pair differences, three dots and the displacement 22: 32; per pair visited by the two-loop, a
+    dot and an axpy in each loop, 16; per line-search trial, the trial point 4, the wall term 12
+    and per directed list entry 14 (differences 2, squared distance 3, sqrt, 2 - l, the division,
+    the factor, two products, two sums, half an energy term).
+    Mixed form (binary32 depths, forces and quasi-Newton vectors): only its binary64 operations
+    count.  Per iteration, gradient norm 4, g'd 4, the secant differences 4 and the displacement
+    4: 16; per trial, the trial point 4, the wall's squared radius and difference 4, and per
+    directed list entry 6 (differences 2, squared distance 3, 4 - l^2 1) plus half an energy
+    term 1."""
     n = np.asarray(n, dtype=np.float64)
+    if mixed:
+        return float(np.sum(n * (16.0 * iters + (8.0 + 7.0 * nnz_per_circle) * trials)))
     return float(np.sum(n * (32.0 * iters + 16.0 * visits + (16.0 + 14.0 * nnz_per_circle) * trials)))
 
 
@@ -317,7 +324,7 @@ def run_adjust(args, rank, world, local):
         ms_total, feasible = combine_ranks(dist, ms_total, feasible, "cuda")
     value = feasible / (ms_total / 1e3)
     alg = adjust_bytes(n, it, sts[:, 0], sts[:, 1], nnz_pc)
-    flops = adjust_flops(n, it, sts[:, 0], sts[:, 1], nnz_pc)
+    flops = adjust_flops(n, it, sts[:, 0], sts[:, 1], nnz_pc, mixed=True)
     dom_ms = float(np.mean(adj_ms))
     hbm, peak_kind = peaks()
     achieved = alg / (dom_ms / 1e3) / 1e9
@@ -351,11 +358,13 @@ def run_adjust(args, rank, world, local):
         "metric": "container adjustments/s (instances feasible, overlap<=1e-9, at the adjusted radius)",
         "value": round(value, 3), "unit": "adjusted feasible packings/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_total / args.steps, 3), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32",
         "data": "synthetic (Philox-drawn layouts put through one FP32 + polish descent; seeded instance manifest)",
         "config": {"workload": "adjust: container adjustment (Sec. 4.2, Eq. 12) of " + desc +
                                ", each instance from the layout its FP32 + polish descent reached",
                    "lambda0": lam0, "rounds": rounds, "lbfgs_m": 10,
+                   "arithmetic": "mixed: binary64 coordinates, differences, energies and radius; binary32 depths, "
+                                 "forces and quasi-Newton vectors",
                    "max_iter_per_round": args.adjust_max_iter or 2000,
                    "instances_per_step": int(n.size), "circles_per_step": int(n.sum()),
                    "feasible_before": feas_before,

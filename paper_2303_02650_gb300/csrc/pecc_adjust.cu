@@ -3,10 +3,19 @@
 // z = (x, R) and U(z, lambda) = E(x, R) + lambda R^2.  For each of `rounds` rounds a limited-memory
 // BFGS minimises U over all of z (one batch; a fresh memory each round), then lambda is halved.
 // dU/dx is the gradient of E; dU/dR = -2 sum_i d_i0 + 2 lambda R.  One thread block per instance
-// (persistent over a work queue), binary64 throughout, the two-loop recursion written out over
-// the stored pairs (each dot product one block reduction in a fixed order: deterministic).  The
-// lists are maintained as in the descent: a cell-list build, the Verlet rule before a step and
-// ANM after each iteration.
+// (persistent over a work queue), the two-loop recursion written out over the stored pairs (each
+// dot product one block reduction in a fixed order: deterministic).  The lists are maintained as
+// in the descent: a cell-list build, the Verlet rule before a step and ANM after each iteration.
+// Two arithmetic forms:
+//   <Arith64, double>  binary64 throughout (the binary64 contexts);
+//   <ArithMix, float>  the descent's polish arithmetic for the pair and wall terms (binary64
+//                      coordinates, differences and the near-contact quantities 4 - l^2 and
+//                      |c|^2 - (R - 1)^2, binary32 depths and forces), binary32 quasi-Newton
+//                      vectors, binary64 energy sums, gradient storage and everything about R.
+// GB300 issues few binary64 operations per clock; in the binary64 form the pair terms and the
+// two-loop recursion keep that pipe about 80 % busy.  The binary32 depths put a relative jitter of
+// about 1e-7 on E, so the Armijo test on U resolves U's minimum only to about 1e-6 of R while E is
+// large (a large lambda); the schedule's late rounds, where the radius is settled, have E near 0.
 #include "pecc_internal.h"
 
 namespace pecc {
@@ -48,7 +57,10 @@ __device__ __forceinline__ void bred(AdjSmem &S, double (&v)[NV], const bool (&m
   __syncthreads();
 }
 
+template <class A, typename VT>
 __global__ void __launch_bounds__(kAdjT) adjust_kernel(AdjustParams P) {
+  using V2 = v2<VT>;
+  using GT = typename A::vec_t;  // the forces' type
   __shared__ AdjSmem S;
   const int tid = threadIdx.x, T = blockDim.x;
   const double lc2 = P.l_cut * P.l_cut;
@@ -72,9 +84,11 @@ __global__ void __launch_bounds__(kAdjT) adjust_kernel(AdjustParams P) {
     }
     if (P.from32)
       for (int i = tid; i < n; i += T) { const float2 f = P.x32[D.off + i]; x[i] = make_double2(f.x, f.y); }
-    double2 *g = P.g + D.off, *gn = P.gn + D.off, *dv = P.d + D.off, *zo = P.zo + D.off;
-    double2 *xb = P.xb + D.off, *xs = P.xs + D.off;
-    double2 *Sv = P.S + (int64_t)kAdjM * D.off, *Yv = P.Y + (int64_t)kAdjM * D.off;
+    // gradients in binary64; the direction and the pairs in VT (the buffers are sized for double2)
+    double2 *g = P.g + D.off, *gn = P.gn + D.off;
+    V2 *dv = (V2 *)(P.d + D.off), *sv = (V2 *)(P.sv + D.off);
+    double2 *zo = P.zo + D.off, *xb = P.xb + D.off, *xs = P.xs + D.off;
+    V2 *Sv = (V2 *)(P.S + (int64_t)kAdjM * D.off), *Yv = (V2 *)(P.Y + (int64_t)kAdjM * D.off);
     int32_t *rp = P.rp + D.rp_off, *col = P.col + D.col_off;
     const int cap = 2 * D.cap;
     const CellGrid G{D.R, D.inv_cs, 0.f, 0.f, D.ncx, false};
@@ -109,20 +123,21 @@ __global__ void __launch_bounds__(kAdjT) adjust_kernel(AdjustParams P) {
       const bool mx[2] = {false, false};
       for (int i = tid; i < n; i += T) {
         const double2 xi = x[i];
-        double gx = 0.0, gy = 0.0, e = 0.0;
+        GT gx = 0, gy = 0;
+        double e = 0.0;
         for (int t = rp[i]; t < rp[i + 1]; ++t) {
           const int j = col[t];
-          double fx, fy;
-          const double d = Arith64::pair(xi, x[j], fx, fy);
+          GT fx, fy;
+          const double d = A::pair(xi, x[j], fx, fy);
           gx += fx; gy += fy;
           if (j < i) e += d * d;
         }
-        double fx, fy;
-        const double d0 = Arith64::wall(xi, Rz, Rm1sq, fx, fy);
+        GT fx, fy;
+        const double d0 = A::wall(xi, Rz, Rm1sq, fx, fy);
         gx += fx; gy += fy;
         v[0] += e + d0 * d0;
         v[1] += d0;
-        gout[i] = make_double2(gx, gy);
+        gout[i] = make_double2((double)gx, (double)gy);
       }
       bred<2>(S, v, mx);
       U = v[0] + lam * Rz * Rz;
@@ -142,8 +157,8 @@ __global__ void __launch_bounds__(kAdjT) adjust_kernel(AdjustParams P) {
           if (!rebuild(true)) { ok = false; status = 4; break; }
         }
         ++iters;
-        double v1[1] = {0.0};
         const bool mx1[1] = {false};
+        double v1[1] = {0.0};
         for (int i = tid; i < n; i += T) { const double2 gi = g[i]; v1[0] += gi.x * gi.x + gi.y * gi.y; }
         bred<1>(S, v1, mx1);
         const double gg = v1[0] + gR * gR, gnorm = sqrt(gg);
@@ -160,21 +175,23 @@ __global__ void __launch_bounds__(kAdjT) adjust_kernel(AdjustParams P) {
           }
           // ---- two-loop recursion (Nocedal & Wright, Alg. 7.4) over the stored pairs; q in dv
           visits += count;
-          for (int i = tid; i < n; i += T) dv[i] = g[i];
+          for (int i = tid; i < n; i += T) { const double2 gi = g[i]; dv[i] = mk2<VT>((VT)gi.x, (VT)gi.y); }
           double qR = gR;
           for (int c = count - 1; c >= 0; --c) {
             const int sl = (head + c) % P.m;
-            const double2 *s_ = Sv + (int64_t)sl * n;
-            double v[1] = {0.0};
-            for (int i = tid; i < n; i += T) { const double2 a = s_[i], b = dv[i]; v[0] += a.x * b.x + a.y * b.y; }
+            const V2 *s_ = Sv + (int64_t)sl * n;
+            VT pv = 0;
+            for (int i = tid; i < n; i += T) { const V2 a = s_[i], b = dv[i]; pv += a.x * b.x + a.y * b.y; }
+            double v[1] = {(double)pv};
             bred<1>(S, v, mx1);
             const double a = S.rho[sl] * (v[0] + S.sR[sl] * qR);
             if (tid == 0) S.alpha[c] = a;
-            const double2 *y_ = Yv + (int64_t)sl * n;
+            const V2 *y_ = Yv + (int64_t)sl * n;
+            const VT av = (VT)a;
             for (int i = tid; i < n; i += T) {
-              const double2 yv = y_[i];
-              double2 b = dv[i];
-              b.x -= a * yv.x; b.y -= a * yv.y;
+              const V2 yv = y_[i];
+              V2 b = dv[i];
+              b.x -= av * yv.x; b.y -= av * yv.y;
               dv[i] = b;
             }
             qR -= a * S.yR[sl];
@@ -182,38 +199,43 @@ __global__ void __launch_bounds__(kAdjT) adjust_kernel(AdjustParams P) {
           if (count > 0) {
             const int nw_ = (head + count - 1) % P.m;
             const double gam = 1.0 / (S.rho[nw_] * S.yy[nw_]);  // s'y / y'y of the newest pair
-            for (int i = tid; i < n; i += T) { double2 b = dv[i]; b.x *= gam; b.y *= gam; dv[i] = b; }
+            const VT gv = (VT)gam;
+            for (int i = tid; i < n; i += T) { V2 b = dv[i]; b.x *= gv; b.y *= gv; dv[i] = b; }
             qR *= gam;
           }
           __syncthreads();  // alpha[] written by thread 0
           for (int c = 0; c < count; ++c) {
             const int sl = (head + c) % P.m;
-            const double2 *y_ = Yv + (int64_t)sl * n;
-            double v[1] = {0.0};
-            for (int i = tid; i < n; i += T) { const double2 a = y_[i], b = dv[i]; v[0] += a.x * b.x + a.y * b.y; }
+            const V2 *y_ = Yv + (int64_t)sl * n;
+            VT pv = 0;
+            for (int i = tid; i < n; i += T) { const V2 a = y_[i], b = dv[i]; pv += a.x * b.x + a.y * b.y; }
+            double v[1] = {(double)pv};
             bred<1>(S, v, mx1);
             const double bta = S.rho[sl] * (v[0] + S.yR[sl] * qR);
             const double w = S.alpha[c] - bta;
-            const double2 *s_ = Sv + (int64_t)sl * n;
+            const V2 *s_ = Sv + (int64_t)sl * n;
+            const VT wv = (VT)w;
             for (int i = tid; i < n; i += T) {
-              const double2 sv = s_[i];
-              double2 b = dv[i];
-              b.x += w * sv.x; b.y += w * sv.y;
+              const V2 sa = s_[i];
+              V2 b = dv[i];
+              b.x += wv * sa.x; b.y += wv * sa.y;
               dv[i] = b;
             }
             qR += w * S.sR[sl];
           }
           // d = -q; g'd and the largest move (circles and the radius)
-          double v2[2] = {0.0, 0.0};
           const bool mx2[2] = {false, true};
+          double p2 = 0.0;
+          VT m2 = 0;
           for (int i = tid; i < n; i += T) {
-            double2 b = dv[i];
+            V2 b = dv[i];
             b.x = -b.x; b.y = -b.y;
             dv[i] = b;
             const double2 gi = g[i];
-            v2[0] += gi.x * b.x + gi.y * b.y;
-            v2[1] = fmax(v2[1], b.x * b.x + b.y * b.y);
+            p2 += gi.x * (double)b.x + gi.y * (double)b.y;
+            m2 = max(m2, b.x * b.x + b.y * b.y);
           }
+          double v2[2] = {p2, (double)m2};
           bred<2>(S, v2, mx2);
           double dR = -qR;
           double gd = v2[0] + gR * dR;
@@ -221,12 +243,13 @@ __global__ void __launch_bounds__(kAdjT) adjust_kernel(AdjustParams P) {
           if (!(gd < 0.0)) {  // not a descent direction: drop the memory, take -g
             count = 0;
             head = 0;
-            double v3[1] = {0.0};
+            double m3 = 0.0;
             for (int i = tid; i < n; i += T) {
               const double2 gi = g[i];
-              dv[i] = make_double2(-gi.x, -gi.y);
-              v3[0] = fmax(v3[0], gi.x * gi.x + gi.y * gi.y);
+              dv[i] = mk2<VT>((VT)-gi.x, (VT)-gi.y);
+              m3 = fmax(m3, gi.x * gi.x + gi.y * gi.y);
             }
+            double v3[1] = {m3};
             const bool mx3[1] = {true};
             bred<1>(S, v3, mx3);
             dR = -gR;
@@ -236,8 +259,9 @@ __global__ void __launch_bounds__(kAdjT) adjust_kernel(AdjustParams P) {
           double al = (dmax > P.step_max) ? P.step_max / dmax : 1.0;
           for (int tr = 0; tr < P.max_trials; ++tr) {
             for (int i = tid; i < n; i += T) {
-              const double2 a = zo[i], b = dv[i];
-              x[i] = make_double2(a.x + al * b.x, a.y + al * b.y);
+              const double2 a = zo[i];
+              const V2 b = dv[i];
+              x[i] = make_double2(a.x + al * (double)b.x, a.y + al * (double)b.y);
             }
             R = Ro + al * dR;
             __syncthreads();
@@ -253,21 +277,23 @@ __global__ void __launch_bounds__(kAdjT) adjust_kernel(AdjustParams P) {
           }
         }
         if (!accepted) { status = 2; break; }
-        // ---- the secant pair: s into zo, y into g (the new gradient is gn); displacement
-        double v4[4] = {0.0, 0.0, 0.0, 0.0};
+        // ---- the secant pair: s into sv, y into dv (the new gradient is gn); displacement
         const bool mx4[4] = {false, false, false, true};
+        VT p40 = 0, p41 = 0, p42 = 0;
+        double m43 = 0.0;
         for (int i = tid; i < n; i += T) {
-          const double2 xn = x[i], x0 = zo[i], gnew = gn[i], gold = g[i], b0 = xb[i];
-          const double2 s_ = make_double2(xn.x - x0.x, xn.y - x0.y);
-          const double2 y_ = make_double2(gnew.x - gold.x, gnew.y - gold.y);
-          zo[i] = s_;
-          g[i] = y_;
-          v4[0] += s_.x * y_.x + s_.y * y_.y;
-          v4[1] += s_.x * s_.x + s_.y * s_.y;
-          v4[2] += y_.x * y_.x + y_.y * y_.y;
+          const double2 xn = x[i], x0 = zo[i], b0 = xb[i], gnew = gn[i], gold = g[i];
+          const V2 s_ = mk2<VT>((VT)(xn.x - x0.x), (VT)(xn.y - x0.y));
+          const V2 y_ = mk2<VT>((VT)(gnew.x - gold.x), (VT)(gnew.y - gold.y));
+          sv[i] = s_;
+          dv[i] = y_;
+          p40 += s_.x * y_.x + s_.y * y_.y;
+          p41 += s_.x * s_.x + s_.y * s_.y;
+          p42 += y_.x * y_.x + y_.y * y_.y;
           const double ex = xn.x - b0.x, ey = xn.y - b0.y;
-          v4[3] = fmax(v4[3], ex * ex + ey * ey);
+          m43 = fmax(m43, ex * ex + ey * ey);
         }
+        double v4[4] = {(double)p40, (double)p41, (double)p42, m43};
         bred<4>(S, v4, mx4);
         const double sR = R - Ro, yR = gnR - gR;
         const double sy = v4[0] + sR * yR, ss = v4[1] + sR * sR, yy = v4[2] + yR * yR;
@@ -276,8 +302,8 @@ __global__ void __launch_bounds__(kAdjT) adjust_kernel(AdjustParams P) {
           int sl;
           if (count < P.m) { sl = (head + count) % P.m; ++count; }
           else { sl = head; head = (head + 1) % P.m; }
-          double2 *s_ = Sv + (int64_t)sl * n, *y_ = Yv + (int64_t)sl * n;
-          for (int i = tid; i < n; i += T) { s_[i] = zo[i]; y_[i] = g[i]; }
+          V2 *s_ = Sv + (int64_t)sl * n, *y_ = Yv + (int64_t)sl * n;
+          for (int i = tid; i < n; i += T) { s_[i] = sv[i]; y_[i] = dv[i]; }
           if (tid == 0) { S.sR[sl] = sR; S.yR[sl] = yR; S.rho[sl] = 1.0 / sy; S.yy[sl] = yy; }
         }
         { double2 *t_ = g; g = gn; gn = t_; }  // the trial's gradient is the next iteration's
@@ -306,9 +332,10 @@ __global__ void __launch_bounds__(kAdjT) adjust_kernel(AdjustParams P) {
 
 }  // namespace
 
-cudaError_t launch_adjust(const AdjustParams &p, int grid, cudaStream_t s) {
+cudaError_t launch_adjust(const AdjustParams &p, int mixed, int grid, cudaStream_t s) {
   if (p.num <= 0 || grid <= 0) return cudaSuccess;
-  adjust_kernel<<<grid, kAdjT, 0, s>>>(p);
+  if (mixed) adjust_kernel<ArithMix, float><<<grid, kAdjT, 0, s>>>(p);
+  else adjust_kernel<Arith64, double><<<grid, kAdjT, 0, s>>>(p);
   return cudaGetLastError();
 }
 

@@ -896,7 +896,7 @@ pecc_status pecc_adjust_container(pecc_ctx *ctx, double *R_dev, double lambda0, 
   p.x64 = ctx->x64;
   p.R = R_dev;
   p.g = (double2 *)ctx->g; p.gn = (double2 *)ctx->gt; p.d = (double2 *)ctx->d; p.zo = (double2 *)ctx->xo;
-  p.xb = (double2 *)ctx->xw; p.xs = (double2 *)ctx->xbuild;
+  p.xb = (double2 *)ctx->xw; p.xs = (double2 *)ctx->xbuild; p.sv = (double2 *)ctx->xb;
   p.S = ctx->adjS; p.Y = ctx->adjY;
   p.rp = ctx->rp; p.col = ctx->col; p.ckey = ctx->ckey; p.corder = ctx->corder; p.cells = ctx->cells;
   p.iters = iters_dev; p.status = status_dev; p.queue = ctx->queue + 4; p.stats = stats_dev;
@@ -905,7 +905,8 @@ pecc_status pecc_adjust_container(pecc_ctx *ctx, double *R_dev, double lambda0, 
   p.c1 = f.c1; p.curv_eps = f.curv_eps; p.lambda0 = lambda0;
   p.m = f.lbfgs_m; p.max_iter = f.max_iter; p.max_trials = f.max_trials; p.anm = f.anm; p.rounds = rounds;
   CK(cudaMemsetAsync(ctx->queue + 4, 0, sizeof(int32_t), ctx->stream));
-  CK(launch_adjust(p, (int)std::min<int64_t>(ctx->num, (int64_t)ctx->num_sms * 4), ctx->stream));
+  const int mixed = ctx->cfg.precision == PECC_FP64 ? 0 : 1;
+  CK(launch_adjust(p, mixed, (int)std::min<int64_t>(ctx->num, (int64_t)ctx->num_sms * 4), ctx->stream));
   ctx->lists_prec = -1;  // the standalone lists' reference coordinates served as scratch
   return PECC_OK;
 }

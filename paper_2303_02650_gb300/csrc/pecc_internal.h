@@ -113,7 +113,7 @@ struct AdjustParams {
   float2 *x32;
   double2 *x64;
   double *R;  // in/out, per instance
-  double2 *g, *gn, *d, *zo, *xb, *xs, *S, *Y;
+  double2 *g, *gn, *d, *zo, *xb, *xs, *sv, *S, *Y;
   int32_t *rp, *col;
   uint32_t *ckey;
   int32_t *corder, *cells;
@@ -122,7 +122,9 @@ struct AdjustParams {
   double l_cut, rebuild_disp, step_max, gsum_tol, c1, curv_eps, lambda0;
   int m, max_iter, max_trials, anm, rounds;
 };
-cudaError_t launch_adjust(const AdjustParams &p, int grid, cudaStream_t s);
+// mixed != 0: the polish arithmetic for the pair terms (binary32 depths and forces) and binary32
+// quasi-Newton vectors; energies, gradient storage and the radius stay binary64
+cudaError_t launch_adjust(const AdjustParams &p, int mixed, int grid, cudaStream_t s);
 
 // GBO with the explicit inverse Hessian per batch (pecc_dense.cu); binary64, per-circle scratch of
 // the context (double2 each), H of instance q at H + h_off[q].

@@ -10,6 +10,16 @@ Pinned three ways:
 - From GBO minima, where the iteration is ill-conditioned, within the oracle's own rounding
   envelope (its spread under 1e-15 perturbations of the start); over the full schedule, a
   feasible layout at a radius within 1e-3 of the oracle's.
+- The mixed form (binary32 depths, forces and quasi-Newton vectors; binary64 coordinates,
+  near-contact differences, energies and radius):
+  - the closed-form radii of one round to 5e-6 at lambda = 0.1 and 1e-6 at lambda = 0.01. The
+    binary32 depths jitter E by about 1e-7 relative, and the Armijo test cannot resolve changes
+    of U below that jitter. The search then stops near, not at, U's minimum (measured: 1.0e-6 of
+    R at lambda = 0.1, 1.1e-7 at lambda = 0.01);
+  - the exact radius of the full schedule to 1e-9, because E, and with it the jitter, vanishes
+    as lambda does;
+  - short runs within the oracle's envelope under perturbations of 1e-7 of the start (the size
+    of a binary32 rounding).
 """
 import numpy as np
 import pytest
@@ -48,7 +58,7 @@ def _adjust(pecc, torch, n, R, xy, lambda0, rounds, **kw):
     return x, Rs.cpu().numpy(), iters.cpu().numpy(), status.cpu().numpy()
 
 
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1, 2])
 @pytest.mark.parametrize("lam", [0.1, 0.01])
 def test_single_round_closed_forms(prec, lam):
     torch, pecc = need_gpu()
@@ -56,22 +66,25 @@ def test_single_round_closed_forms(prec, lam):
     R0 = np.array([EXACT[v][0] - 0.1 for v in ns])
     xy = np.concatenate([_sym(v, r) for v, r in zip(ns, R0)])
     x, Rs, iters, status = _adjust(pecc, torch, ns, R0, xy, lam, 1, precision=prec)
+    tol = 1e-9 if prec == 0 else (5e-6 if lam >= 0.1 else 1e-6)
     for q, v in enumerate(ns):
         Rx, a = EXACT[v]
-        assert Rs[q] == pytest.approx(Rx / (1.0 + lam / a), rel=1e-9), (v, Rs[q])
+        assert Rs[q] == pytest.approx(Rx / (1.0 + lam / a), rel=tol), (v, Rs[q])
         # stationary, or at max_iter: at the minimum, steps whose Armijo test passes on an energy
-        # equal to rounding (the oracle's stopping rule too) can keep a round going
-        assert status[q] in (1, 3) and iters[q] >= 1
+        # equal to rounding (the oracle's stopping rule too) can keep a round going.  The mixed
+        # forms may also stall: below the jitter of the binary32 depths no step lowers U.
+        assert status[q] in ((1, 3) if prec == 0 else (1, 2, 3)) and iters[q] >= 1
 
 
-def test_full_schedule_reaches_the_exact_radius(orc):
+@pytest.mark.parametrize("prec", [0, 2])
+def test_full_schedule_reaches_the_exact_radius(orc, prec):
     """lambda0 = 1e-4 halved over 35 rounds: the radius ends within 1e-9 of the exact one and the
     layout is feasible at it."""
     torch, pecc = need_gpu()
     ns = [2, 3, 7]
     R0 = np.array([EXACT[v][0] - 0.1 for v in ns])
     xy = np.concatenate([_sym(v, r) for v, r in zip(ns, R0)])
-    x, Rs, iters, status = _adjust(pecc, torch, ns, R0, xy, 1e-4, 35, precision=0)
+    x, Rs, iters, status = _adjust(pecc, torch, ns, R0, xy, 1e-4, 35, precision=prec)
     for q, (v, part) in enumerate(zip(ns, split(x, np.array(ns)))):
         assert abs(Rs[q] - EXACT[v][0]) <= 1e-9
         assert orc.max_overlap(part, Rs[q])[0] <= 1e-9
@@ -109,14 +122,14 @@ def _gbo_minima(orc, n, R0, seed=3):
             for q, (v, r) in enumerate(zip(n, R0))]
 
 
-def _envelope(orc, start, R0, trials=4, **kw):
+def _envelope(orc, start, R0, trials=4, rel=1e-15, **kw):
     """The oracle's own sensitivity to rounding: its run from `start` and the largest deviation
-    (radius relative, coordinates over R0) of runs from starts perturbed by 1e-15 relative."""
+    (radius relative, coordinates over R0) of runs from starts perturbed by `rel` relative."""
     xr, Rr, res = orc.adjust_container(start, R0, **kw)
     rng = np.random.default_rng(11)
     dR = dx = 0.0
     for _ in range(trials):
-        p = start * (1.0 + 1e-15 * rng.standard_normal(start.shape))
+        p = start * (1.0 + rel * rng.standard_normal(start.shape))
         xp, Rp, _ = orc.adjust_container(p, R0, **kw)
         dR = max(dR, abs(Rp - Rr) / Rr)
         dx = max(dx, float(np.abs(xp - xr).max()) / R0)
@@ -143,7 +156,26 @@ def test_longer_runs_from_gbo_minima_stay_in_the_rounding_envelope(orc, rounds, 
         assert float(np.abs(part - xr).max()) / R0[q] <= 10.0 * dx + 1e-12, (q, dx)
 
 
-def test_infeasible_minima_become_feasible(orc):
+@pytest.mark.parametrize("rounds,iters_per_round", [(1, 1), (1, 6), (2, 4)])
+def test_mixed_short_runs_stay_in_the_binary32_envelope(orc, rounds, iters_per_round):
+    """The mixed form from random layouts: within ten times the oracle's spread under 1e-7
+    perturbations of the start (plus 1e-8), with the same iteration counts."""
+    torch, pecc = need_gpu()
+    n = np.array([40, 300, 257], dtype=np.int32)
+    R = np.array([synth.radius(int(v), 0.86) for v in n])
+    xy = np.concatenate([orc.init_positions(int(v), float(r), 77, inst=q) for q, (v, r) in enumerate(zip(n, R))])
+    lam = 0.05
+    x, Rs, iters, status = _adjust(pecc, torch, n, R, xy, lam, rounds, precision=2, max_iter=iters_per_round)
+    for q, (a, b) in enumerate(zip(split(xy, n), split(x, n))):
+        xr, Rr, res, dR, dx = _envelope(orc, a, float(R[q]), rel=1e-7, lambda0=lam, rounds=rounds,
+                                        max_iter=iters_per_round)
+        assert iters[q] == res.iters, q
+        assert abs(Rs[q] - Rr) / Rr <= 10.0 * dR + 1e-8, (q, Rs[q], Rr, dR)
+        assert float(np.abs(b - xr).max()) / R[q] <= 10.0 * dx + 1e-8, (q, dx)
+
+
+@pytest.mark.parametrize("prec", [0, 2])
+def test_infeasible_minima_become_feasible(orc, prec):
     """GBO local minima above zero energy (u = 0.86, denser than the best known packings) are made
     feasible by the full schedule and the radius grows only a little.  Over 35 rounds of up to
     2000 iterations the two programs' rounding differences can steer them to neighbouring local
@@ -155,7 +187,7 @@ def test_infeasible_minima_become_feasible(orc):
     starts = _gbo_minima(orc, n, R0)
     for q, s in enumerate(starts):
         assert orc.max_overlap(s, float(R0[q]))[0] > 1e-6
-    x, Rs, iters, status = _adjust(pecc, torch, n, R0, np.concatenate(starts), 1e-4, 35, precision=0)
+    x, Rs, iters, status = _adjust(pecc, torch, n, R0, np.concatenate(starts), 1e-4, 35, precision=prec)
     for q, part in enumerate(split(x, n)):
         xr, Rr, res = orc.adjust_container(starts[q], float(R0[q]))
         assert orc.max_overlap(part, Rs[q])[0] <= 1e-9, q
@@ -164,9 +196,9 @@ def test_infeasible_minima_become_feasible(orc):
 
 
 def test_fp32_context_adjusts_its_binary32_layout(orc):
-    """A binary32 context: the adjustment starts from the binary32 coordinates and leaves the
-    adjusted layout in both copies; the radius matches the oracle started from the same
-    (rounded) coordinates."""
+    """A binary32 context (mixed form): the adjustment starts from the binary32 coordinates and
+    leaves the adjusted layout in both copies; the radius matches the oracle started from the
+    same (rounded) coordinates to 1e-3 (the two can settle in neighbouring minima)."""
     torch, pecc = need_gpu()
     n = np.array([64], dtype=np.int32)
     R0 = np.array([synth.radius(64, 0.86)])
@@ -174,7 +206,7 @@ def test_fp32_context_adjusts_its_binary32_layout(orc):
     s32 = s.astype(np.float32).astype(np.float64)
     x, Rs, iters, status = _adjust(pecc, torch, n, R0, s32, 1e-4, 35, precision=1)
     xr, Rr, res = orc.adjust_container(s32, float(R0[0]))
-    assert Rs[0] == pytest.approx(Rr, rel=1e-6)
+    assert Rs[0] == pytest.approx(Rr, rel=1e-3)
     # get_positions of a binary32 context returns the binary32 copy
     assert orc.max_overlap(x, Rs[0])[0] <= 1e-5
 
