@@ -50,6 +50,11 @@ UNIT = "feasible packings/s"
 # batch-number study (k = 1 is faster still, but is one batch, plain L-BFGS); the paper's 3 / 5 for
 # n in [300, 1000) tuned its CPU dense BFGS.
 K_DEFAULT = {"c3": 2, "c3-fp64": 2}
+# The build's own readings that the paper does not fix, tuned for the batch workloads on GB300
+# (a sweep of the step cap, the FP32 stagnation rule, the polish gate and the Verlet skin): a step
+# cap of 0.3 (within the skin rule 0.3 < 2 x 0.25) and polishing only FP32 results with E <= 1e-5.
+# 9161 against 8574 feasible packings/s at the library defaults (0.1, 1e-4), the same success.
+CFG_DEFAULT = {"c3": ["step_max=0.3", "polish_gate=0.00001"], "c3-fp64": ["step_max=0.3"]}
 
 
 def workload(name: str):
@@ -170,7 +175,8 @@ class Clocks:
 # traffic is that ratio times its algorithmic bytes.  The figure holds for the kernel sources it
 # was measured on: once their hash changes the bench reports traffic as null.
 FUSED_TRAFFIC = {"sources": ["pecc_descend_kernel.cuh", "pecc_dev.cuh", "pecc_descend_fused.cu"], "k": 2,
-                 "sha256_16": "0499380df5b27243", "dram_per_algorithmic_byte": 5.338089e9 / 224.914342e9}
+                 "cfg": ["step_max=0.3", "polish_gate=0.00001"],
+                 "sha256_16": "0499380df5b27243", "dram_per_algorithmic_byte": 4.679270e9 / 208.822060e9}
 
 
 def fused_traffic(alg_bytes):
@@ -797,6 +803,9 @@ def run_ours(args, rank, world, local):
         shape["fuse_phases"] = args.fuse
     if args.k:
         shape["k_batches"] = args.k
+    for kv in args.cfg:  # further pecc_config fields, e.g. step_max=0.2
+        key, val = kv.split("=", 1)
+        shape[key] = float(val) if any(c in val for c in ".e") else int(val)
     ctx = pecc.Context(n, precision=prec, **shape)
     ctx.set_radius(R)
     tuned = None
@@ -927,6 +936,7 @@ def run_ours(args, rank, world, local):
                    "instances_per_step": int(n.size), "circles_per_step": int(n.sum()),
                    "l_cut": 2.5, "rebuild_disp": 0.25, "lbfgs_m": 10, "max_iter": 2000,
                    "k_batches": (args.k if args.k else "1 (n<300), 3 (n<500), 5"), "partition": "sector",
+                   "settings": args.cfg,
                    "l2": "working set per step > 129 MB L2 (histories and lists of all instances); no flush",
                    "launch": dict(zip(["block_threads", "blocks_per_sm", "grid"], ctx.launch_shape()),
                                   autotuned=tuned is not None),
@@ -944,7 +954,8 @@ def run_ours(args, rank, world, local):
                      "frac": round(achieved / hbm, 4),
                      # the capture's ratio holds for the workload it was taken on (the batch)
                      "traffic": (round(fused_traffic(dom_bytes)) if fused and args.workload == "c3" and
-                                 args.k == FUSED_TRAFFIC["k"] and fused_traffic(dom_bytes) else None),
+                                 args.k == FUSED_TRAFFIC["k"] and sorted(args.cfg) == sorted(FUSED_TRAFFIC["cfg"]) and
+                                 fused_traffic(dom_bytes) else None),
                      "kernel": ("descend_fused_kernel (FP32 descent + FP64 polish per instance)" if fused else
                                 ("descend_grid_kernel" if big else "descend_kernel") +
                                 ("<Arith64>" if prec == 0 else "<Arith32> (FP32 bulk phase)")),
@@ -1197,6 +1208,8 @@ def main():
                     help="adjust workload: iterations per round at most (profiling case; default 2000)")
     ap.add_argument("--adjust-rounds", type=int, default=0, help="adjust workload: rounds (profiling case; default 35)")
     ap.add_argument("--sed-iters", type=int, default=0, help="sed workload: SED iterations per step (default 10)")
+    ap.add_argument("--cfg", action="append", default=[], metavar="FIELD=VALUE",
+                    help="set a pecc_config field of the descent context (repeatable), e.g. step_max=0.2")
     ap.add_argument("--k", type=int, default=-1,
                     help="batches per instance for every instance; 0: the paper's 1, 3, 5 by n; default: "
                          "2 for the batch workloads (c3, c3-fp64), the paper's otherwise")
@@ -1205,6 +1218,8 @@ def main():
     args = ap.parse_args()
     if args.k < 0:
         args.k = K_DEFAULT.get(args.workload, 0)
+    given = {kv.split("=", 1)[0] for kv in args.cfg}
+    args.cfg = [kv for kv in CFG_DEFAULT.get(args.workload, []) if kv.split("=", 1)[0] not in given] + args.cfg
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
     rank = int(os.environ.get("RANK", "0"))
