@@ -590,12 +590,14 @@ def run_sed(args, rank, world, local):
 
         dist.init_process_group("nccl")
     M = 25
-    sed = pecc.Sed(n, precision=pecc.FP32_POLISH64, max_candidates=M, s_iter=iters)
+    # the candidates descend with the batch workload's GB300 settings (k = 2, step cap 0.3, gate 1e-5)
+    dcfg = {"k_batches": 2, "step_max": 0.3, "polish_gate": 1e-5}
+    sed = pecc.Sed(n, precision=pecc.FP32_POLISH64, max_candidates=M, s_iter=iters, **dcfg)
     sed.set_radius(R)
     chk = pecc.Context(n, precision=pecc.FP64)  # the feasibility check of x* (S10)
     chk.set_radius(R)
     seed0 = args.seed + 1_000_003 * rank
-    kvec = np.array([1 if v < 300 else (3 if v < 500 else 5) for v in n], dtype=np.float64)
+    kvec = np.full(n.size, 2.0)
     slot_n = np.repeat(n, M)
     slot_k = np.repeat(kvec, M)
     xb = torch.empty((int(n.sum()), 2), dtype=torch.float64, device="cuda")
@@ -699,6 +701,7 @@ def run_sed(args, rank, world, local):
         "data": "synthetic (Philox-drawn layouts and perturbations; seeded instance manifest)",
         "config": {"workload": f"sed: SED (Sec. 5.2) on the first {n.size} instances of the " + desc,
                    "sed_iterations": iters, "max_candidates": M, "e_feas": 1e-25, "amp": 0.8,
+                   "descent_settings": dcfg,
                    "precision": "FP32 bulk + FP64 polish (each candidate)", "instances_per_step": int(n.size),
                    "circles_per_step": int(n.sum()),
                    "l2": "working set per step > 129 MB L2 (candidate slots of all instances); no flush",
