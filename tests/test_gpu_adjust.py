@@ -211,6 +211,22 @@ def test_fp32_context_adjusts_its_binary32_layout(orc):
     assert orc.max_overlap(x, Rs[0])[0] <= 1e-5
 
 
+@pytest.mark.parametrize("prec", [0, 2])
+def test_one_circle_closed_form(prec):
+    """One circle: R* = 1 / (1 + lambda) after one round (to 1e-7: the wall term is a cone at the
+    centre, where the search stalls, as in the oracle), and 1 after the full schedule."""
+    torch, pecc = need_gpu()
+    n = [1, 1]
+    R0 = np.array([0.9, 1.4])
+    xy = np.array([[0.3, -0.2], [-0.1, 0.05]])
+    lam = 0.3
+    x, Rs, iters, status = _adjust(pecc, torch, n, R0, xy, lam, 1, precision=prec)
+    tol = 1e-7 if prec == 0 else 5e-6
+    np.testing.assert_allclose(Rs, 1.0 / (1.0 + lam), rtol=tol)
+    x, Rs, iters, status = _adjust(pecc, torch, n, R0, xy, 1e-4, 35, precision=prec)
+    np.testing.assert_allclose(Rs, 1.0, rtol=0, atol=1e-9)
+
+
 def test_empty_and_whole_gpu_instances_are_left_alone():
     torch, pecc = need_gpu()
     n = np.array([0, 16384, 7], dtype=np.int32)

@@ -160,7 +160,7 @@ def test_start_and_one_iteration_follow_the_oracle_fp64(orc):
         assert E1[q] == pytest.approx(Ec[ref], rel=1e-9)
 
 
-@pytest.mark.parametrize("prec", [0, 2])
+@pytest.mark.parametrize("prec", [0, 1, 2])
 def test_reaches_zero_energy_at_the_exact_radius_of_seven(orc, prec):
     """R = 3 packs 7 circles exactly; every instance of the batch ends with E(x*) <= 1e-25 and a
     feasible layout, as the oracle's searches do."""
@@ -168,7 +168,9 @@ def test_reaches_zero_energy_at_the_exact_radius_of_seven(orc, prec):
     num = 16
     n = np.full(num, 7, dtype=np.int32)
     R = np.full(num, 3.0)
-    with pecc.Sed(n, precision=prec, s_iter=30) as s:
+    # a binary32 context cannot resolve 1e-25: its search stops at its own energy floor
+    e_feas = 1e-25 if prec != 1 else 1e-12
+    with pecc.Sed(n, precision=prec, s_iter=30, e_feas=e_feas) as s:
         s.set_radius(R)
         s.start(5)
         ran, left = s.iterate(30)
@@ -177,9 +179,9 @@ def test_reaches_zero_energy_at_the_exact_radius_of_seven(orc, prec):
         status = st["status"].cpu().numpy()
         xb = st["xbest"].cpu().numpy()
     assert left == 0
-    assert np.all(status == 0) and np.all(Eb <= 1e-25)
+    assert np.all(status == 0) and np.all(Eb <= e_feas)
     for q, part in enumerate(split(xb, n)):
-        assert orc.max_overlap(part, 3.0)[0] <= 1e-9
+        assert orc.max_overlap(part, 3.0)[0] <= (1e-9 if prec != 1 else 1e-5)
     r = orc.sed(7, 3.0, 5, inst=0, s_iter=30)
     assert r.status == "converged"
 

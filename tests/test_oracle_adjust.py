@@ -87,3 +87,18 @@ def test_adjust_random_infeasible_layout_becomes_feasible(orc):
     xs, Rs, res = orc.adjust_container(r.x, R0)
     assert orc.max_overlap(xs, Rs)[0] <= 1e-9
     assert R0 < Rs < 1.1 * R0
+
+
+@pytest.mark.parametrize("lam", [0.3, 0.05])
+def test_one_circle_closed_form(orc, lam):
+    """One circle: U = (|c| + 1 - R)^2 + lambda R^2 is least at c = 0 with R = 1 / (1 + lambda)
+    (dU/dR = -2 (1 - R) + 2 lambda R = 0); the full schedule ends at R = 1 (the circle itself).
+    |c| is a cone at the centre, so the wall's force keeps its size 2 (1 - R) as c -> 0 and the
+    search stalls once c oscillates about 0: one round settles R to about 1e-8 (measured
+    1.2e-8), the schedule (1 - R -> 0) to 1e-9."""
+    x0 = np.array([[0.3, -0.2]])
+    xs, Rs, res = orc.adjust_container(x0, 0.9, lambda0=lam, rounds=1)
+    assert Rs == pytest.approx(1.0 / (1.0 + lam), rel=1e-7)
+    assert np.abs(xs).max() <= 1e-6
+    xs, Rs, res = orc.adjust_container(x0, 0.9)
+    assert abs(Rs - 1.0) <= 1e-9
