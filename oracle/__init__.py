@@ -103,6 +103,8 @@ def lib():
             "orc_sed_select": (C.c_int, [C.c_int, d, C.c_double, C.c_uint64, C.c_int, C.c_int]),
             "orc_sed": (C.c_int, [C.c_int, C.c_double, C.c_uint64, C.c_int, C.c_int, _P(Opts), C.c_int, C.c_int,
                                   C.c_double, C.c_int, C.c_double, d, _P(SedResult), i32, i32, d, d]),
+            "orc_frame": (C.c_int, [C.c_int, C.c_double, C.c_uint64, C.c_int, C.c_int, _P(Opts), C.c_int, C.c_int,
+                                    C.c_int, C.c_double, C.c_double, C.c_double, C.c_int, d, d, d]),
             "orc_solve_batch": (C.c_double, [C.c_int, i32, d, C.c_uint64, C.c_int, C.c_int, _P(Opts),
                                              C.c_double, C.c_int, d, i32, i32, d, d, _P(C.c_uint8)]),
         }
@@ -390,6 +392,20 @@ def sed(n, R, seed, inst=0, s_iter=500, max_cand=25, e_feas=1e-25, shared=0, amp
                   _ptr(st, C.c_int32), _ptr(ex, C.c_double), _ptr(eb, C.c_double))
     k = r.iters
     return SedOut(x, r.E, r.E0, k, STATUS[r.status], r.descents, mt[:k], st[:k], ex[:k], eb[:k])
+
+
+def frame(n, Rb, seed, inst=0, outer=2, s_iter=10, max_cand=25, e_feas=1e-25, amp=0.8, lambda0=1e-4, rounds=35,
+          init_mode=0, **kw):
+    """The framework of Sec. 5.1 with `outer` iterations in place of the cut-off time:
+    (x*, R*, R_trace)."""
+    o = default_opts(**kw)
+    x = np.zeros((int(n), 2))
+    Rb_out = np.zeros(1)
+    tr = np.zeros(outer + 1)
+    lib().orc_frame(int(n), float(Rb), int(seed), int(inst), int(init_mode), C.byref(o), int(outer), int(s_iter),
+                    int(max_cand), float(e_feas), float(amp), float(lambda0), int(rounds), _ptr(x, C.c_double),
+                    _ptr(Rb_out, C.c_double), _ptr(tr, C.c_double))
+    return x, float(Rb_out[0]), tr
 
 
 def max_overlap(xy, R):

@@ -38,6 +38,8 @@
  *   feasibility     Eq. 1 / Eq. 2: maximum pair and boundary overlap depth.
  *   adjustment      Sec. 4.2, Eq. 12 (container adjustment by L-BFGS over (x, R)).
  *   SED             Sec. 5.2, Algorithm SED and the select operator of Eq. 18.
+ *   framework       Sec. 5.1, the framework algorithm (GBO, adjustment, then SED and
+ *                   adjustment repeated at min(R_b, R*), keeping the smallest feasible radius).
  */
 #include <math.h>
 #include <pthread.h>
@@ -1431,5 +1433,47 @@ int orc_sed(int n, double R, uint64_t seed, int inst, int init_mode, const orc_o
     free(x);
     free(cand);
     free(Ec);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* The framework of Sec. 5.1 (Algorithm 5) with an iteration count in place  */
+/* of the cut-off time: x* = GBO(random_solution(n, R_b)), (x*, R*) =        */
+/* adjust(x*, R_b); then `outer` times: R = min(R_b, R*), x = SED(n, R),     */
+/* (x, R) = adjust(x, R), and x*, R* = x, R when R < R*.  Random keys: the   */
+/* first layout draws under `seed`, SED call t under seed + 1 + t.  The GBO  */
+/* and SED stop at e_feas.  R_trace (outer + 1, may be NULL): R* after      */
+/* the first adjustment and after every iteration.                           */
+/* ------------------------------------------------------------------------ */
+int orc_frame(int n, double Rb, uint64_t seed, int inst, int init_mode, const orc_opts *o, int outer, int s_iter,
+              int max_cand, double e_feas, double amp, double lambda0, int rounds, double *xy_best, double *R_best,
+              double *R_trace)
+{
+    size_t vb = sizeof(double) * 2 * (size_t)(n > 0 ? n : 1);
+    double *x = (double *)malloc(vb);
+    orc_result r;
+    orc_opts os = *o;
+    os.e_tol = e_feas;
+    orc_init_positions(n, Rb, seed, inst, init_mode, x);
+    orc_gbo(n, x, Rb, &os, &r, NULL);
+    double Rs = Rb;
+    orc_adjust_container(n, x, &Rs, o, lambda0, rounds, &r);
+    memcpy(xy_best, x, sizeof(double) * 2 * (size_t)n);
+    if (R_trace) R_trace[0] = Rs;
+    for (int t = 0; t < outer; t++) {
+        const double R = Rb < Rs ? Rb : Rs;
+        orc_sed_result sr;
+        orc_sed(n, R, seed + 1 + (uint64_t)t, inst, init_mode, &os, s_iter, max_cand, e_feas, 0, amp, x, &sr, NULL,
+                NULL, NULL, NULL);
+        double Rn = R;
+        orc_adjust_container(n, x, &Rn, o, lambda0, rounds, &r);
+        if (Rn < Rs) {
+            Rs = Rn;
+            memcpy(xy_best, x, sizeof(double) * 2 * (size_t)n);
+        }
+        if (R_trace) R_trace[t + 1] = Rs;
+    }
+    *R_best = Rs;
+    free(x);
     return 0;
 }

@@ -10,6 +10,8 @@
   m = max(1, J(E(x))), and the descent count is 1 + the sum of m.
 - Its purpose is checked too: it reaches zero energy at the exact radius of 7 circles, and it
   lowers the energy of dense jammed layouts.
+- The framework of Sec. 5.1 keeps the exact radii of 2, 3 and 7 circles, its record never
+  grows, and on a dense instance it ends below R_b with a feasible layout.
 """
 from fractions import Fraction
 
@@ -133,3 +135,28 @@ def test_lowers_the_energy_of_jammed_layouts(orc):
 def test_easy_instance_needs_no_exploring(orc):
     r = orc.sed(19, np.sqrt(19 / 0.80), 3, s_iter=10)
     assert r.iters == 0 and r.status == "converged" and r.descents == 1
+
+
+# ---------------------------------------------------------------- the framework (Sec. 5.1)
+R3 = 1.0 + 2.0 / np.sqrt(3.0)
+
+
+@pytest.mark.parametrize("n,Rb", [(2, 2.0), (3, R3), (7, 3.0)])
+def test_framework_keeps_the_exact_radius(orc, n, Rb):
+    """At the exact radius of 2, 3 and 7 circles the framework's record is that radius (to
+    rounding) with a feasible layout, and the record never grows."""
+    x, R, tr = orc.frame(n, Rb, 5, outer=2, s_iter=5)
+    assert abs(R - Rb) <= 1e-9
+    assert orc.max_overlap(x, R)[0] <= 1e-9
+    assert np.all(np.diff(tr) <= 0.0)
+
+
+def test_framework_improves_a_dense_instance(orc):
+    """n = 40 at R_b = sqrt(40 / 0.78): the first adjustment enlarges the container; searching at
+    min(R_b, R*) then finds a feasible layout below R_b.  The record only shrinks."""
+    n, Rb = 40, np.sqrt(40 / 0.78)
+    x, R, tr = orc.frame(n, Rb, 2, outer=3, s_iter=3, max_iter=300)
+    assert np.all(np.diff(tr) <= 0.0)
+    assert tr[0] > Rb and R < Rb
+    assert R == tr[-1]
+    assert orc.max_overlap(x, R)[0] <= 1e-9
