@@ -19,6 +19,9 @@ the FP64 feasibility check.  Workloads:
   ksweep  the batch-number study of Sec. 6.5: for n = 300, 500, 1000 and k = 1, 2, 3, 5, 7, 10, 15
           (sector; at n = 1000 also annulus, fence and random), 608 instances per setting at
           u = 0.83 descend from random layouts; mean device time per instance against k
+  frame   the framework of Sec. 5.1 on the first 304 instances of the c3 batch, R_b = their radii:
+          GBO and adjustment, then one iteration of SED (5 iterations) and adjustment at
+          min(R_b, R*); the smallest feasible radius found
   adjust  container adjustment (Sec. 4.2, Eq. 12) of the first 304 instances of the c3 batch (one
           resident wave: two instance blocks per SM), each from the layout its FP32 + polish
           descent reached; lambda0 = 1e-4, 35 rounds of up to 2000 iterations
@@ -738,6 +741,142 @@ def run_sed(args, rank, world, local):
         dist.destroy_process_group()
 
 
+FRAME_INSTANCES, FRAME_OUTER, FRAME_SED_ITERS = 304, 1, 5
+
+
+def run_frame(args, rank, world, local):
+    """The framework of Sec. 5.1 through pecc_frame_run."""
+    import torch
+
+    from paper_2303_02650_gb300 import pecc
+
+    torch.cuda.set_device(local)
+    n, R, _, desc = workload("c3")
+    count = args.instances or FRAME_INSTANCES
+    n, R = n[:count], R[:count]
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    dcfg = {"k_batches": 2, "step_max": 0.3, "polish_gate": 1e-5}
+    sed = pecc.Sed(n, precision=pecc.FP32_POLISH64, max_candidates=25, s_iter=FRAME_SED_ITERS, **dcfg)
+    adj = pecc.Context(n, precision=pecc.FP32_POLISH64)
+    chk = pecc.Context(n, precision=pecc.FP64)
+    Rb = torch.as_tensor(R, dtype=torch.float64, device="cuda")
+    stats = torch.zeros(3 * n.size, dtype=torch.int32, device="cuda")
+    seed0 = args.seed + 1_000_003 * rank
+    res = []
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        for w in range(args.warmup):
+            pecc.frame_run(sed, adj, Rb, seed0 + 90_000 + w, outer=FRAME_OUTER, sed_iters=FRAME_SED_ITERS)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        clk.mark_start()
+        e0.record()
+        for s_ in range(args.steps):
+            out = pecc.frame_run(sed, adj, Rb, seed0 + s_, outer=FRAME_OUTER, sed_iters=FRAME_SED_ITERS, stats=stats)
+            res.append((out[0].clone(), out[1].clone(), out[2].clone(), stats.clone()))
+        e1.record()
+        torch.cuda.synchronize()
+        clk.mark_end()
+    ms_total = e0.elapsed_time(e1)
+    feasible, growth, improved = 0, [], 0
+    flops = 0.0
+    chk.set_radius(res[0][0].cpu().numpy())
+    chk.set_positions(res[0][1])
+    chk.rebuild_neighbors(force=True, eval=0)
+    nnz_pc = chk.neighbor_count() / max(1, int(n.sum()))  # list entries per circle at the final layouts
+    for Rbest, xbest, trace, st in res:
+        Rs = Rbest.cpu().numpy()
+        chk.set_radius(Rs)
+        chk.set_positions(xbest)
+        feas, _ = chk.check_feasible(1e-9)
+        feasible += int(feas.sum().item())
+        growth.append(Rs / R - 1.0)
+        tr = trace.cpu().numpy()
+        improved += int(np.sum(tr[-1] < tr[0]))
+        stn = st.cpu().numpy().astype(np.float64)
+        flops += adjust_flops(n, stn[:n.size], stn[n.size::2], stn[n.size + 1::2], nnz_pc, mixed=True)
+    if dist:
+        ms_total, feasible = combine_ranks(dist, ms_total, feasible, "cuda")
+    value = feasible / (ms_total / 1e3)
+    growth = np.concatenate(growth)
+    gflops = flops / (ms_total / 1e3) / 1e9
+    line = {
+        "metric": "framework runs/s (Sec. 5.1; layout feasible, overlap<=1e-9, at the final radius)",
+        "value": round(value, 3), "unit": "feasible framework results/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_total / args.steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+        "data": "synthetic (Philox-drawn layouts and perturbations; seeded instance manifest)",
+        "config": {"workload": f"frame: the framework of Sec. 5.1 on the first {n.size} instances of the " + desc +
+                               ", R_b = their radii",
+                   "outer_iterations": FRAME_OUTER, "sed_iterations": FRAME_SED_ITERS, "max_candidates": 25,
+                   "lambda0": 1e-4, "rounds": 35, "descent_settings": dcfg,
+                   "adjustment": "mixed form (binary32 depths, forces and quasi-Newton vectors)",
+                   "l2": "working set per step > 129 MB L2 (candidate slots); no flush",
+                   "parallelism": f"instances sharded over {world} GPU(s), no collective on the data path"},
+        "success_rate": round(feasible / (args.steps * n.size * world), 4),
+        "radius_vs_Rb": {"mean": float(np.mean(growth)), "min": float(np.min(growth)), "max": float(np.max(growth)),
+                         "below_Rb": round(float(np.mean(growth < 0)), 4)},
+        "improved_by_search": round(improved / (args.steps * n.size), 4),
+        "roofline": {"bound": "alu", "achieved": round(gflops, 1), "peak": round(FP64_PEAK_GFLOPS, 1),
+                     "unit": "GFLOP/s (binary64)", "frac": round(gflops / FP64_PEAK_GFLOPS, 4), "traffic": None,
+                     "kernel": "adjust_kernel (mixed form), its binary64 flops over the whole step",
+                     "peak_kind": "derived: 152 SMs x 2 FP64 FMA/clk x 2.07 GHz"},
+        "e2e": None,
+        "e2e_note": "pecc_frame_run takes device buffers; the host path of the descent is the batch workload's",
+        # per call: the first search start (init, prepare, list, stamp, descent, select) and adjustment
+        # (set_pos, adjust, get_pos, two statistics sums); per outer iteration the radius kernel, a
+        # search start, the iterate's first prepare and list, 5 kernels per SED iteration, an
+        # adjustment and the record
+        "gpu_launches": args.steps * (11 + FRAME_OUTER * (15 + 5 * FRAME_SED_ITERS)),
+        "clocks": clk.summary(),
+    }
+    sed.close()
+    adj.close()
+    chk.close()
+    if rank == 0:
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline_frame(args, n, R)
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def oracle_frame_sample(n, R, seed, idx, cores):
+    """The oracle's framework on instances idx (threads over instances): (seconds, feasible)."""
+    import concurrent.futures as cf
+
+    import oracle
+
+    def one(q):
+        x, Rs, _ = oracle.frame(int(n[q]), float(R[q]), seed, inst=int(q), outer=FRAME_OUTER, s_iter=FRAME_SED_ITERS)
+        return oracle.max_overlap(x, Rs)[0] <= 1e-9
+
+    with cf.ThreadPoolExecutor(cores) as ex:
+        t0 = time.perf_counter()
+        ok = list(ex.map(one, idx))
+        t = time.perf_counter() - t0
+    return t, int(sum(ok))
+
+
+def cpu_baseline_frame(args, n, R):
+    import oracle
+
+    oracle.build()
+    cores = os.cpu_count() or 1
+    count = min(n.size, cores)
+    t, feas = oracle_frame_sample(n, R, args.seed, list(range(count)), cores)
+    return {"value": round(feas / t, 3), "unit": "feasible framework results/s", "cores": cores, "kind": "oracle",
+            "sample": f"first {count} of the {n.size} instances, one framework iteration, plain FP64, {cores} threads",
+            "seconds": round(t, 2), "success_rate": round(feas / count, 4)}
+
+
 def oracle_sed_sample(n, R, seed, idx, iters, cores):
     """The oracle's SED on instances idx (threads over instances): (seconds, feasible count)."""
     import concurrent.futures as cf
@@ -1200,7 +1339,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c3", choices=["c3", "c3-fp64", "c2", "c2-fp64", "c1", "c4", "c5", "adjust", "sed", "ksweep"])
+    ap.add_argument("--workload", default="c3", choices=["c3", "c3-fp64", "c2", "c2-fp64", "c1", "c4", "c5", "adjust", "sed", "ksweep", "frame"])
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shape")
@@ -1240,6 +1379,8 @@ def main():
         run_sed(args, rank, world, local)
     elif args.workload == "ksweep":
         run_ksweep(args, rank, world, local)
+    elif args.workload == "frame":
+        run_frame(args, rank, world, local)
     else:
         run_ours(args, rank, world, local)
 

@@ -456,6 +456,31 @@ pecc_status pecc_sed_get(pecc_sed *sed, double *x_dev, double *xbest_dev, double
  * NULL if sed is NULL. */
 pecc_ctx *pecc_sed_context(pecc_sed *sed);
 
+/* ============================================================================ the framework
+ * The framework of Sec. 5.1 (Algorithm 5) over a batch, with `outer` iterations in place of the
+ * cut-off time:
+ *   x* = GBO(random_solution(n, R_b)); (x*, R*) = adjust_container(x*, R_b);
+ *   repeat outer times: R = min(R_b, R*); x = SED(n, R) (sed_iters iterations);
+ *                       (x, R) = adjust_container(x, R); x*, R* = x, R where R < R*.
+ *   sed        the search (its instances, candidate slots and descent settings); the first layout
+ *              draws under `seed` (pecc_sed_start), SED call t under seed + 1 + t
+ *   adj        a context holding the same instances on the same stream, for the container
+ *              adjustments (its arithmetic and iteration limits apply); its radii and positions
+ *              are overwritten
+ *   Rb_dev     device double[num_instances]: the best-known radii R_b
+ *   Rbest_dev  device double[num_instances] out: R*;  xbest_dev device double[2 * sum n] out: x*
+ *   Rtrace_dev device double[(outer + 1) * num_instances] or NULL: R* after the first adjustment
+ *              and after every iteration (row t + 1 after iteration t)
+ *   adj_stats_dev device int32[3 * num_instances] or NULL: summed over every adjustment of the
+ *              call, the iterations (first num), then per instance {line-search trials, pairs
+ *              visited by the two-loop recursion} (as pecc_adjust_container's stats)
+ * Synchronises (radius changes); allocates scratch for the call.  Errors: PECC_ERR_ARG for NULL
+ * outputs, negative counts, or an adjustment context with other instances; the message is in
+ * pecc_sed_last_error(sed). */
+pecc_status pecc_frame_run(pecc_sed *sed, pecc_ctx *adj, const double *Rb_dev, uint64_t seed, int32_t outer,
+                           int32_t sed_iters, double lambda0, int32_t rounds, double *Rbest_dev, double *xbest_dev,
+                           double *Rtrace_dev, int32_t *adj_stats_dev);
+
 #ifdef __cplusplus
 }
 #endif

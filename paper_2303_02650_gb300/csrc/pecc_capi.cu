@@ -1436,4 +1436,86 @@ pecc_status pecc_sed_iterate(pecc_sed *sed, int32_t max_iterations, int32_t *ran
   return PECC_OK;
 }
 
+
+pecc_status pecc_frame_run(pecc_sed *sed, pecc_ctx *adj, const double *Rb_dev, uint64_t seed, int32_t outer,
+                           int32_t sed_iters, double lambda0, int32_t rounds, double *Rbest_dev, double *xbest_dev,
+                           double *Rtrace_dev, int32_t *adj_stats_dev) {
+  if (!sed || !adj) return PECC_ERR_ARG;
+  if (!Rb_dev || !Rbest_dev || !xbest_dev) return sfail(sed, PECC_ERR_ARG, "pecc_frame_run: NULL pointer");
+  if (outer < 0 || sed_iters < 0 || rounds < 0 || !(lambda0 >= 0.0) || !std::isfinite(lambda0))
+    return sfail(sed, PECC_ERR_ARG, "pecc_frame_run: outer, sed_iters, rounds >= 0 and lambda0 finite, >= 0");
+  if (adj->num != sed->num || adj->n != sed->n)
+    return sfail(sed, PECC_ERR_ARG, "pecc_frame_run: the adjustment context must hold the search's instances");
+  if (adj->stream != sed->stream)
+    return sfail(sed, PECC_ERR_ARG, "pecc_frame_run: the search and the adjustment context must share a stream");
+  const int num = sed->num;
+  if (num == 0) return PECC_OK;
+  cudaStream_t s = sed->stream;
+  double *R = nullptr, *Rn = nullptr;
+  double2 *x = nullptr;
+  int32_t *iters = nullptr, *status = nullptr, *stats = nullptr;
+  pecc_status st = PECC_OK;
+  auto cleanup = [&]() {
+    cudaStreamSynchronize(s);
+    cudaFree(R); cudaFree(Rn); cudaFree(x); cudaFree(iters); cudaFree(status); cudaFree(stats);
+  };
+  if (cudaMalloc(&R, sizeof(double) * num) || cudaMalloc(&Rn, sizeof(double) * num) ||
+      cudaMalloc(&x, sizeof(double2) * std::max<int64_t>(sed->total, 1)) ||
+      cudaMalloc(&iters, sizeof(int32_t) * num) || cudaMalloc(&status, sizeof(int32_t) * num) ||
+      cudaMalloc(&stats, sizeof(int32_t) * 2 * num)) {
+    cleanup();
+    return sfail(sed, PECC_ERR_OOM, "pecc_frame_run: scratch allocation failed");
+  }
+  auto ctx_err = [&](pecc_status e) { return sfail(sed, e, "%s", pecc_last_error(adj)); };
+  auto adjust = [&](const double *Rin, double *Rout, const double2 *xin) -> pecc_status {
+    pecc_status e;
+    if ((e = pecc_set_radius(adj, Rin))) return ctx_err(e);
+    if ((e = pecc_set_positions(adj, (const double *)xin))) return ctx_err(e);
+    if (cudaMemcpyAsync(Rout, Rin, sizeof(double) * num, cudaMemcpyDeviceToDevice, s)) return PECC_ERR_CUDA;
+    if ((e = pecc_adjust_container(adj, Rout, lambda0, rounds, iters, status, stats))) return ctx_err(e);
+    if ((e = pecc_get_positions(adj, (double *)x))) return ctx_err(e);
+    if (adj_stats_dev &&
+        (launch_add_i32(num, iters, adj_stats_dev, s) || launch_add_i32(2 * num, stats, adj_stats_dev + num, s)))
+      return PECC_ERR_CUDA;
+    return PECC_OK;
+  };
+  if (adj_stats_dev && cudaMemsetAsync(adj_stats_dev, 0, sizeof(int32_t) * 3 * num, s)) {
+    cleanup();
+    return sfail(sed, PECC_ERR_CUDA, "pecc_frame_run: clearing the statistics");
+  }
+  do {
+    // x* = GBO(random_solution(n, R_b)); (x*, R*) = adjust(x*, R_b)
+    if ((st = pecc_sed_set_radius(sed, Rb_dev)) || (st = pecc_sed_start(sed, seed))) break;
+    if ((st = pecc_sed_get(sed, (double *)x, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr)))
+      break;
+    if ((st = adjust(Rb_dev, Rbest_dev, x))) break;
+    if (cudaMemcpyAsync(xbest_dev, x, sizeof(double2) * sed->total, cudaMemcpyDeviceToDevice, s) ||
+        (Rtrace_dev && cudaMemcpyAsync(Rtrace_dev, Rbest_dev, sizeof(double) * num, cudaMemcpyDeviceToDevice, s))) {
+      st = PECC_ERR_CUDA;
+      break;
+    }
+    for (int t = 0; t < outer && st == PECC_OK; ++t) {
+      // R = min(R_b, R*); x = SED(n, R); (x, R) = adjust(x, R); keep it when R < R*
+      if (launch_frame_radius(num, Rb_dev, Rbest_dev, R, s)) { st = PECC_ERR_CUDA; break; }
+      int32_t ran = 0, left = 0;
+      if ((st = pecc_sed_set_radius(sed, R)) || (st = pecc_sed_start(sed, seed + 1 + (uint64_t)t)) ||
+          (st = pecc_sed_iterate(sed, sed_iters, &ran, &left)))
+        break;
+      if ((st = pecc_sed_get(sed, nullptr, (double *)x, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+                             nullptr)))
+        break;
+      if ((st = adjust(R, Rn, x))) break;
+      if (launch_frame_record(sed->p, Rn, x, Rbest_dev, (double2 *)xbest_dev, s) ||
+          (Rtrace_dev && cudaMemcpyAsync(Rtrace_dev + (size_t)(t + 1) * num, Rbest_dev, sizeof(double) * num,
+                                         cudaMemcpyDeviceToDevice, s))) {
+        st = PECC_ERR_CUDA;
+        break;
+      }
+    }
+  } while (false);
+  cleanup();
+  if (st == PECC_ERR_CUDA && sed->err.empty()) sfail(sed, st, "pecc_frame_run: CUDA error");
+  return st;
+}
+
 }  // extern "C"

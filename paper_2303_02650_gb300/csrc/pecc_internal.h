@@ -172,6 +172,11 @@ cudaError_t launch_sed_init(const SedParams &p, cudaStream_t s);
 cudaError_t launch_sed_prepare(const SedParams &p, int start, cudaStream_t s);  // prepare + active list
 cudaError_t launch_sed_select(const SedParams &p, const double *Ecand, int start, cudaStream_t s);
 cudaError_t launch_sed_status(const SedParams &p, int32_t *status, cudaStream_t s);
+// The framework of Sec. 5.1 (pecc_sed.cu): R = min(R_b, R*); keep (x, R) where R < R*.
+cudaError_t launch_frame_radius(int num, const double *Rb, const double *Rbest, double *R, cudaStream_t s);
+cudaError_t launch_add_i32(int count, const int32_t *a, int32_t *acc, cudaStream_t s);  // acc += a
+cudaError_t launch_frame_record(const SedParams &p, const double *Rn, const double2 *x, double *Rbest,
+                                double2 *xbest, cudaStream_t s);
 int adjust_max_m();
 
 // Largest instance whose coordinates the block energy + gradient kernel stages in shared memory.

@@ -188,7 +188,52 @@ __global__ void sed_status_kernel(SedParams P, int32_t *status) {
   if (q < P.num) status[q] = P.Eb[q] <= P.e_feas ? 0 : 3;
 }
 
+// The framework of Sec. 5.1: the search radius min(R_b, R*) of every instance.
+__global__ void frame_radius_kernel(int num, const double *Rb, const double *Rbest, double *R) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < num) R[q] = fmin(Rb[q], Rbest[q]);
+}
+
+// The framework's record: instance q keeps (x, R) when R < R*.  One block per instance.
+__global__ void frame_record_kernel(const int32_t *n, const int64_t *off, const double *Rn, const double2 *x,
+                                    double *Rbest, double2 *xbest) {
+  const int q = blockIdx.x;
+  __shared__ int better;
+  if (threadIdx.x == 0) {
+    better = Rn[q] < Rbest[q];
+    if (better) Rbest[q] = Rn[q];
+  }
+  __syncthreads();
+  if (!better) return;
+  const int64_t o = off[q];
+  for (int i = threadIdx.x; i < n[q]; i += blockDim.x) xbest[o + i] = x[o + i];
+}
+
+__global__ void add_i32_kernel(int count, const int32_t *a, int32_t *acc) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < count) acc[i] += a[i];
+}
+
 }  // namespace
+
+cudaError_t launch_add_i32(int count, const int32_t *a, int32_t *acc, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  add_i32_kernel<<<(count + 255) / 256, 256, 0, s>>>(count, a, acc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_frame_radius(int num, const double *Rb, const double *Rbest, double *R, cudaStream_t s) {
+  if (num <= 0) return cudaSuccess;
+  frame_radius_kernel<<<(num + 255) / 256, 256, 0, s>>>(num, Rb, Rbest, R);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_frame_record(const SedParams &p, const double *Rn, const double2 *x, double *Rbest,
+                                double2 *xbest, cudaStream_t s) {
+  if (p.num <= 0) return cudaSuccess;
+  frame_record_kernel<<<p.num, kSedT, 0, s>>>(p.n, p.off, Rn, x, Rbest, xbest);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_sed_status(const SedParams &p, int32_t *status, cudaStream_t s) {
   if (p.num <= 0) return cudaSuccess;

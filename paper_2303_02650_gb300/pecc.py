@@ -57,7 +57,8 @@ _EXPORTS = ["pecc_config_default", "pecc_create", "pecc_destroy", "pecc_set_radi
             "pecc_features", "pecc_targets", "pecc_warm_start", "pecc_autotune", "pecc_selftest_grid_barrier",
             "pecc_adjust_container", "pecc_sed_config_default", "pecc_sed_create", "pecc_sed_destroy",
             "pecc_sed_last_error", "pecc_sed_set_radius", "pecc_sed_start", "pecc_sed_set_state", "pecc_sed_iterate",
-            "pecc_sed_prepare", "pecc_sed_descend", "pecc_sed_select", "pecc_sed_get", "pecc_sed_context"]
+            "pecc_sed_prepare", "pecc_sed_descend", "pecc_sed_select", "pecc_sed_get", "pecc_sed_context",
+            "pecc_frame_run"]
 NOALLOC_MAX_N = 4096
 ENERGY_STAGE_BYTES = 96 * 1024  # PECC_ENERGY_STAGE_BYTES
 
@@ -131,6 +132,8 @@ def load(build_if_missing: bool = True):
         "pecc_sed_select": (st, [vp, vp]),
         "pecc_sed_get": (st, [vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]),
         "pecc_sed_context": (vp, [vp]),
+        "pecc_frame_run": (st, [vp, vp, vp, C.c_uint64, C.c_int32, C.c_int32, C.c_double, C.c_int32, vp, vp, vp,
+                                vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -570,3 +573,18 @@ class Sed:
         if candidates:
             out["cand"] = cand
         return out
+
+
+def frame_run(sed, adj, Rb, seed, outer=2, sed_iters=10, lambda0=1e-4, rounds=35, stats=None):
+    """pecc_frame_run: the framework of Sec. 5.1 over the instances of `sed` (a Sed), adjusting
+    in `adj` (a Context with the same instances).  Returns (R*, x*, R_trace) device tensors;
+    stats: optional device int32[3 * num] receiving the adjustments' summed statistics."""
+    dev = sed.dev
+    Rb = torch.as_tensor(Rb, dtype=torch.float64, device=dev).contiguous()
+    Rbest = torch.empty(sed.num, dtype=torch.float64, device=dev)
+    xbest = torch.empty((sed.total, 2), dtype=torch.float64, device=dev)
+    trace = torch.empty((outer + 1, sed.num), dtype=torch.float64, device=dev)
+    sed._check(sed._L.pecc_frame_run(sed.h, adj.h, _ptr(Rb), C.c_uint64(seed), int(outer), int(sed_iters),
+                                     float(lambda0), int(rounds), _ptr(Rbest), _ptr(xbest), _ptr(trace), _ptr(stats)),
+               "pecc_frame_run")
+    return Rbest, xbest, trace
