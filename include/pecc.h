@@ -336,9 +336,15 @@ pecc_status pecc_check_feasible_noalloc(const double *xy_dev, int32_t n, double 
 
 /* Container adjustment (Sec. 4.2, Algorithm adjust_container, Eq. 12): with z = (x, R) and
  * U(z, lambda) = E(x, R) + lambda R^2, for each of `rounds` rounds a limited-memory BFGS (the
- * descent's step, one batch, lbfgs_m pairs, a fresh memory each round, binary64) minimises U over
- * all of z, then lambda is halved; the paper's schedule is lambda0 = 1e-4, rounds = 35.  A round
- * ends when |grad U| <= gsum_tol, when no step is accepted, or after max_iter iterations.
+ * descent's step, one batch, lbfgs_m pairs, a fresh memory each round) minimises U over all of z,
+ * then lambda is halved; the paper's schedule is lambda0 = 1e-4, rounds = 35.  A round ends when
+ * |grad U| <= gsum_tol, when no step is accepted, or after max_iter iterations.
+ * Arithmetic: PECC_FP64 contexts run it in binary64.  The others use the polish arithmetic for
+ * the pair terms (binary64 differences and 4 - l^2, binary32 depths and forces), binary32
+ * quasi-Newton vectors, and binary64 energies, gradient storage and radius.  There, while E is
+ * large (a large lambda), a round settles within about 1e-6 of U's minimum; the schedule's late
+ * rounds (E -> 0) settle the radius as binary64 does. */
+/* Arguments:
  *   R_dev       device double[num_instances]: the starting radii in, the adjusted radii out (the
  *               context's own radii, those of pecc_set_radius, are left as they are)
  *   iters_dev   device int32[num_instances]: quasi-Newton iterations over all rounds
