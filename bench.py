@@ -52,7 +52,7 @@ UNIT = "feasible packings/s"
 # GBO batches per instance for the batch workloads: the fastest geometric batching on GB300 in the
 # batch-number study (k = 1 is faster still, but is one batch, plain L-BFGS); the paper's 3 / 5 for
 # n in [300, 1000) tuned its CPU dense BFGS.
-K_DEFAULT = {"c3": 2, "c3-fp64": 2, "c2": 2, "c2-fp64": 2}
+K_DEFAULT = {"c3": 2, "c3-fp64": 2, "c2": 2, "c2-fp64": 2, "c4": 2}
 # The build's own readings that the paper does not fix, tuned for the batch workloads on GB300
 # (sweeps of the step cap, the stagnation rules, the polish gate and the Verlet skin): a step cap
 # of 0.3 (within the skin rule 0.3 < 2 x 0.25), polishing only FP32 results with E <= 1e-5, the
@@ -61,7 +61,8 @@ K_DEFAULT = {"c3": 2, "c3-fp64": 2, "c2": 2, "c2-fp64": 2}
 CFG_DEFAULT = {"c3": ["step_max=0.3", "polish_gate=0.00001", "stall_window=5", "polish_stall_window=50"],
                "c3-fp64": ["step_max=0.3"],
                "c2": ["step_max=0.3", "polish_gate=0.00001", "stall_window=5", "polish_stall_window=50"],
-               "c2-fp64": ["step_max=0.3"]}
+               "c2-fp64": ["step_max=0.3"],
+               "c4": ["step_max=0.3"]}
 
 
 def workload(name: str):
@@ -1358,7 +1359,7 @@ def main():
                     help="set a pecc_config field of the descent context (repeatable), e.g. step_max=0.2")
     ap.add_argument("--k", type=int, default=-1,
                     help="batches per instance for every instance; 0: the paper's 1, 3, 5 by n; default: "
-                         "2 for c3, c3-fp64, c2, c2-fp64, the paper's otherwise")
+                         "2 for c3, c3-fp64, c2, c2-fp64, c4, the paper's otherwise")
     ap.add_argument("--dense", action="store_true",
                     help="ksweep workload: the explicit per-batch inverse Hessian (Eq. 11), binary64")
     args = ap.parse_args()
