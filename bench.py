@@ -1299,18 +1299,22 @@ def run_learned(args, rank, world, local):
     rounds = int(np.ceil(1e6 / (T * per_round)))
     mlp = pecc.MLP(seed=args.seed)
     t0 = time.time()
+    # the batch workload's GB300 settings for the descents the network learns from and precedes
+    dcfg = {"k_batches": 2, "step_max": 0.3}
+    ecfg = dict(dcfg, polish_gate=1e-5, stall_window=5, polish_stall_window=50)
     losses, rows = learned.train(mlp, synth.batch_manifest(per_round, seed=777), rounds=rounds, T=T, steps=10,
-                                 lr=1e-3, seed=5000)
+                                 lr=1e-3, seed=5000, **dcfg)
     torch.cuda.synchronize()
     train_s = time.time() - t0
     test = synth.batch_manifest(1024, seed=10**6 + 7)
     res = []
     with Clocks(local) as clk:
         for s in range(args.warmup):
-            learned.gain(mlp, (test[0][:64], test[1][:64]), seed=900 + s, precision=pecc.FP32_POLISH64)
+            learned.gain(mlp, (test[0][:64], test[1][:64]), seed=900 + s, precision=pecc.FP32_POLISH64, **ecfg)
         clk.mark_start()
         for s in range(args.steps):
-            res.append(learned.gain(mlp, test, seed=args.seed + s, warm_rounds=2, precision=pecc.FP32_POLISH64))
+            res.append(learned.gain(mlp, test, seed=args.seed + s, warm_rounds=2, precision=pecc.FP32_POLISH64,
+                                    **ecfg))
         clk.mark_end()
     wf = sum(r["warm_feasible"] for r in res)
     pf = sum(r["plain_feasible"] for r in res)
@@ -1323,6 +1327,7 @@ def run_learned(args, rank, world, local):
         "data": "synthetic (Philox-drawn layouts; seeded instance manifest); training samples from the descent",
         "config": {"workload": "c5: learned form, MLP 25-128-128-128-2 trained on 10^6 descent steps of the "
                                "batch distribution, evaluated on 1024 fresh instances n~U{300..1000}",
+                   "descent_settings": ecfg,
                    "train_rounds": rounds, "train_rows": rows, "train_seconds": round(train_s, 2),
                    "final_loss": round(losses[-1], 6), "first_loss": round(losses[0], 6), "warm_rounds": 2},
         "learned": {"feasible": wf, "ms": round(wms, 2), "success_rate": round(wf / (1024 * args.steps), 4),

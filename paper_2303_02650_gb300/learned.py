@@ -15,9 +15,10 @@ import torch
 from . import pecc
 
 
-def descent_samples(n, R, seed, T=50):
-    """Features and targets of every circle of the instances (n[], R[]) from one random start."""
-    with pecc.Context(n, precision=pecc.FP32, max_iter=T, stall_window=0) as c:
+def descent_samples(n, R, seed, T=50, **cfg):
+    """Features and targets of every circle of the instances (n[], R[]) from one random start.
+    cfg: further settings of the FP32 descent that makes the targets (k_batches, step_max, ...)."""
+    with pecc.Context(n, precision=pecc.FP32, max_iter=T, stall_window=0, **cfg) as c:
         c.set_radius(R)
         c.init_random(seed)
         x0 = c.get_positions()
@@ -27,13 +28,14 @@ def descent_samples(n, R, seed, T=50):
     return feat, tgt
 
 
-def train(mlp, manifest, rounds=8, T=50, steps=20, lr=1e-3, seed=1000, log=None):
-    """rounds x (fresh descent samples of the manifest's instances, `steps` full-batch Adam steps)."""
+def train(mlp, manifest, rounds=8, T=50, steps=20, lr=1e-3, seed=1000, log=None, **cfg):
+    """rounds x (fresh descent samples of the manifest's instances, `steps` full-batch Adam steps).
+    cfg: settings of the descent the targets come from (those the warm start will precede)."""
     n, R = manifest
     losses = []
     rows = 0
     for r in range(rounds):
-        feat, tgt = descent_samples(n, R, seed + r, T)
+        feat, tgt = descent_samples(n, R, seed + r, T, **cfg)
         rows += feat.shape[0]
         for s in range(steps):
             loss = mlp.train_step(feat, tgt, lr)
