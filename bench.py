@@ -1313,8 +1313,8 @@ def run_learned(args, rank, world, local):
             learned.gain(mlp, (test[0][:64], test[1][:64]), seed=900 + s, precision=pecc.FP32_POLISH64, **ecfg)
         clk.mark_start()
         for s in range(args.steps):
-            res.append(learned.gain(mlp, test, seed=args.seed + s, warm_rounds=2, precision=pecc.FP32_POLISH64,
-                                    **ecfg))
+            res.append(learned.gain(mlp, test, seed=args.seed + s, warm_rounds=args.warm_rounds,
+                                    precision=pecc.FP32_POLISH64, **ecfg))
         clk.mark_end()
     wf = sum(r["warm_feasible"] for r in res)
     pf = sum(r["plain_feasible"] for r in res)
@@ -1329,7 +1329,8 @@ def run_learned(args, rank, world, local):
                                "batch distribution, evaluated on 1024 fresh instances n~U{300..1000}",
                    "descent_settings": ecfg,
                    "train_rounds": rounds, "train_rows": rows, "train_seconds": round(train_s, 2),
-                   "final_loss": round(losses[-1], 6), "first_loss": round(losses[0], 6), "warm_rounds": 2},
+                   "final_loss": round(losses[-1], 6), "first_loss": round(losses[0], 6),
+                   "warm_rounds": args.warm_rounds},
         "learned": {"feasible": wf, "ms": round(wms, 2), "success_rate": round(wf / (1024 * args.steps), 4),
                     "iters_mean": round(float(np.mean([r["warm_iters"] for r in res])), 1)},
         "plain": {"feasible": pf, "ms": round(pms, 2), "value": round(pf / (pms / 1e3), 3),
@@ -1365,6 +1366,7 @@ def main():
     ap.add_argument("--k", type=int, default=-1,
                     help="batches per instance for every instance; 0: the paper's 1, 3, 5 by n; default: "
                          "2 for c3, c3-fp64, c2, c2-fp64, c4, the paper's otherwise")
+    ap.add_argument("--warm-rounds", type=int, default=2, help="c5: applications of the network before a descent")
     ap.add_argument("--dense", action="store_true",
                     help="ksweep workload: the explicit per-batch inverse Hessian (Eq. 11), binary64")
     args = ap.parse_args()
