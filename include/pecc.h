@@ -261,8 +261,8 @@ pecc_status pecc_get_launch(pecc_ctx *ctx, int32_t *block_threads, int32_t *bloc
  * Learned warm start.  Not in the paper: a per-circle MLP (25 -> 128 -> 128 -> 128 -> 2, ReLU,
  * BF16 weights on the tensor cores, FP32 accumulation and FP32 master weights) maps the local
  * neighborhood of a circle to a displacement; it is trained on displacements the descent itself
- * makes, and the plain descent stays its fallback and the test of its moves (a warm-start move of an instance is
- * kept only if it does not raise that instance's energy).
+ * makes, and the plain descent stays its fallback and the test of its moves (a warm-start move of
+ * an instance is kept only if it does not raise that instance's energy).
  * Features of circle i (FP32, correctly rounded): frame e_r = c_i/|c_i| (e_r = (1, 0) at the
  * origin), e_t = (-e_r.y, e_r.x); the 12 nearest other centres within 4.5 (by squared distance,
  * then index) as offsets c_j - c_i in (e_r, e_t) coordinates, zero-padded: 24 values; then
