@@ -1083,7 +1083,8 @@ def run_ours(args, rank, world, local):
         "config": {"workload": f"{args.workload}: {desc}",
                    "precision": "plain FP64" if prec == 0 else "FP32 bulk + FP64 polish",
                    "instances_per_step": int(n.size), "circles_per_step": int(n.sum()),
-                   "l_cut": 2.5, "rebuild_disp": 0.25, "lbfgs_m": 10, "max_iter": 2000,
+                   "l_cut": ctx.cfg.l_cut, "rebuild_disp": ctx.cfg.rebuild_disp, "lbfgs_m": ctx.cfg.lbfgs_m,
+                   "max_iter": ctx.cfg.max_iter, "step_max": ctx.cfg.step_max,
                    "k_batches": (args.k if args.k else "1 (n<300), 3 (n<500), 5"), "partition": "sector",
                    "settings": args.cfg,
                    "l2": "working set per step > 129 MB L2 (histories and lists of all instances); no flush",
