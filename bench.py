@@ -65,6 +65,24 @@ CFG_DEFAULT = {"c3": _TUNED, "c3-fp64": ["step_max=0.3", "lbfgs_m=5"],
                "c4": ["step_max=0.3", "lbfgs_m=5"]}
 
 
+def apply_workload_defaults(args):
+    """The workload's k (unless --k is given) and settings (each unless --cfg sets that field)."""
+    if args.k < 0:
+        args.k = K_DEFAULT.get(args.workload, 0)
+    given = {kv.split("=", 1)[0] for kv in args.cfg}
+    args.cfg = [kv for kv in CFG_DEFAULT.get(args.workload, []) if kv.split("=", 1)[0] not in given] + args.cfg
+    return args
+
+
+def cfg_fields(cfg):
+    """--cfg FIELD=VALUE strings as pecc_config keyword arguments."""
+    out = {}
+    for kv in cfg:
+        key, val = kv.split("=", 1)
+        out[key] = float(val) if any(c in val for c in ".e") else int(val)
+    return out
+
+
 def workload(name: str):
     if name in ("c3", "c3-fp64"):
         n, R = synth.batch_manifest(4096, seed=2303)
@@ -952,9 +970,7 @@ def run_ours(args, rank, world, local):
         shape["fuse_phases"] = args.fuse
     if args.k:
         shape["k_batches"] = args.k
-    for kv in args.cfg:  # further pecc_config fields, e.g. step_max=0.2
-        key, val = kv.split("=", 1)
-        shape[key] = float(val) if any(c in val for c in ".e") else int(val)
+    shape.update(cfg_fields(args.cfg))  # further pecc_config fields, e.g. step_max=0.2
     ctx = pecc.Context(n, precision=prec, **shape)
     ctx.set_radius(R)
     tuned = None
@@ -1372,11 +1388,7 @@ def main():
     ap.add_argument("--warm-rounds", type=int, default=2, help="c5: applications of the network before a descent")
     ap.add_argument("--dense", action="store_true",
                     help="ksweep workload: the explicit per-batch inverse Hessian (Eq. 11), binary64")
-    args = ap.parse_args()
-    if args.k < 0:
-        args.k = K_DEFAULT.get(args.workload, 0)
-    given = {kv.split("=", 1)[0] for kv in args.cfg}
-    args.cfg = [kv for kv in CFG_DEFAULT.get(args.workload, []) if kv.split("=", 1)[0] not in given] + args.cfg
+    args = apply_workload_defaults(ap.parse_args())
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
     rank = int(os.environ.get("RANK", "0"))

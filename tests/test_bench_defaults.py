@@ -1,0 +1,41 @@
+"""The bench's per-workload defaults (CPU): the batch workloads run at k = 2 with their tuned
+settings, a --cfg field replaces the default of that field only, and every default names a
+pecc_config field with a value of the field's type."""
+import argparse
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+pecc = pytest.importorskip("paper_2303_02650_gb300.pecc")
+
+
+def _args(workload, k=-1, cfg=()):
+    return bench.apply_workload_defaults(argparse.Namespace(workload=workload, k=k, cfg=list(cfg)))
+
+
+def test_batch_workload_defaults():
+    a = _args("c3")
+    assert a.k == 2
+    f = bench.cfg_fields(a.cfg)
+    assert f == {"step_max": 0.3, "polish_gate": 1e-5, "stall_window": 5, "polish_stall_window": 50, "lbfgs_m": 5}
+    assert _args("c3", k=0).k == 0  # the paper's k by n on request
+    assert _args("c5").k == 0 and _args("c5").cfg == []
+
+
+def test_cfg_overrides_only_its_field():
+    f = bench.cfg_fields(_args("c3", cfg=["lbfgs_m=10"]).cfg)
+    assert f["lbfgs_m"] == 10 and f["step_max"] == 0.3
+
+
+def test_defaults_name_config_fields():
+    names = {n for n, _ in pecc.Config._fields_}
+    for wl, cfg in bench.CFG_DEFAULT.items():
+        for key, val in bench.cfg_fields(cfg).items():
+            assert key in names, (wl, key)
+            ctype = dict(pecc.Config._fields_)[key]
+            assert isinstance(val, float) == (ctype.__name__ == "c_double"), (wl, key)
