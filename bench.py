@@ -13,7 +13,7 @@ the FP64 feasibility check.  Workloads:
   c4      one instance n = 100000, u = 0.85; FP32, whole-GPU descent (pair-gradient evaluations/s)
   c5      learned form: the MLP trained on 10^6 descent steps (instance-sweeps) of the batch
           distribution, then 1024 fresh instances n ~ U{300..1000}: warm start + descent vs plain
-  sed     SED (Sec. 5.2) on the first 1024 instances of the c3 batch at their radii: the start
+  sed     SED (Sec. 5.2) on the 4096 instances of the c3 batch at their radii: the start
           (random layout + descent) and 10 iterations of perturbed candidates (up to 25 per
           instance), all candidates of all instances descending together; FP32 + FP64 polish
   ksweep  the batch-number study of Sec. 6.5: for n = 300, 500, 1000 and k = 1, 2, 3, 5, 7, 10, 15
@@ -468,7 +468,7 @@ def cpu_baseline_adjust(args, n, R, lam0, rounds, budget_s=15.0):
             "success_rate": round(feas / count, 4)}
 
 
-SED_INSTANCES, SED_ITERS = 1024, 10
+SED_INSTANCES, SED_ITERS = 4096, 10
 KSWEEP_N = (300, 500, 1000)
 KSWEEP_K = (1, 2, 3, 5, 7, 10, 15)
 KSWEEP_INSTANCES = 608
