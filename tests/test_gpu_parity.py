@@ -265,6 +265,28 @@ def test_descend_short_runs_fp64(orc, k, sweeps):
         assert E[q] == pytest.approx(r.E, rel=1e-9)
 
 
+@pytest.mark.parametrize("sweeps", [1, 3, 6])
+def test_descend_short_runs_at_the_batch_settings_fp64(orc, sweeps):
+    """The batch workload's settings (k = 2, m = 5 secant pairs, step cap 0.3, so that the Verlet
+    rule rebuilds once the largest displacement passes 0.1): a few binary64 sweeps follow the
+    oracle's at the same settings to 1e-9."""
+    torch, pecc = need_gpu()
+    n = np.array([300, 257, 640, 1000], dtype=np.int32)
+    R = _radii(n, 0.82)
+    with _ctx(pecc, n, R, precision=0, k_batches=2, lbfgs_m=5, step_max=0.3, max_iter=sweeps) as c:
+        c.init_random(71)
+        x0 = c.get_positions().cpu().numpy()
+        iters, status = c.descend()
+        x1 = c.get_positions().cpu().numpy()
+        E = c.get_energy().cpu().numpy()
+        iters = iters.cpu().numpy()
+    for q, (a, b) in enumerate(zip(split(x0, n), split(x1, n))):
+        r = orc.gbo(a, float(R[q]), k=2, m=5, step_max=0.3, max_iter=sweeps)
+        assert iters[q] == r.iters
+        np.testing.assert_allclose(b, r.x, rtol=0, atol=1e-9 * float(R[q]))
+        assert E[q] == pytest.approx(r.E, rel=1e-9)
+
+
 @pytest.mark.parametrize("part,k,sweeps", [(3, 3, 2), (3, 5, 3), (1, 3, 2), (2, 4, 2)])
 def test_descend_short_runs_other_partitions_fp64(orc, part, k, sweeps):
     """The annulus, fence and random partitions of Sec. 4.1 (random: Philox-keyed order under
