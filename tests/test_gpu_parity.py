@@ -354,6 +354,21 @@ def _check_outcomes(orc, out, n, R):
             assert out["E"][q] <= 1e-20 and mo <= 1e-9, q
 
 
+def test_descend_outcomes_at_the_batch_settings(orc):
+    """The batch workload's settings on the FP32 + polish path (k = 2, m = 5, step cap 0.3, polish
+    gate 1e-5, stagnation checks every 5 / 50 sweeps): the same per-instance checks as at the
+    library's settings, and a feasible count within 5 of the oracle's at the same k, m and cap."""
+    torch, pecc = need_gpu()
+    n = np.array([300, 420, 640, 900, 1000, 512] * 4, dtype=np.int32)
+    R = _radii(n, 0.80)
+    cfg = dict(k_batches=2, lbfgs_m=5, step_max=0.3, polish_gate=1e-5, stall_window=5, polish_stall_window=50)
+    out = _solve(pecc, torch, n, R, 43, precision=2, **cfg)
+    _check_outcomes(orc, out, n, R)
+    _, ref = orc.solve_batch(n, R, 43, nthreads=8, k=2, m=5, step_max=0.3)
+    assert out["feasible"].sum() >= len(n) - 8
+    assert abs(int(out["feasible"].sum()) - int(ref["feasible"].sum())) <= 5
+
+
 @pytest.mark.parametrize("block", [128, 512])
 def test_descend_launch_shapes(orc, block):
     """FP32 descent and FP64 polish at 128 and 512 threads per block (the polish at min(block,
