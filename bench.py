@@ -235,16 +235,21 @@ def algorithmic_bytes_descent(n, k, iters, trials, m, vec_bytes=8, pos_bytes=8):
 ADJUST_INSTANCES = 304
 
 
-def adjust_bytes(n, iters, trials, visits, nnz_per_circle):
-    """Algorithmic bytes of the container adjustment, binary64, summed over the instances and all
-    rounds.  Per circle and iteration: the gradient norm (read g), the start copy (read x, write
-    zo), the two-loop's copy-in and final pass (dv = g; read dv and g, write dv), the secant pair
-    (read x, zo, gn, g, xb; write s, y in place) and its store (read 2, write 2 vectors): 19
+def adjust_bytes(n, iters, trials, visits, nnz_per_circle, mixed=False):
+    """Algorithmic bytes of the container adjustment, summed over the instances and all rounds.
+    Binary64 form, per circle and iteration: the gradient norm (read g), the start copy (read x,
+    write zo), the two-loop's copy-in and final pass (dv = g; read dv and g, write dv), the secant
+    pair (read x, zo, gn, g, xb; write s, y in place) and its store (read 2, write 2 vectors): 19
     double2 = 304 B.  Per pair visited by the two-loop: s, y and dv read and dv written in each
     loop, 128 B.  Per line-search trial: the trial point (read zo, dv; write x) and one energy +
     gradient pass (x, two row pointers, the row's column indices, write the gradient):
-    88 + 4 D B for D list entries per circle."""
+    88 + 4 D B for D list entries per circle.
+    Mixed form: the gradients and the quasi-Newton vectors are float2 (8 B), the coordinates x,
+    zo and xb double2.  Per iteration 8 + 32 + 16 + 24 + 80 + 32 = 192 B, per visited pair 64 B,
+    per trial 40 + 32 + 4 D B."""
     n = np.asarray(n, dtype=np.float64)
+    if mixed:
+        return float(np.sum(n * (192.0 * iters + 64.0 * visits + (72.0 + 4.0 * nnz_per_circle) * trials)))
     return float(np.sum(n * (304.0 * iters + 128.0 * visits + (88.0 + 4.0 * nnz_per_circle) * trials)))
 
 
@@ -255,14 +260,14 @@ def adjust_flops(n, iters, trials, visits, nnz_per_circle, mixed=False):
     dot and an axpy in each loop, 16; per line-search trial, the trial point 4, the wall term 12
     and per directed list entry 14 (differences 2, squared distance 3, sqrt, 2 - l, the division,
     the factor, two products, two sums, half an energy term).
-    Mixed form (binary32 depths, forces and quasi-Newton vectors): only its binary64 operations
-    count.  Per iteration, gradient norm 4, g'd 4, the secant differences 4 and the displacement
-    4: 16; per trial, the trial point 4, the wall's squared radius and difference 4, and per
+    Mixed form (binary32 depths, forces, gradients and quasi-Newton vectors): only its binary64
+    operations count.  Per iteration, the secant pair's position differences 2 and the
+    displacement 4: 6; per trial, the trial point 4, the wall's squared radius and difference 4, and per
     directed list entry 6 (differences 2, squared distance 3, 4 - l^2 1) plus half an energy
     term 1."""
     n = np.asarray(n, dtype=np.float64)
     if mixed:
-        return float(np.sum(n * (16.0 * iters + (8.0 + 7.0 * nnz_per_circle) * trials)))
+        return float(np.sum(n * (6.0 * iters + (8.0 + 7.0 * nnz_per_circle) * trials)))
     return float(np.sum(n * (32.0 * iters + 16.0 * visits + (16.0 + 14.0 * nnz_per_circle) * trials)))
 
 
@@ -356,7 +361,7 @@ def run_adjust(args, rank, world, local):
     if dist:
         ms_total, feasible = combine_ranks(dist, ms_total, feasible, "cuda")
     value = feasible / (ms_total / 1e3)
-    alg = adjust_bytes(n, it, sts[:, 0], sts[:, 1], nnz_pc)
+    alg = adjust_bytes(n, it, sts[:, 0], sts[:, 1], nnz_pc, mixed=True)
     flops = adjust_flops(n, it, sts[:, 0], sts[:, 1], nnz_pc, mixed=True)
     dom_ms = float(np.mean(adj_ms))
     hbm, peak_kind = peaks()
@@ -397,7 +402,7 @@ def run_adjust(args, rank, world, local):
                                ", each instance from the layout its FP32 + polish descent reached",
                    "lambda0": lam0, "rounds": rounds, "lbfgs_m": 10,
                    "arithmetic": "mixed: binary64 coordinates, differences, energies and radius; binary32 depths, "
-                                 "forces and quasi-Newton vectors",
+                                 "forces, gradients and quasi-Newton vectors",
                    "max_iter_per_round": args.adjust_max_iter or 2000,
                    "instances_per_step": int(n.size), "circles_per_step": int(n.sum()),
                    "feasible_before": feas_before,
@@ -840,7 +845,7 @@ def run_frame(args, rank, world, local):
                                ", R_b = their radii",
                    "outer_iterations": FRAME_OUTER, "sed_iterations": FRAME_SED_ITERS, "max_candidates": 25,
                    "lambda0": 1e-4, "rounds": 35, "descent_settings": dcfg,
-                   "adjustment": "mixed form (binary32 depths, forces and quasi-Newton vectors)",
+                   "adjustment": "mixed form (binary32 depths, forces, gradients and quasi-Newton vectors)",
                    "l2": "working set per step > 129 MB L2 (candidate slots); no flush",
                    "parallelism": f"instances sharded over {world} GPU(s), no collective on the data path"},
         "success_rate": round(feasible / (args.steps * n.size * world), 4),

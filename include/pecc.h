@@ -341,7 +341,7 @@ pecc_status pecc_check_feasible_noalloc(const double *xy_dev, int32_t n, double 
  * |grad U| <= gsum_tol, when no step is accepted, or after max_iter iterations.
  * Arithmetic: PECC_FP64 contexts run it in binary64.  The others use the polish arithmetic for
  * the pair terms (binary64 differences and 4 - l^2, binary32 depths and forces), binary32
- * quasi-Newton vectors, and binary64 energies, gradient storage and radius.  There, while E is
+ * gradients and quasi-Newton vectors, and binary64 energies and radius.  There, while E is
  * large (a large lambda), a round settles within about 1e-6 of U's minimum; the schedule's late
  * rounds (E -> 0) settle the radius as binary64 does. */
 /* Arguments:

@@ -10,8 +10,8 @@
 //   <Arith64, double>  binary64 throughout (the binary64 contexts);
 //   <ArithMix, float>  the descent's polish arithmetic for the pair and wall terms (binary64
 //                      coordinates, differences and the near-contact quantities 4 - l^2 and
-//                      |c|^2 - (R - 1)^2, binary32 depths and forces), binary32 quasi-Newton
-//                      vectors, binary64 energy sums, gradient storage and everything about R.
+//                      |c|^2 - (R - 1)^2, binary32 depths and forces), binary32 gradients and
+//                      quasi-Newton vectors, binary64 energy sums and everything about R.
 // GB300 issues few binary64 operations per clock; in the binary64 form the pair terms and the
 // two-loop recursion keep that pipe about 80 % busy.  The binary32 depths put a relative jitter of
 // about 1e-7 on E, so the Armijo test on U resolves U's minimum only to about 1e-6 of R while E is
@@ -60,7 +60,8 @@ __device__ __forceinline__ void bred(AdjSmem &S, double (&v)[NV], const bool (&m
 template <class A, typename VT>
 __global__ void __launch_bounds__(kAdjT) adjust_kernel(AdjustParams P) {
   using V2 = v2<VT>;
-  using GT = typename A::vec_t;  // the forces' type
+  using GT = typename A::vec_t;  // the forces' and the stored gradient's type
+  using GV2 = v2<GT>;
   __shared__ AdjSmem S;
   const int tid = threadIdx.x, T = blockDim.x;
   const double lc2 = P.l_cut * P.l_cut;
@@ -84,8 +85,9 @@ __global__ void __launch_bounds__(kAdjT) adjust_kernel(AdjustParams P) {
     }
     if (P.from32)
       for (int i = tid; i < n; i += T) { const float2 f = P.x32[D.off + i]; x[i] = make_double2(f.x, f.y); }
-    // gradients in binary64; the direction and the pairs in VT (the buffers are sized for double2)
-    double2 *g = P.g + D.off, *gn = P.gn + D.off;
+    // gradients in the forces' type, the direction and the pairs in VT (the buffers are sized for
+    // double2)
+    GV2 *g = (GV2 *)(P.g + D.off), *gn = (GV2 *)(P.gn + D.off);
     V2 *dv = (V2 *)(P.d + D.off), *sv = (V2 *)(P.sv + D.off);
     double2 *zo = P.zo + D.off, *xb = P.xb + D.off, *xs = P.xs + D.off;
     V2 *Sv = (V2 *)(P.S + (int64_t)kAdjM * D.off), *Yv = (V2 *)(P.Y + (int64_t)kAdjM * D.off);
@@ -117,7 +119,7 @@ __global__ void __launch_bounds__(kAdjT) adjust_kernel(AdjustParams P) {
       return true;
     };
     // U, its gradient over x into gout, and dU/dR, at the current x and radius Rz
-    auto eval = [&](double2 *gout, double Rz, double lam, double &U, double &gR) {
+    auto eval = [&](GV2 *gout, double Rz, double lam, double &U, double &gR) {
       const double Rm1sq = (Rz >= 1.0) ? (Rz - 1.0) * (Rz - 1.0) : -1.0;
       double v[2] = {0.0, 0.0};
       const bool mx[2] = {false, false};
@@ -137,7 +139,7 @@ __global__ void __launch_bounds__(kAdjT) adjust_kernel(AdjustParams P) {
         gx += fx; gy += fy;
         v[0] += e + d0 * d0;
         v[1] += d0;
-        gout[i] = make_double2((double)gx, (double)gy);
+        gout[i] = mk2<GT>(gx, gy);
       }
       bred<2>(S, v, mx);
       U = v[0] + lam * Rz * Rz;
@@ -158,8 +160,9 @@ __global__ void __launch_bounds__(kAdjT) adjust_kernel(AdjustParams P) {
         }
         ++iters;
         const bool mx1[1] = {false};
-        double v1[1] = {0.0};
-        for (int i = tid; i < n; i += T) { const double2 gi = g[i]; v1[0] += gi.x * gi.x + gi.y * gi.y; }
+        GT p1 = 0;
+        for (int i = tid; i < n; i += T) { const GV2 gi = g[i]; p1 += gi.x * gi.x + gi.y * gi.y; }
+        double v1[1] = {(double)p1};
         bred<1>(S, v1, mx1);
         const double gg = v1[0] + gR * gR, gnorm = sqrt(gg);
         if (!(gnorm > P.gsum_tol)) { status = 1; break; }
@@ -175,7 +178,7 @@ __global__ void __launch_bounds__(kAdjT) adjust_kernel(AdjustParams P) {
           }
           // ---- two-loop recursion (Nocedal & Wright, Alg. 7.4) over the stored pairs; q in dv
           visits += count;
-          for (int i = tid; i < n; i += T) { const double2 gi = g[i]; dv[i] = mk2<VT>((VT)gi.x, (VT)gi.y); }
+          for (int i = tid; i < n; i += T) { const GV2 gi = g[i]; dv[i] = mk2<VT>((VT)gi.x, (VT)gi.y); }
           double qR = gR;
           for (int c = count - 1; c >= 0; --c) {
             const int sl = (head + c) % P.m;
@@ -225,17 +228,17 @@ __global__ void __launch_bounds__(kAdjT) adjust_kernel(AdjustParams P) {
           }
           // d = -q; g'd and the largest move (circles and the radius)
           const bool mx2[2] = {false, true};
-          double p2 = 0.0;
+          GT p2 = 0;
           VT m2 = 0;
           for (int i = tid; i < n; i += T) {
             V2 b = dv[i];
             b.x = -b.x; b.y = -b.y;
             dv[i] = b;
-            const double2 gi = g[i];
-            p2 += gi.x * (double)b.x + gi.y * (double)b.y;
+            const GV2 gi = g[i];
+            p2 += gi.x * (GT)b.x + gi.y * (GT)b.y;
             m2 = max(m2, b.x * b.x + b.y * b.y);
           }
-          double v2[2] = {p2, (double)m2};
+          double v2[2] = {(double)p2, (double)m2};
           bred<2>(S, v2, mx2);
           double dR = -qR;
           double gd = v2[0] + gR * dR;
@@ -243,13 +246,13 @@ __global__ void __launch_bounds__(kAdjT) adjust_kernel(AdjustParams P) {
           if (!(gd < 0.0)) {  // not a descent direction: drop the memory, take -g
             count = 0;
             head = 0;
-            double m3 = 0.0;
+            GT m3 = 0;
             for (int i = tid; i < n; i += T) {
-              const double2 gi = g[i];
+              const GV2 gi = g[i];
               dv[i] = mk2<VT>((VT)-gi.x, (VT)-gi.y);
-              m3 = fmax(m3, gi.x * gi.x + gi.y * gi.y);
+              m3 = max(m3, gi.x * gi.x + gi.y * gi.y);
             }
-            double v3[1] = {m3};
+            double v3[1] = {(double)m3};
             const bool mx3[1] = {true};
             bred<1>(S, v3, mx3);
             dR = -gR;
@@ -282,7 +285,8 @@ __global__ void __launch_bounds__(kAdjT) adjust_kernel(AdjustParams P) {
         VT p40 = 0, p41 = 0, p42 = 0;
         double m43 = 0.0;
         for (int i = tid; i < n; i += T) {
-          const double2 xn = x[i], x0 = zo[i], b0 = xb[i], gnew = gn[i], gold = g[i];
+          const double2 xn = x[i], x0 = zo[i], b0 = xb[i];
+          const GV2 gnew = gn[i], gold = g[i];
           const V2 s_ = mk2<VT>((VT)(xn.x - x0.x), (VT)(xn.y - x0.y));
           const V2 y_ = mk2<VT>((VT)(gnew.x - gold.x), (VT)(gnew.y - gold.y));
           sv[i] = s_;
@@ -306,7 +310,7 @@ __global__ void __launch_bounds__(kAdjT) adjust_kernel(AdjustParams P) {
           for (int i = tid; i < n; i += T) { s_[i] = sv[i]; y_[i] = dv[i]; }
           if (tid == 0) { S.sR[sl] = sR; S.yR[sl] = yR; S.rho[sl] = 1.0 / sy; S.yy[sl] = yy; }
         }
-        { double2 *t_ = g; g = gn; gn = t_; }  // the trial's gradient is the next iteration's
+        { GV2 *t_ = g; g = gn; gn = t_; }  // the trial's gradient is the next iteration's
         U0 = Ut;
         gR = gnR;
         __syncthreads();
