@@ -189,8 +189,10 @@ pecc_status pecc_export_cells(pecc_ctx *ctx, uint32_t *key_dev, int32_t *order_d
  * grad_dev = device float2[sum n] (FP32 contexts) or double2[sum n] (PECC_FP64).
  * One block per instance with its coordinates staged in shared memory (one launch for all
  * instances up to PECC_ENERGY_STAGE_BYTES of coordinates); larger instances take one thread
- * per circle and a per-instance reduction.  The gradient is gathered (no atomics) and E is
- * summed in a fixed order (deterministic). */
+ * per circle and a per-instance reduction.
+ * The gradient is gathered (no atomics) and E is summed in a fixed order (deterministic).
+ * An instance whose last build overflowed its list capacity (nbr_capacity) gets E = NaN and
+ * a NaN gradient. */
 pecc_status pecc_energy_grad(pecc_ctx *ctx, double *E_dev, void *grad_dev);
 
 /* Same, with an explicit arithmetic: eval = PECC_FP64 (double2 gradient), PECC_FP32

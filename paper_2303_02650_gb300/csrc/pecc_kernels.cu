@@ -134,6 +134,12 @@ __global__ void __launch_bounds__(256) energy_grad_kernel(StandaloneParams P, in
   vec_t gx = 0, gy = 0;
   acc_t e = 0;
   const int lo = __ldg(rp + i), hi = __ldg(rp + i + 1);
+  if (__ldg(rp + P.desc[q].n) > P.desc[q].cap) {  // the last build overflowed the list's capacity: no valid list
+    VV gv; gv.x = gv.y = (vec_t)NAN;
+    ((VV *)grad_)[gi] = gv;
+    ((acc_t *)ecirc_)[gi] = (acc_t)NAN;
+    return;
+  }
   for (int t = lo; t < hi; ++t) {
     int j = __ldg(cl + t);
     vec_t fx, fy;
@@ -168,18 +174,28 @@ __global__ void __launch_bounds__(256) energy_grad_block_kernel(StandaloneParams
   const int q = blockIdx.x;
   const int n = P.desc[q].n;
   if (n > stage_n) return;  // the per-circle kernels' instance (uniform across the block)
+  if (n == 0) {
+    if (threadIdx.x == 0) E[q] = 0.0;
+    return;
+  }
   const int64_t off = P.desc[q].off;
   const int64_t col_off = P.desc[q].col_s_off;
   const double Rd = P.desc[q].R;
   const acc_t R = (acc_t)Rd;
   const acc_t Rm1sq = (acc_t)((Rd >= 1.0) ? (Rd - 1.0) * (Rd - 1.0) : -1.0);
   const PP *x = (sizeof(pos_t) == 4) ? (const PP *)(P.x32 + off) : (const PP *)(P.x64 + off);
-  PP *xs = (PP *)stage;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) xs[i] = x[i];
-  __syncthreads();
   const int32_t *rp = P.rp + off + q;
   const int32_t *cl = P.col + col_off;
   VV *grad = (VV *)grad_ + off;
+  const int end = __ldg(rp + n);  // in flight with the coordinates
+  PP *xs = (PP *)stage;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) xs[i] = x[i];
+  if (end > P.desc[q].cap) {  // the last build overflowed the list's capacity: no valid list
+    for (int i = threadIdx.x; i < n; i += blockDim.x) { VV gv; gv.x = gv.y = (vec_t)NAN; grad[i] = gv; }
+    if (threadIdx.x == 0) E[q] = NAN;
+    return;
+  }
+  __syncthreads();
   acc_t e = 0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     const PP xi = xs[i];

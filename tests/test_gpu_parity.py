@@ -150,6 +150,44 @@ def test_energy_grad_staged_and_per_circle_paths(orc):
     assert np.all(np.linalg.norm(g - gr, axis=1) <= 1e-12 * np.maximum(gn, 1e-300) + 1e-13)
 
 
+def test_energy_grad_over_dense_instance(orc):
+    """An over-dense instance (about 19 neighbors per circle, rows far longer than at the
+    method's densities) beside ordinary and empty ones: every instance matches the oracle."""
+    torch, pecc = need_gpu()
+    n = np.array([300, 200, 0, 37], dtype=np.int32)
+    R = np.array([math.sqrt(300 / 2.5), synth.radius(200, 0.83), 5.0, synth.radius(37, 0.83)])
+    with _ctx(pecc, n, R, precision=0, nbr_capacity=40.0) as c:
+        xy = _layout(c, torch, 21)
+        c.rebuild_neighbors(force=True)
+        rp, col = [t.cpu().numpy() for t in c.export_neighbors()]
+        E, g = [t.cpu().numpy() for t in c.energy_grad()]
+    assert rp[300] - rp[0] > 12 * 300  # long rows
+    Er, gr = _oracle_eg(orc, xy, n, R)
+    np.testing.assert_allclose(E, Er, rtol=1e-12, atol=1e-300)
+    gn = np.linalg.norm(gr, axis=1)
+    assert np.all(np.linalg.norm(g - gr, axis=1) <= 1e-12 * np.maximum(gn, 1e-300) + 1e-13)
+
+
+def test_energy_grad_after_list_overflow_is_nan(orc):
+    """Every circle of the first instance at one point: its list needs n - 1 entries per circle,
+    over a capacity of 2 + 64 / n.  Its energy and gradient come back NaN (nothing past the
+    capacity is read); the other instance, sparse enough for its capacity, is unaffected."""
+    torch, pecc = need_gpu()
+    n = np.array([64, 10], dtype=np.int32)
+    R = np.array([20.0, 20.0])
+    with _ctx(pecc, n, R, precision=0, nbr_capacity=2.0) as c:
+        c.init_random(5)
+        xy = c.get_positions().cpu().numpy()
+        xy[:64] = 0.0
+        c.set_positions(torch.from_numpy(xy))
+        c.rebuild_neighbors(force=True)
+        E, g = [t.cpu().numpy() for t in c.energy_grad()]
+    assert np.isnan(E[0]) and np.all(np.isnan(g[:64]))
+    Er, gr = _oracle_eg(orc, xy[64:], n[1:], R[1:])
+    assert E[1] == pytest.approx(Er[0], rel=1e-12)
+    assert np.all(np.isfinite(g[64:]))
+
+
 def test_energy_grad_fp32(orc):
     """FP32: d = 2 - l carries an absolute error of about ulp(2) = 2.4e-7 per pair (and the
     wall depth about ulp(R)), so E is compared to 1e-5 relative plus 4 ulp32(2) * sum 2 d, and
