@@ -489,10 +489,12 @@ pecc_status pecc_export_neighbors(pecc_ctx *ctx, int32_t *row_ptr_dev, int32_t *
   for (int q = 0; q < ctx->num; ++q) base[q + 1] = base[q] + v[q];
   int64_t *dbase = nullptr;
   CK(cudaMalloc(&dbase, sizeof(int64_t) * (ctx->num + 1)));
-  cudaMemcpyAsync(dbase, base.data(), sizeof(int64_t) * (ctx->num + 1), cudaMemcpyHostToDevice, ctx->stream);
-  cudaError_t e = launch_export_csr(sparams(ctx), dbase, row_ptr_dev, col_dev, ctx->stream);
-  cudaStreamSynchronize(ctx->stream);
+  cudaError_t e = cudaMemcpyAsync(dbase, base.data(), sizeof(int64_t) * (ctx->num + 1), cudaMemcpyHostToDevice,
+                                  ctx->stream);
+  if (e == cudaSuccess) e = launch_export_csr(sparams(ctx), dbase, row_ptr_dev, col_dev, ctx->stream);
+  const cudaError_t es = cudaStreamSynchronize(ctx->stream);  // base[] and dbase live until here
   cudaFree(dbase);
+  if (e == cudaSuccess) e = es;
   if (e != cudaSuccess) return fail(ctx, PECC_ERR_CUDA, "export: %s", cudaGetErrorString(e));
   return PECC_OK;
 }
