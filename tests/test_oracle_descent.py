@@ -21,6 +21,24 @@ def test_pseudo_angle_orders_like_atan2(orc):
     assert orc.pseudo_angle(1.0, -0.0) == 0.0 and orc.pseudo_angle(0.0, 0.0) == 0.0
 
 
+def test_default_batch_number_follows_the_paper_scales(orc):
+    """Sec. 6.1 sets k = 3 on the moderate scale (300 <= n <= 320) and k = 5 on both large scales
+    (500 <= n <= 1000); the gap between them is read as k = 3, and smaller instances as one
+    batch.  A descent without an explicit k uses that number."""
+    assert [orc.default_k(n) for n in (1, 2, 50, 299)] == [1, 1, 1, 1]
+    assert all(orc.default_k(n) == 3 for n in range(300, 321))
+    assert all(orc.default_k(n) == 3 for n in (321, 400, 499))
+    assert all(orc.default_k(n) == 5 for n in range(500, 1001))
+    assert orc.default_k(100000) == 5
+    # gbo without k: the same sweeps as with the explicit default
+    xy = synth.random_layout(320, synth.radius(320, 0.8), seed=5)
+    R = synth.radius(320, 0.8)
+    a = orc.gbo(xy, R, max_iter=3)
+    b = orc.gbo(xy, R, k=3, max_iter=3)
+    assert a.iters == b.iters and np.array_equal(a.x, b.x)
+    assert not np.array_equal(a.x, orc.gbo(xy, R, k=1, max_iter=3).x)
+
+
 def test_partition_sizes_and_keys(orc):
     xy = synth.random_layout(1003, 30.0, seed=3)
     for k in [1, 3, 5, 7, 1003]:
