@@ -1231,11 +1231,24 @@ def run_reference(args, rank, world):
         return run_reference_adjust(args, world)
     if args.workload == "sed":
         return run_reference_sed(args, world)
-    n, R, prec, desc = workload(args.workload)
+    if args.workload == "frame":
+        return run_reference_frame(args, world)
+    if args.workload == "ksweep":
+        return run_reference_ksweep(args, world)
+    if args.workload == "c5":
+        # the learned form's evaluation set, descended by the plain method (the oracle has no
+        # network: the plain descent is the learned form's fallback and the judge of its error)
+        n, R = synth.batch_manifest(1024, seed=10**6 + 7)
+        desc = "learned form's evaluation set: 1024 fresh instances n~U{300..1000}, plain FP64 descent"
+    else:
+        n, R, prec, desc = workload(args.workload)
     cores = os.cpu_count() or 1
     per_step = max(1, min(n.size, 2 * cores))
+    # warm-up: the library and the thread pool, on the smallest instance of the workload (a whole
+    # 100000-circle descent would not be a bounded warm-up)
+    w0 = int(np.argmin(n))
     for w in range(args.warmup):
-        oracle.solve_batch(n[:1], R[:1], args.seed + w, nthreads=1)
+        oracle.solve_batch(n[w0:w0 + 1], R[w0:w0 + 1], args.seed + w, nthreads=1)
     tot_t, tot_f = 0.0, 0
     for s in range(args.steps):
         lo = (s * per_step) % n.size
@@ -1309,6 +1322,62 @@ def run_reference_sed(args, world):
                    "precision": "FP64 oracle"},
         "cpu_baseline": {"value": round(value, 3), "unit": unit, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": round(value, 3), "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def run_reference_frame(args, world):
+    n, R, _, desc = workload("c3")
+    n, R = n[:FRAME_INSTANCES], R[:FRAME_INSTANCES]
+    cores = os.cpu_count() or 1
+    per_step = max(1, cores)
+    oracle_frame_sample(n, R, args.seed, [int(np.argmin(n))], 1)  # warm-up
+    tot_t, tot_f = 0.0, 0
+    for s in range(args.steps):
+        idx = [(s * per_step + i) % n.size for i in range(per_step)]
+        t, f = oracle_frame_sample(n, R, args.seed, idx, cores)
+        tot_t += t
+        tot_f += f
+    value = tot_f / tot_t
+    unit = "feasible framework results/s"
+    sample = (f"{per_step} instances per step, one framework iteration (SED with {FRAME_SED_ITERS} iterations), "
+              f"plain FP64, {cores} threads")
+    print(json.dumps({
+        "impl": "reference", "metric": "framework runs/s (Sec. 5.1; layout feasible, overlap<=1e-9, at the final radius)",
+        "value": round(value, 3), "unit": unit, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(tot_t * 1e3 / args.steps, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"frame: the framework of Sec. 5.1 on the first {n.size} instances of the " + desc +
+                               ", R_b = their radii", "precision": "FP64 oracle"},
+        "cpu_baseline": {"value": round(value, 3), "unit": unit, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": round(value, 3), "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def run_reference_ksweep(args, world):
+    """The oracle's batch-number ratio (n = 1000, sector, k = 5 over k = 1), one sample per step."""
+    dense = bool(args.dense)
+    cores = os.cpu_count() or 1
+    rs, secs = [], []
+    for s in range(args.steps):
+        t0 = time.perf_counter()
+        r = cpu_baseline_ksweep(argparse.Namespace(seed=args.seed + s), count=cores, dense=dense)
+        secs.append(time.perf_counter() - t0)
+        rs.append(r["value"])
+    value = float(np.mean(rs))
+    unit = "ratio T_k5 / T_k1"
+    sample = (f"{cores} descents of n = 1000 at each of k = 1 and k = 5 per step, {cores} threads" +
+              (", explicit inverse Hessian" if dense else ", L-BFGS"))
+    print(json.dumps({
+        "impl": "reference",
+        "metric": "descent time at the best batch number over k = 1 (n = 1000, sector; Sec. 6.5 ratio)" +
+                  (", explicit per-batch inverse Hessian (Eq. 11)" if dense else ""),
+        "value": round(value, 4), "unit": unit, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(1e3 * float(np.mean(secs)), 3), "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "ksweep: n = 1000 (sector), u = 0.83, k = 5 (the paper's large-scale setting) against "
+                               "k = 1; a sweep over every k would not fit a bounded sample", "precision": "FP64 oracle"},
+        "cpu_baseline": {"value": round(value, 4), "unit": unit, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": round(value, 4), "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
 

@@ -39,3 +39,27 @@ def test_defaults_name_config_fields():
             assert key in names, (wl, key)
             ctype = dict(pecc.Config._fields_)[key]
             assert isinstance(val, float) == (ctype.__name__ == "c_double"), (wl, key)
+
+
+def _reference_line(*extra):
+    import json
+    import subprocess
+
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                          "--warmup", "3", *extra], capture_output=True, text=True, timeout=300, cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+@pytest.mark.parametrize("extra", [(), ("--workload", "ksweep")])
+def test_reference_arm_line(extra):
+    """The reference arm (the FP64 oracle on the host cores) prints one JSON line with the bench's
+    keys: its own cpu_baseline and an e2e with no host-device copies, both carrying the line's value."""
+    r = _reference_line(*extra)
+    assert r["impl"] == "reference" and r["value"] > 0 and r["steps"] == 1 and r["warmup"] == 3
+    for key in ("metric", "unit", "n_gpus", "ms_per_step", "higher_is_better", "scaling", "dtype", "config"):
+        assert key in r, key
+    cb = r["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["sample"] and cb["value"] == r["value"]
+    assert cb["unit"] == r["unit"]
+    assert r["e2e"] == {"value": r["value"], "unit": r["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
