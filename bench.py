@@ -1244,11 +1244,12 @@ def run_reference(args, rank, world):
         n, R, prec, desc = workload(args.workload)
     cores = os.cpu_count() or 1
     per_step = max(1, min(n.size, 2 * cores))
-    # warm-up: the library and the thread pool, on the smallest instance of the workload (a whole
-    # 100000-circle descent would not be a bounded warm-up)
+    # warm-up: the library and the thread pool, on the smallest instance of the workload, or on 50
+    # circles where that is larger than 1000 (one 100000-circle descent takes minutes)
     w0 = int(np.argmin(n))
+    wn, wR = (n[w0:w0 + 1], R[w0:w0 + 1]) if n[w0] <= 1000 else (np.array([50], np.int32), np.array([synth.radius(50, 0.8)]))
     for w in range(args.warmup):
-        oracle.solve_batch(n[w0:w0 + 1], R[w0:w0 + 1], args.seed + w, nthreads=1)
+        oracle.solve_batch(wn, wR, args.seed + w, nthreads=1)
     tot_t, tot_f = 0.0, 0
     for s in range(args.steps):
         lo = (s * per_step) % n.size
