@@ -23,9 +23,12 @@
  *    off[q] = n[0] + ... + n[q-1].
  *  - Pointers named *_dev are DEVICE pointers owned by the caller (for
  *    example a torch CUDA tensor's data_ptr()); *_host are host pointers.
- *  - Every call is asynchronous and ordered on the context's CUDA stream, and
- *    returns after enqueueing; only pecc_destroy, pecc_neighbor_count,
- *    pecc_solve_host and pecc_last_error synchronise.
+ *  - Every call is ordered on the context's CUDA stream and returns after
+ *    enqueueing, except those that read something back and so synchronise the
+ *    stream: pecc_set_radius (the radii size the cell grids), pecc_neighbor_count,
+ *    pecc_export_neighbors, pecc_autotune, pecc_phase_times, pecc_solve_host,
+ *    pecc_destroy; pecc_sed_create, pecc_sed_set_radius, pecc_sed_iterate (every
+ *    check_every iterations), pecc_sed_destroy, pecc_frame_run, pecc_mlp_destroy.
  *  - Argument errors are returned synchronously.  Errors found on the device
  *    (non-finite coordinates, a neighbor list over capacity, a time budget
  *    exceeded) are written to the per-instance status outputs of the call
@@ -146,7 +149,8 @@ pecc_status pecc_create(const pecc_config *cfg, void *stream, pecc_ctx **out);
 /* Synchronise the stream and free the context and its device memory. */
 pecc_status pecc_destroy(pecc_ctx *ctx);
 
-/* Container radii: R_dev = device double[num_instances], each R > 0 (read on the stream). */
+/* Container radii: R_dev = device double[num_instances], each R finite and > 0.  Synchronises:
+ * the radii are read back to size each instance's cell grid (PECC_ERR_ARG for a bad radius). */
 pecc_status pecc_set_radius(pecc_ctx *ctx, const double *R_dev);
 
 /* Coordinates: xy_dev = device double[2 * sum n].  FP32 contexts round them to binary32. */
@@ -167,12 +171,14 @@ pecc_status pecc_get_positions(pecc_ctx *ctx, double *xy_dev);
  * receives 1 where a list was rebuilt. */
 pecc_status pecc_rebuild_neighbors(pecc_ctx *ctx, int32_t force, int32_t *rebuilt_dev);
 
-/* Number of stored neighbor entries (sum over instances of sum_i |Gamma(i)|); synchronises. */
+/* Number of stored neighbor entries (sum over instances of sum_i |Gamma(i)|); synchronises.
+ * PECC_ERR_NBR_OVERFLOW when an instance's last build exceeded its capacity (nbr_capacity). */
 pecc_status pecc_neighbor_count(pecc_ctx *ctx, int64_t *nnz_host);
 
 /* Export the neighbor lists as one CSR over all circles: row_ptr_dev = device
  * int32[sum n + 1], col_dev = device int32[cap] of global circle indices, each row
- * ascending.  PECC_ERR_ARG if cap is below the count of pecc_neighbor_count. */
+ * ascending.  PECC_ERR_ARG if cap is below the count of pecc_neighbor_count, and its
+ * PECC_ERR_NBR_OVERFLOW after an overflowed build.  Synchronises. */
 pecc_status pecc_export_neighbors(pecc_ctx *ctx, int32_t *row_ptr_dev, int32_t *col_dev, int64_t cap);
 
 /* Export the cell binning of the last build: key_dev = device uint32[sum n] (cell index
