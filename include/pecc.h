@@ -223,7 +223,9 @@ pecc_status pecc_get_energy(pecc_ctx *ctx, double *E_dev);
 /* Feasibility (Eq. 1, Eq. 2): largest pair overlap depth over ALL pairs (a fresh FP64 cell
  * list with cutoff l_cut > 2 holds every overlapping pair) and largest container overlap
  * depth, in FP64 with correctly rounded operations; feasible_dev (device uint8[num]) is 1
- * where the larger of the two is <= tol, max_overlap_dev (device double[num]) receives it. */
+ * where the larger of the two is <= tol, max_overlap_dev (device double[num]) receives it.
+ * An instance that cannot be checked (a non-finite coordinate, or more list entries than twice
+ * its capacity) gets max_overlap NaN and feasible 0. */
 pecc_status pecc_check_feasible(pecc_ctx *ctx, double tol, uint8_t *feasible_dev, double *max_overlap_dev);
 
 /* The whole path from host memory: copy R_host (double[num]) to the device, draw the
