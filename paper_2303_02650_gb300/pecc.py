@@ -247,6 +247,11 @@ class Context:
     """One pecc_ctx: independent instances of sizes n[], container radii, positions.
 
     Device arguments are torch CUDA tensors; host arguments of solve_host are numpy arrays.
+    The calls are enqueued on the context's stream, while the tensors the methods allocate (their
+    outputs, and device copies of host inputs) come from torch's caching allocator on the stream
+    current at the call.  With the default (the current stream at creation) the two are the same
+    and memory reuse is stream-ordered.  A caller that passes another stream makes its calls under
+    `torch.cuda.stream(ctx.stream)`, or keeps those tensors alive until that stream has run.
     """
 
     def __init__(self, n, stream=None, **cfg):
