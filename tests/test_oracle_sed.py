@@ -160,3 +160,18 @@ def test_framework_improves_a_dense_instance(orc):
     assert tr[0] > Rb and R < Rb
     assert R == tr[-1]
     assert orc.max_overlap(x, R)[0] <= 1e-9
+
+
+@pytest.mark.parametrize("Rb", [1.0, 1.5, 3.0])
+def test_framework_one_circle_reaches_the_unit_radius(orc, Rb):
+    """One circle packs exactly into R = 1 (its centre at the origin). From any R_b >= 1 the
+    adjustments take the record there, within the schedule's last lambda, feasibly."""
+    x, R, tr = orc.frame(1, Rb, 3, outer=2, s_iter=3)
+    assert abs(R - 1.0) <= 1e-9
+    assert orc.max_overlap(x, R)[0] <= 1e-9
+    assert np.all(np.diff(tr) <= 0.0)
+
+
+def test_framework_empty_instance_keeps_its_radius(orc):
+    x, R, tr = orc.frame(0, 2.0, 3, outer=1, s_iter=2)
+    assert x.shape == (0, 2) and R == 2.0 and np.all(tr == 2.0)
