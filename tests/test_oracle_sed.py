@@ -105,6 +105,16 @@ def test_reaches_zero_energy_at_the_exact_radius_of_seven(orc):
         assert orc.max_overlap(r.x, 3.0)[0] <= 1e-9
 
 
+@pytest.mark.parametrize("n,R", [(1, 1.0), (2, 2.0), (3, 1.0 + 2.0 / np.sqrt(3.0))])
+def test_reaches_zero_energy_at_the_smallest_exact_radii(orc, n, R):
+    """One circle at R = 1, two at R = 2 and three at R = 1 + 2/sqrt(3) pack exactly: the search
+    ends converged (E(x*) <= e_feas = 1e-25) with a feasible layout."""
+    for seed in range(1, 4):
+        r = orc.sed(n, R, seed, s_iter=20)
+        assert r.status == "converged" and r.E <= 1e-25, (seed, r.E)
+        assert orc.max_overlap(r.x, R)[0] <= 1e-9
+
+
 def test_trace_invariants_on_a_dense_instance(orc):
     n, R = 30, np.sqrt(30 / 0.80)
     r = orc.sed(n, R, 2, s_iter=10)
