@@ -233,8 +233,9 @@ def test_descent_one_batch_is_plain_quasi_newton(orc):
 
 
 def test_anm_deferral_doubles_on_stable_layout(orc):
-    """Algorithm ANM on a layout that no longer changes: builds after sweeps 1, 2, 4, 8, ...
-    (cnt reaches len = 1, 2, 4, ... with Gamma' == Gamma each time)."""
+    """Algorithm ANM on a layout that no longer changes: builds after sweeps 1, 3, 7, 15, ...
+    (cnt counts from 0 after each build and reaches len = 1, 2, 4, 8, ... with Gamma' == Gamma
+    each time)."""
     xy = synth.hex_patch(4, 2.2)  # no overlaps: zero gradient, nothing moves
     R = 100.0
     r = orc.gbo(xy, R, max_iter=40, e_tol=-1.0, gsum_tol=-1.0)
@@ -264,3 +265,72 @@ def test_solve_batch_threads_deterministic(orc):
     t2, b = orc.solve_batch(n, R, seed=5, nthreads=3, max_iter=200)
     np.testing.assert_array_equal(a["xy"], b["xy"])
     np.testing.assert_array_equal(a["iters"], b["iters"])
+
+
+def _armijo_layout(eps):
+    """Two circles on the x axis, 1.5 apart (pair depth d = 1/2): M at (1, 0) is batch 0 of the
+    sector partition (pseudo-angle 0), F at (-1/2, 0) batch 1 (pseudo-angle 2).  M's gradient is
+    (-2d, 0) = (-1, 0); with an empty memory its direction is -g, g'd = -1, and with step_max = 2
+    the first trial is alpha = 1.  That trial puts M at (2, 0): the pair no longer overlaps and M
+    presses into the wall by w = sqrt(1 - eps) / 2, so E(alpha = 1) = (1 - eps) / 4 against
+    E0 = 1 / 4.  The halved trial (M at (1.5, 0), 2 from F, w - 1/2 < 0 from the wall) has E = 0."""
+    w = 0.5 * math.sqrt(1.0 - eps)
+    return np.array([[1.0, 0.0], [-0.5, 0.0]]), 3.0 - w
+
+
+ARMIJO_KW = dict(k=2, step_max=2.0, max_iter=1, m=5)
+
+
+@pytest.mark.parametrize("eps,c1,trials,xm", [
+    (3.9e-4, 1e-4, 2, 1.5),  # E(1) - E0 = -eps / 4 above c1 alpha g'd = -1e-4: rejected, alpha halves
+    (4.1e-4, 1e-4, 1, 2.0),  # -eps / 4 below -1e-4: accepted at once
+    (3.9e-4, 0.0, 1, 2.0),   # without the c1 term any decrease is accepted
+    (3.9e-4, 1e-5, 1, 2.0),  # a c1 ten times smaller accepts the same trial
+])
+def test_armijo_acceptance_by_hand(orc, eps, c1, trials, xm):
+    """Eq. 9's line search read as Armijo backtracking (accept E(x + alpha d) <= E(x) + c1 alpha
+    g'd, else halve alpha): on the layout above, alpha = 1 is accepted exactly when eps / 4 >=
+    c1, so the threshold sits at eps = 4 c1 = 4e-4.  The trial count and M's final position follow
+    by hand; a wrong c1, a missing c1 term, a sign error in it or another backtracking factor
+    (0.3 would stop at M = (1.3, 0), pair depth 0.2) each fail one of the cases."""
+    xy, R = _armijo_layout(eps)
+    r = orc.gbo(xy, R, c1=c1, **ARMIJO_KW)
+    assert r.trials == trials
+    assert r.x[0].tolist() == [xm, 0.0] and r.x[1].tolist() == [-0.5, 0.0]
+    if trials == 2:
+        assert r.E == 0.0 and r.status == "converged"
+    else:
+        assert r.E == pytest.approx((1.0 - eps) / 4.0, rel=1e-12)
+        assert r.status == "max_iter"
+
+
+def _stationary_layout(delta, h):
+    """Two circles at (+-t, 0) in a container of radius R = 2 - delta.  The symmetric stationary
+    point is t = 1 - delta / 3 (pair depth 2 - 2t and wall depth t + 1 - R both 2 delta / 3, E =
+    4 delta^2 / 3); circle 1's gradient is (6 (t - 1) + 2 delta, 0), so at t + h each circle's
+    gradient has norm 6 h and the batch's (k = 1 below 300 circles) 6 sqrt(2) h."""
+    t = 1.0 - delta / 3.0
+    return np.array([[t + h, 0.0], [-(t + h), 0.0]]), 2.0 - delta
+
+
+def test_stationary_stop_by_hand(orc):
+    """Algorithm GBO stops when the sum over batches of |g_p|_2 (the gradients taken before each
+    batch's step) is at most gsum_tol.  At 6 sqrt(2) h = 8.49e-10 (h = 1e-10) a tolerance of 1e-9
+    ends the run after sweep 1 with status stationary and that sum reported; 8e-10 lets the run
+    continue past sweep 1.  At the stationary point itself (h = 0) the sum is 0: the rule fires
+    for any tolerance >= 0, and with the rule off (gsum_tol = -1) the run instead ends because no
+    batch moved."""
+    delta = 3e-3
+    xy, R = _stationary_layout(delta, 1e-10)
+    r = orc.gbo(xy, R, max_iter=5, gsum_tol=1e-9)
+    assert r.status == "stationary" and r.iters == 1
+    assert r.gsum == pytest.approx(6.0 * math.sqrt(2.0) * 1e-10, rel=1e-5)
+    assert r.E == pytest.approx(4.0 * delta ** 2 / 3.0, rel=1e-9)
+    r = orc.gbo(xy, R, max_iter=5, gsum_tol=8e-10)
+    assert r.iters >= 2
+    xy, R = _stationary_layout(delta, 0.0)
+    r = orc.gbo(xy, R, max_iter=5, gsum_tol=0.0)
+    assert r.status == "stationary" and r.iters == 1 and r.gsum == 0.0
+    assert np.array_equal(r.x, xy)
+    r = orc.gbo(xy, R, max_iter=5, gsum_tol=-1.0)
+    assert r.status == "stalled" and r.iters == 1
