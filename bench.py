@@ -83,6 +83,83 @@ def cfg_fields(cfg):
     return out
 
 
+def oracle_settings(args):
+    """The descent settings of the workload that the FP64 oracle also has (k, m, step cap), so that
+    the CPU baseline and the reference arm run the same algorithm as the GPU arm."""
+    f = cfg_fields(args.cfg)
+    kw = {"k": args.k if args.k and args.k > 0 else 0}
+    if "lbfgs_m" in f:
+        kw["m"] = int(f["lbfgs_m"])
+    if "step_max" in f:
+        kw["step_max"] = float(f["step_max"])
+    return kw
+
+
+def plain_fp64_leg(args, n, R, seed0, steps=2):
+    """The metric's comparison: the same instances and seeds through the plain FP64 GPU form (the
+    c3-fp64 workload's settings), after one untimed step (graph capture and first use)."""
+    import torch
+
+    from paper_2303_02650_gb300 import pecc
+
+    cfg = cfg_fields(CFG_DEFAULT["c3-fp64"])
+    ctx = pecc.Context(n, precision=pecc.FP64, k_batches=K_DEFAULT["c3-fp64"], **cfg)
+    ctx.set_radius(R)
+    ctx.init_random(seed0 + 20_000)
+    ctx.descend()
+    ctx.check_feasible(1e-9)
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    fs = torch.zeros((), dtype=torch.int64, device="cuda")
+    a.record()
+    for s in range(steps):
+        ctx.init_random(seed0 + s)
+        ctx.descend()
+        f, _ = ctx.check_feasible(1e-9)
+        fs += f.to(torch.int64).sum()
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    feas = int(fs.item())
+    ctx.close()
+    return {"value": round(feas / (ms / 1e3), 3), "unit": UNIT, "steps": steps, "ms_per_step": round(ms / steps, 3),
+            "success_rate": round(feas / (steps * n.size), 4), "seeds": "the timed steps' first seeds",
+            "settings": dict(cfg, k_batches=K_DEFAULT["c3-fp64"])}
+
+
+def error_vs_oracle(ctx, n, R, count=64):
+    """The error of the GPU's results against the FP64 oracle, per result, on the first `count`
+    instances of the last timed step: the energy the GPU reports against the oracle's energy of
+    the GPU's own final layout (all pairs, Neumaier sums), and the GPU's largest overlap depth
+    against the oracle's brute force (bit equality) with the feasibility decision it implies."""
+    import oracle
+
+    count = min(count, n.size)
+    xy = ctx.get_positions().cpu().numpy()
+    E = ctx.get_energy().cpu().numpy()
+    pol = ctx.get_stats().cpu().numpy()[:, 7]
+    feas, mo = [t.cpu().numpy() for t in ctx.check_feasible(1e-9)]
+    off = np.concatenate([[0], np.cumsum(n)])
+    rel, eq, agree, kind = [], 0, 0, []
+    for q in range(count):
+        x = xy[off[q]:off[q + 1]]
+        e_ref = oracle.energy_allpairs(x, float(R[q]))
+        m_ref = oracle.max_overlap(x, float(R[q]))[0]
+        rel.append(abs(E[q] - e_ref) / e_ref if e_ref > 0 else (0.0 if E[q] == 0 else float("inf")))
+        eq += int(mo[q] == m_ref)
+        agree += int(bool(feas[q]) == (m_ref <= 1e-9))
+        kind.append("polished" if pol[q] else "fp32")
+    rel = np.array(rel)
+    polm = np.array([k == "polished" for k in kind])
+    return {"sample": f"first {count} instances of the last timed step, the GPU's final layouts",
+            "energy_rel_err_max_polished": float(rel[polm].max()) if polm.any() else None,
+            "energy_rel_err_max_fp32": float(rel[~polm].max()) if (~polm).any() else None,
+            "max_overlap_bit_equal": f"{eq}/{count}", "feasible_decision_agrees": f"{agree}/{count}",
+            "per_result_energy_rel_err": [float(f"{v:.2g}") for v in rel],
+            "per_result_form": ["p" if k == "polished" else "f" for k in kind]}
+
+
 def workload(name: str):
     if name in ("c3", "c3-fp64"):
         n, R = synth.batch_manifest(4096, seed=2303)
@@ -218,16 +295,25 @@ def fused_traffic(alg_bytes):
     return float(alg_bytes * FUSED_TRAFFIC["dram_per_algorithmic_byte"])
 
 
+def pass_bytes(vec_bytes=8, pos_bytes=8):
+    """One fused energy + gradient pass per circle: read x pos_bytes, row pointer 4 B, about 6
+    neighbor indices 24 B, write g vec_bytes (44 B in FP32)."""
+    return pos_bytes + 4 + 24 + vec_bytes
+
+
+def per_sweep_bytes(m, vec_bytes=8, pos_bytes=8):
+    """Per circle and sweep: the fused pass, the two-loop recursion over the m stored pairs (read
+    4 m vectors of vec_bytes) and the new pair (write s, y: 2 vec_bytes).  220 B in FP32 at m = 5."""
+    return pass_bytes(vec_bytes, pos_bytes) + 4 * m * vec_bytes + 2 * vec_bytes
+
+
 def algorithmic_bytes_descent(n, k, iters, trials, m, vec_bytes=8, pos_bytes=8):
-    """Algorithmic DRAM bytes of a descent phase (per launch).
-    Per circle and sweep: one fused energy + gradient pass (read x pos_bytes, row pointer 4 B, about
-    6 neighbor indices 24 B, write g vec_bytes: 44 B in FP32), the quasi-Newton direction over the
-    m stored pairs (read 4 m vectors of vec_bytes), the new pair (write s, y: 2 vec_bytes).  Per
-    line-search trial: one fused pass over the batch's n/k circles."""
+    """Algorithmic DRAM bytes of a descent phase (per launch): per_sweep_bytes per circle and
+    sweep with the context's own memory m, plus one fused pass over the batch's n/k circles per
+    line-search trial."""
     n = n.astype(np.float64)
-    pass_b = pos_bytes + 4 + 24 + vec_bytes
-    per_sweep = pass_b + 4 * m * vec_bytes + 2 * vec_bytes
-    return float(np.sum(n * iters * per_sweep) + np.sum(n / k * trials * pass_b))
+    return float(np.sum(n * iters * per_sweep_bytes(m, vec_bytes, pos_bytes)) +
+                 np.sum(n / k * trials * pass_bytes(vec_bytes, pos_bytes)))
 
 
 # one resident wave of the adjustment's instance blocks on 152 SMs (two 256-thread blocks per SM):
@@ -532,8 +618,9 @@ def run_ksweep(args, rank, world, local):
                         b_ = float(I) * float(st[:, 0].mean()) * 5 * 4 * (2 * nb) ** 2 * 8
                     else:
                         kv = np.full(I, 5.0)
-                        b_ = algorithmic_bytes_descent(n, kv, st[:, 8], st[:, 9], 10, 8, 8)
-                        b_ += algorithmic_bytes_descent(n, np.ones(I), st[:, 0] - st[:, 8], st[:, 4] - st[:, 9], 10, 8,
+                        m_ = int(ctx.cfg.lbfgs_m)
+                        b_ = algorithmic_bytes_descent(n, kv, st[:, 8], st[:, 9], m_, 8, 8)
+                        b_ += algorithmic_bytes_descent(n, np.ones(I), st[:, 0] - st[:, 8], st[:, 4] - st[:, 9], m_, 8,
                                                         16)
                     dom = (t, b_)
                 ctx.close()
@@ -694,9 +781,9 @@ def run_sed(args, rank, world, local):
             act = (np.arange(M)[None, :] < m[:, None]).ravel()
             if not act.any():
                 continue
-            b = algorithmic_bytes_descent(slot_n[act], slot_k[act], st[act, 8], st[act, 9], 10, 8, 8)
+            b = algorithmic_bytes_descent(slot_n[act], slot_k[act], st[act, 8], st[act, 9], dcfg["lbfgs_m"], 8, 8)
             b += algorithmic_bytes_descent(slot_n[act], np.ones(int(act.sum())), st[act, 0] - st[act, 8],
-                                           st[act, 4] - st[act, 9], 10, 8, 16)
+                                           st[act, 4] - st[act, 9], dcfg["lbfgs_m"], 8, 16)
             desc_ms.append(ev[2 * t].elapsed_time(ev[2 * t + 1]))
             desc_bytes.append(b)
             cands.append(int(act.sum()))
@@ -978,6 +1065,7 @@ def run_ours(args, rank, world, local):
     shape.update(cfg_fields(args.cfg))  # further pecc_config fields, e.g. step_max=0.2
     ctx = pecc.Context(n, precision=prec, **shape)
     ctx.set_radius(R)
+    m_ctx = int(ctx.cfg.lbfgs_m)  # the byte model charges the memory the context runs with
     tuned = None
     if not args.no_autotune and not args.launch and n.size > 1:
         tuned = ctx.autotune(sweeps=40, seed=args.seed + 31337)  # launch shape (untimed, before warm-up)
@@ -1024,9 +1112,11 @@ def run_ours(args, rank, world, local):
             return
         phase_ms.append(ms[0])
         phase2_ms.append(ms[1])
-        b = algorithmic_bytes_descent(n, kvec, st[:, 8], st[:, 9], 10, 16 if prec == 0 else 8, 16 if prec == 0 else 8)
+        b = algorithmic_bytes_descent(n, kvec, st[:, 8], st[:, 9], m_ctx, 16 if prec == 0 else 8,
+                                      16 if prec == 0 else 8)
         if fused:  # the polish runs in the same kernel: one batch, binary64 coordinates
-            b += algorithmic_bytes_descent(n, np.ones_like(kvec), st[:, 0] - st[:, 8], st[:, 4] - st[:, 9], 10, 8, 16)
+            b += algorithmic_bytes_descent(n, np.ones_like(kvec), st[:, 0] - st[:, 8], st[:, 4] - st[:, 9], m_ctx, 8,
+                                           16)
         phase_bytes.append(b)
         it_all.append(st[:, 0])
         st_all.append(st[:, 1])
@@ -1066,6 +1156,9 @@ def run_ours(args, rank, world, local):
     value = feasible / (ms_total / 1e3)
     solved = sum(int(n.size) for _ in range(args.steps)) * world
 
+    # the last timed step's results against the oracle (per result), before anything moves them
+    err_orc = error_vs_oracle(ctx, n, R) if rank == 0 and not big else None
+
     # neighbor-pair gradient evaluations per second inside the descent (first phase)
     # and the standalone fused energy + gradient kernel against the HBM roofline
     eg = energy_grad_roofline(ctx, torch, n)
@@ -1089,6 +1182,16 @@ def run_ours(args, rank, world, local):
         e2e_ms += (time.perf_counter() - t0) * 1e3
         e2e_feas += int(out["feasible"].sum())
 
+    # the plain FP64 GPU form on the same instances and seeds (the metric's "vs plain FP64")
+    plain = None
+    if args.workload == "c3" and not args.no_plain:
+        plain = plain_fp64_leg(args, n, R, seed0)
+        if dist:
+            pms, pf = combine_ranks(dist, plain["ms_per_step"] * plain["steps"],
+                                    int(round(plain["value"] * plain["ms_per_step"] * plain["steps"] / 1e3)), "cuda")
+            plain["value"] = round(pf / (pms / 1e3), 3)
+        plain["ratio"] = round(value / plain["value"], 3) if plain["value"] > 0 else None
+
     hbm, peak_kind = peaks()
     dom_ms = float(np.mean(phase_ms))
     dom_bytes = float(np.mean(phase_bytes))
@@ -1099,10 +1202,14 @@ def run_ours(args, rank, world, local):
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_total / args.steps, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if prec == 0 else "f32+f64",
+        "dtype": "f64" if prec == 0 else ("f32" if prec == 1 else "f32 bulk; polish f64 coords + f32 depths; f64 check"),
         "data": "synthetic (Philox-drawn layouts; instance manifest from a seeded generator)",
         "config": {"workload": f"{args.workload}: {desc}",
-                   "precision": "plain FP64" if prec == 0 else "FP32 bulk + FP64 polish",
+                   "precision": "plain FP64" if prec == 0 else (
+                       "FP32" if prec == 1 else
+                       "FP32 bulk descent, then a polish descent with binary64 coordinates, pair differences, "
+                       "4 - l^2 and energy sums but binary32 depths, gradients and quasi-Newton vectors; "
+                       "binary64 feasibility check"),
                    "instances_per_step": int(n.size), "circles_per_step": int(n.sum()),
                    "l_cut": ctx.cfg.l_cut, "rebuild_disp": ctx.cfg.rebuild_disp, "lbfgs_m": ctx.cfg.lbfgs_m,
                    "max_iter": ctx.cfg.max_iter, "step_max": ctx.cfg.step_max,
@@ -1134,6 +1241,8 @@ def run_ours(args, rank, world, local):
                      "algorithmic_bytes_per_launch": dom_bytes,
                      "polish_kernel_ms": round(float(np.mean(phase2_ms)), 3)},
         "energy_grad_roofline": eg,
+        "plain_fp64": plain,
+        "error_vs_oracle": err_orc,
         "e2e": {"value": round(e2e_feas / (e2e_ms / 1e3), 3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": (4 if prec == 0 else 5) * args.steps + (2 if prec == 2 else 1) * args.steps * int(big),
@@ -1202,19 +1311,20 @@ def cpu_baseline(args, n, R, prec, budget_s=15.0):
     cores = os.cpu_count() or 1
     rng_order = np.arange(n.size)
     # time one instance first, then size the sample to about budget_s of wall time
-    t1, _ = oracle.solve_batch(n[:1], R[:1], args.seed, nthreads=1)
+    kw = oracle_settings(args)
+    t1, _ = oracle.solve_batch(n[:1], R[:1], args.seed, nthreads=1, **kw)
     per = max(t1, 1e-3)
     count = int(max(1, min(n.size, budget_s * cores / per)))
     if n.size == 1:
         count = max(1, min(int(budget_s / per), 64))
         nn = np.repeat(n, count)
         RR = np.repeat(R, count)
-        t, out = oracle.solve_batch(nn, RR, args.seed, nthreads=cores)
-        sample = f"{count} runs of the single instance (different seeds), {cores} threads"
+        t, out = oracle.solve_batch(nn, RR, args.seed, nthreads=cores, **kw)
+        sample = f"{count} runs of the single instance (different seeds), {cores} threads, settings {kw}"
     else:
         idx = rng_order[:count]
-        t, out = oracle.solve_batch(n[idx], R[idx], args.seed, nthreads=cores)
-        sample = f"first {count} of the {n.size} instances, {cores} threads"
+        t, out = oracle.solve_batch(n[idx], R[idx], args.seed, nthreads=cores, **kw)
+        sample = f"first {count} of the {n.size} instances, {cores} threads (dynamic queue), settings {kw}"
     feas = int(out["feasible"].sum())
     return {"value": round(feas / t, 3), "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
             "seconds": round(t, 2), "success_rate": round(feas / len(out["feasible"]), 4),
@@ -1243,7 +1353,10 @@ def run_reference(args, rank, world):
     else:
         n, R, prec, desc = workload(args.workload)
     cores = os.cpu_count() or 1
-    per_step = max(1, min(n.size, 2 * cores))
+    # eight instances per thread and step: the threads take instances from one queue, so the
+    # ragged sizes balance out (with two per thread most threads idled behind the largest)
+    per_step = max(1, min(n.size, 8 * cores))
+    kw = oracle_settings(args) if args.workload != "c5" else {}
     # warm-up: the library and the thread pool, on the smallest instance of the workload, or on 50
     # circles where that is larger than 1000 (one 100000-circle descent takes minutes)
     w0 = int(np.argmin(n))
@@ -1254,11 +1367,11 @@ def run_reference(args, rank, world):
     for s in range(args.steps):
         lo = (s * per_step) % n.size
         idx = np.arange(lo, lo + per_step) % n.size
-        t, out = oracle.solve_batch(n[idx], R[idx], args.seed + s, inst_base=int(lo), nthreads=cores)
+        t, out = oracle.solve_batch(n[idx], R[idx], args.seed + s, inst_base=int(lo), nthreads=cores, **kw)
         tot_t += t
         tot_f += int(out["feasible"].sum())
     value = tot_f / tot_t
-    sample = f"{per_step} instances per step of the workload, {cores} threads"
+    sample = f"{per_step} instances per step of the workload, {cores} threads (dynamic queue), settings {kw}"
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(tot_t * 1e3 / args.steps, 3),
@@ -1445,6 +1558,7 @@ def main():
     ap.add_argument("--workload", default="c3", choices=["c3", "c3-fp64", "c2", "c2-fp64", "c1", "c4", "c5", "adjust", "sed", "ksweep", "frame"])
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true", help="c3: skip the plain FP64 leg")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shape")
     ap.add_argument("--fuse", type=int, default=-1, choices=[-1, 0, 1],
                     help="FP32 descent and polish in one kernel (1) or two (0); -1 = the library default")

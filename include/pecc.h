@@ -141,16 +141,23 @@ typedef struct {
 /* Fill *cfg with the defaults listed above (num_instances = 0, n = NULL). */
 void pecc_config_default(pecc_config *cfg);
 
-/* Create a context on the current CUDA device.  stream: a cudaStream_t (NULL =
- * the legacy default stream).  Allocates every device buffer the context needs
- * (sized from n[] and the config); *out receives the context or NULL. */
+/* Create a context on the current CUDA device for num_instances independent problems of the kind
+ * Sec. 3.1 states: instance q places n[q] unit circles in a container of radius R[q] so that no
+ * two overlap (Eq. 1) and none leaves the container (Eq. 2).  The radii come later
+ * (pecc_set_radius).  stream: a cudaStream_t (NULL = the legacy default stream).  Allocates every
+ * device buffer the context needs (sized from n[] and the config); *out receives the context or
+ * NULL.  Synchronous (device allocations and uploads). */
 pecc_status pecc_create(const pecc_config *cfg, void *stream, pecc_ctx **out);
 
 /* Synchronise the stream and free the context and its device memory. */
 pecc_status pecc_destroy(pecc_ctx *ctx);
 
-/* Container radii: R_dev = device double[num_instances], each R finite and > 0.  Synchronises:
- * the radii are read back to size each instance's cell grid (PECC_ERR_ARG for a bad radius). */
+/* Container radii R of the problem statement (Sec. 3.1; the container constraint of Eq. 2 and the
+ * wall depth of Eq. 3 use them): R_dev = device double[num_instances], each R finite and > 0.
+ * Synchronises, unlike the stream-ordered calls of the descent: the radii are read back to the
+ * host, where they size each instance's cell grid (cells per side, which bound the shared-memory
+ * plan of the descent kernels and the cell-table allocation) and are checked (PECC_ERR_ARG for a
+ * bad radius).  Call it once per set of radii, before the descents. */
 pecc_status pecc_set_radius(pecc_ctx *ctx, const double *R_dev);
 
 /* Coordinates: xy_dev = device double[2 * sum n].  FP32 contexts round them to binary32. */
@@ -216,6 +223,21 @@ pecc_status pecc_rebuild_neighbors_ex(pecc_ctx *ctx, int32_t eval, int32_t force
  * iters_dev (device int32[num_instances], may be NULL): sweeps done (both phases);
  * status_dev (device int32[num_instances], may be NULL): PECC_DESC_* of the last phase. */
 pecc_status pecc_descend(pecc_ctx *ctx, int32_t *iters_dev, int32_t *status_dev);
+
+/* Parity hook for tests of the descent's own neighbor lists (Sec. 4.3): every following
+ * pecc_descend writes, for each instance below 16384 circles, the lists in force at the end of its
+ * first phase (the binary32 lists of the FP32 descent of PECC_FP32 and PECC_FP32_POLISH64, the
+ * binary64 lists of PECC_FP64) and the coordinates they were built at.
+ *   stride   entries kept per row, >= 1
+ *   cnt_dev  device int32[sum n]: the row length of circle i (caller's numbering), or -1 when the
+ *            row is longer than stride or the phase ended without a complete build
+ *   col_dev  device int32[sum n * stride]: row i at i * stride, instance-local circle indices, in
+ *            the descent's own order (not sorted)
+ *   xb_dev   device double[2 * sum n]: the coordinates of that build (binary32 values widened in
+ *            the FP32 phase)
+ * cnt_dev = NULL turns the hook off.  The buffers must outlive every descent that writes them.
+ * Changing the hook makes the next pecc_descend capture its graph again.  Asynchronous. */
+pecc_status pecc_set_list_dump(pecc_ctx *ctx, int32_t stride, int32_t *cnt_dev, int32_t *col_dev, double *xb_dev);
 
 /* Per-instance energies after the last pecc_descend: device double[num_instances]. */
 pecc_status pecc_get_energy(pecc_ctx *ctx, double *E_dev);
@@ -327,7 +349,7 @@ pecc_status pecc_warm_start(pecc_ctx *ctx, pecc_mlp *mlp, int32_t rounds, int32_
 /* The feasibility check of pecc_check_feasible for ONE instance, without any device allocation.
  * The paper has no counterpart: this is a service for callers that cannot call cudaMalloc
  * (code running while its stream is captured into a CUDA graph, plug-ins whose host owns all
- * device memory, real-time loops).  Its scratch (about 0.6 MB) is a fixed array in device
+ * device memory, real-time loops).  Its scratch (about 0.85 MB) is a fixed array in device
  * memory that every GPU loading the library holds until the process exits.
  *   xy_dev          device double[2 n], interleaved (x, y)
  *   n               0 .. PECC_NOALLOC_MAX_N circles, else PECC_ERR_ARG (nothing launched)
@@ -336,11 +358,15 @@ pecc_status pecc_warm_start(pecc_ctx *ctx, pecc_mlp *mlp, int32_t rounds, int32_
  *   feasible_dev    device uint8[1];  max_overlap_dev  device double[1] (NaN if not checkable)
  *   stream          cudaStream_t the kernel is enqueued on (NULL = legacy default stream)
  * The first call on a device takes the array's device address (cudaGetSymbolAddress, with that
- * device current); make that first call before any stream capture.  Every call shares the one
- * array and finds the previous call's contents there (the kernel clears what must start at
- * zero); calls whose kernels overlap on the GPU race on it, so order them on one stream.  Errors
- * are returned synchronously; the message is in pecc_last_error(NULL).  Results are identical
- * to pecc_check_feasible's for the same coordinates. */
+ * device current) and keeps it for the life of the process; make that first call before any
+ * stream capture.  A cudaDeviceReset (or a lost context) on that device leaves the kept address
+ * stale: make no further call on that device afterwards.  Every call shares the one array and
+ * finds the previous call's contents there (the kernel clears what must start at zero); calls
+ * whose kernels overlap on the GPU race on it, so order them on one stream.  Errors are returned
+ * synchronously; the message is in pecc_last_error(NULL).  The neighbor list holds at most
+ * 2 (16 n + 64) entries, as pecc_check_feasible's in a context with the default nbr_capacity of
+ * 16: with that context the results are identical for the same coordinates, NaN included (an
+ * instance whose list would exceed it gets max_overlap NaN and feasible 0). */
 pecc_status pecc_check_feasible_noalloc(const double *xy_dev, int32_t n, double R, double l_cut, double tol,
                                         uint8_t *feasible_dev, double *max_overlap_dev, void *stream);
 

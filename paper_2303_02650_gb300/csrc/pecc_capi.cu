@@ -64,6 +64,10 @@ struct pecc_ctx {
   float *feat = nullptr, *dout = nullptr;
   float2 *backup = nullptr;
   double *Eb = nullptr, *Ea = nullptr;
+  // parity hook of pecc_set_list_dump (caller's device buffers; nullptr = off)
+  int32_t *dump_cnt = nullptr, *dump_col = nullptr;
+  double *dump_xb = nullptr;
+  int dump_stride = 0;
   std::string err;
 };
 
@@ -650,6 +654,12 @@ static DescendParams dparams(pecc_ctx *c, int phase) {
   p.budget_ns = f.time_budget_ns;
   p.k_override = (phase == 2) ? f.polish_k : 0;
   p.smem_bytes = c->lc[phase].smem;
+  if (phase <= 1 && c->dump_cnt) {  // the first phase only: FP64, or the FP32 descent
+    p.dump_cnt = c->dump_cnt;
+    p.dump_col = c->dump_col;
+    p.dump_xb = (double2 *)c->dump_xb;
+    p.dump_stride = c->dump_stride;
+  }
   return p;
 }
 
@@ -785,6 +795,18 @@ pecc_status pecc_descend(pecc_ctx *ctx, int32_t *iters_dev, int32_t *status_dev)
   ctx->lists_prec = -1;  // the descent reuses the scratch the standalone lists rely on
   if (iters_dev || status_dev)
     CK(launch_outputs(ctx->out, ctx->num, iters_dev, status_dev, nullptr, nullptr, nullptr, nullptr, ctx->stream));
+  return PECC_OK;
+}
+
+pecc_status pecc_set_list_dump(pecc_ctx *ctx, int32_t stride, int32_t *cnt_dev, int32_t *col_dev, double *xb_dev) {
+  if (!ctx) return PECC_ERR_ARG;
+  if (cnt_dev && (stride < 1 || !col_dev || !xb_dev))
+    return fail(ctx, PECC_ERR_ARG, "pecc_set_list_dump: stride must be >= 1 with col_dev and xb_dev set");
+  ctx->dump_cnt = cnt_dev;
+  ctx->dump_col = cnt_dev ? col_dev : nullptr;
+  ctx->dump_xb = cnt_dev ? xb_dev : nullptr;
+  ctx->dump_stride = cnt_dev ? stride : 0;
+  if (ctx->graph) { cudaGraphExecDestroy(ctx->graph); ctx->graph = nullptr; }  // captured again
   return PECC_OK;
 }
 

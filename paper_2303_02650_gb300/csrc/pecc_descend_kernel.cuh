@@ -246,6 +246,7 @@ __device__ __forceinline__ void descend_instance(const DescendParams &P, Smem<A,
   bad = __syncthreads_or(bad);
 
   int status = 3;  // max_iter unless something else ends the run
+  bool lists_ok = false;  // the lists and xb hold a complete build
   int iters = 0, builds = 0, changes = 0, trials = 0, resets = 0, stalls = 0;
   int cnt = 0, len = 1;
   unsigned long long hcur = 0ull;  // digest of the current lists
@@ -268,7 +269,7 @@ __device__ __forceinline__ void descend_instance(const DescendParams &P, Smem<A,
   };
   // ANM step (Algorithm ANM): Gamma' replaces Gamma; equal sets double the deferral length
   auto anm_rebuild = [&]() -> bool {
-    if (!build()) return false;
+    if (!build()) { lists_ok = false; return false; }
     ++builds;
     const unsigned long long h = S.hash;
     if (h != hcur) { hcur = h; len = 1; ++changes; }
@@ -307,6 +308,7 @@ __device__ __forceinline__ void descend_instance(const DescendParams &P, Smem<A,
     if (!build()) status = 4;
     else {
       builds = 1;
+      lists_ok = true;
       for (int p = tid; p < n; p += T) xb[p] = xw[p];  // the cell table of the build used xb
       hcur = S.hash;
       E = full_energy();
@@ -684,6 +686,20 @@ __device__ __forceinline__ void descend_instance(const DescendParams &P, Smem<A,
   }
 
   if (status < 4 && e_at != iters) E = full_energy();  // the final energy of the run
+  // ---- parity hook: the lists in force now, in the caller's numbering, and their build's layout
+  if (P.dump_cnt != nullptr) {
+    const int64_t stride = P.dump_stride;
+    for (int pos = tid; pos < n; pos += T) {
+      const int i = perm[pos];
+      const int b0 = lists_ok ? rp[pos] : 0, len_ = lists_ok ? rp[pos + 1] - b0 : 0;
+      const bool ok = lists_ok && len_ <= P.dump_stride;
+      P.dump_cnt[D.off + i] = ok ? len_ : -1;
+      if (ok)
+        for (int t = 0; t < len_; ++t) P.dump_col[(D.off + i) * stride + t] = perm[col[b0 + t]];
+      const PP v = xb[pos];
+      P.dump_xb[D.off + i] = make_double2((double)v.x, (double)v.y);
+    }
+  }
   // ---- 4. merge: scatter back to the caller's order
   for (int pos = tid; pos < n; pos += T) {
     int i = perm[pos];

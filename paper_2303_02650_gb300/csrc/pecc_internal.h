@@ -61,6 +61,11 @@ struct DescendParams {
   long long budget_ns;    // 0 = no time budget
   int k_override;         // > 0: batches per instance for this phase (capped at the instance's k)
   size_t smem_bytes;      // dynamic shared memory per block for the working set
+  // parity hook (pecc_set_list_dump): the lists in force at the end of each instance's phase and
+  // the coordinates of their build; dump_cnt == nullptr: off
+  int32_t *dump_cnt, *dump_col;
+  double2 *dump_xb;
+  int dump_stride;
 };
 
 cudaError_t launch_stamp(long long *t0, cudaStream_t s);

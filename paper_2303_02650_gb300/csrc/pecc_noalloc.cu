@@ -17,7 +17,10 @@ namespace {
 
 constexpr int kMaxN = PECC_NOALLOC_MAX_N;
 constexpr int kMaxNc = 128;                      // max(16, ceil(2 sqrt(kMaxN)))
-constexpr int kCap = 16 * kMaxN + 64;            // neighbor entries
+// Neighbor entries: the list capacity pecc_check_feasible builds with in a context created with the
+// default nbr_capacity of 16 per circle, 2 (16 n + 64), taken per call and sized here for kMaxN.
+__host__ __device__ constexpr int call_cap(int n) { return 2 * (16 * n + 64); }
+constexpr int kCap = call_cap(kMaxN);
 constexpr size_t kOffX = 0;                                   // double2[kMaxN]
 constexpr size_t kOffXs = kOffX + sizeof(double2) * kMaxN;    // double2[kMaxN]
 constexpr size_t kOffKey = kOffXs + sizeof(double2) * kMaxN;  // uint32[kMaxN]
@@ -30,6 +33,8 @@ constexpr size_t kScratchBytes = kOffCol + 4 * (size_t)kCap;
 // The scratch every call shares; its address is taken per device with cudaGetSymbolAddress.
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
+// The array's device address per device, taken once by the first call on that device.  A
+// cudaDeviceReset (or a lost context) on that device leaves this address stale.
 std::mutex g_mu;
 void *g_ptr[256];
 bool g_ready[256];
@@ -37,6 +42,7 @@ bool g_ready[256];
 __global__ void noalloc_feasible_kernel(unsigned char *scratch, const double *__restrict__ xy, int n, double R,
                                         double inv, int nc, double lc2, double tol, uint8_t *feasible,
                                         double *max_overlap) {
+  const int cap = call_cap(n);
   __shared__ int32_t sh[40];
   __shared__ double red[32];
   double2 *x = (double2 *)(scratch + kOffX);
@@ -48,10 +54,10 @@ __global__ void noalloc_feasible_kernel(unsigned char *scratch, const double *__
   // the build zeroes the cell counters it uses and overwrites everything else it reads
   const int tot = cta_build_neighbors<double, int32_t>(
       x, n, G, lc2, (uint32_t *)(scratch + kOffKey), (int32_t *)(scratch + kOffOrd), (int32_t *)(scratch + kOffCells),
-      (double2 *)(scratch + kOffXs), rp, col, kCap, sh, nullptr, false);
+      (double2 *)(scratch + kOffXs), rp, col, cap, sh, nullptr, false);
   double m = 0.0;
   int bad = 0;
-  if (tot <= kCap) {
+  if (tot <= cap) {
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
       const double2 xi = x[i];
       bad |= !(isfinite(xi.x) && isfinite(xi.y));

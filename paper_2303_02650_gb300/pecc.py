@@ -58,7 +58,7 @@ _EXPORTS = ["pecc_config_default", "pecc_create", "pecc_destroy", "pecc_set_radi
             "pecc_adjust_container", "pecc_sed_config_default", "pecc_sed_create", "pecc_sed_destroy",
             "pecc_sed_last_error", "pecc_sed_set_radius", "pecc_sed_start", "pecc_sed_set_state", "pecc_sed_iterate",
             "pecc_sed_prepare", "pecc_sed_descend", "pecc_sed_select", "pecc_sed_get", "pecc_sed_context",
-            "pecc_frame_run"]
+            "pecc_frame_run", "pecc_set_list_dump"]
 NOALLOC_MAX_N = 4096
 ENERGY_STAGE_BYTES = 96 * 1024  # PECC_ENERGY_STAGE_BYTES
 
@@ -134,6 +134,7 @@ def load(build_if_missing: bool = True):
         "pecc_sed_context": (vp, [vp]),
         "pecc_frame_run": (st, [vp, vp, vp, C.c_uint64, C.c_int32, C.c_int32, C.c_double, C.c_int32, vp, vp, vp,
                                 vp]),
+        "pecc_set_list_dump": (st, [vp, C.c_int32, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -366,6 +367,22 @@ class Context:
         E = torch.empty(self.num, dtype=torch.float64, device=self.dev)
         self._check(self._L.pecc_get_energy(self.h, _ptr(E)), "pecc_get_energy")
         return E
+
+    def set_list_dump(self, stride=32):
+        """pecc_set_list_dump: the following descents write the lists in force at the end of their
+        first phase; returns the device tensors (cnt int32[total], col int32[total, stride], xb
+        float64[total, 2]) they write.  stride=None turns the hook off."""
+        if stride is None:
+            self._check(self._L.pecc_set_list_dump(self.h, 0, None, None, None), "pecc_set_list_dump")
+            self._dump = None
+            return None
+        cnt = torch.full((self.total,), -2, dtype=torch.int32, device=self.dev)
+        col = torch.zeros((self.total, int(stride)), dtype=torch.int32, device=self.dev)
+        xb = torch.zeros((self.total, 2), dtype=torch.float64, device=self.dev)
+        self._check(self._L.pecc_set_list_dump(self.h, int(stride), _ptr(cnt), _ptr(col), _ptr(xb)),
+                    "pecc_set_list_dump")
+        self._dump = (cnt, col, xb)  # kept alive while the hook is set
+        return self._dump
 
     def get_counters(self):
         b = torch.empty(self.num, dtype=torch.int32, device=self.dev)

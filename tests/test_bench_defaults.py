@@ -63,3 +63,31 @@ def test_reference_arm_line(extra):
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["sample"] and cb["value"] == r["value"]
     assert cb["unit"] == r["unit"]
     assert r["e2e"] == {"value": r["value"], "unit": r["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_byte_model_charges_the_configured_memory():
+    """The roofline's byte model charges the two-loop recursion 4 m vectors per circle and sweep with
+    the m the context runs with: 220 B per circle-sweep in FP32 at the batch workloads' m = 5 (380 B
+    at the library's m = 10), and no call of the model passes a fixed m."""
+    import re
+
+    assert bench.per_sweep_bytes(5, 8, 8) == 44 + 4 * 5 * 8 + 16 == 220
+    assert bench.per_sweep_bytes(10, 8, 8) == 380
+    for wl, cfg in bench.CFG_DEFAULT.items():
+        m = bench.cfg_fields(cfg).get("lbfgs_m", 10)
+        assert bench.per_sweep_bytes(m, 8, 8) == 44 + 32 * m + 16, wl
+    src = open(os.path.join(ROOT, "bench.py")).read()
+    calls = re.findall(r"algorithmic_bytes_descent\(([^()]*(?:\([^()]*\)[^()]*)*)\)", src)
+    assert len(calls) >= 6
+    for c in calls:
+        args = [a.strip() for a in c.split(",")]
+        if args[0].startswith("n, k, iters"):  # the definition
+            continue
+        assert not re.fullmatch(r"\d+", args[4]), c  # m is the context's, never a literal
+
+
+def test_oracle_runs_the_workload_settings():
+    """The CPU baseline and the reference arm run the oracle with the GPU arm's k, m and step cap."""
+    assert bench.oracle_settings(_args("c3")) == {"k": 2, "m": 5, "step_max": 0.3}
+    assert bench.oracle_settings(_args("c3", cfg=["lbfgs_m=10"])) == {"k": 2, "m": 10, "step_max": 0.3}
+    assert bench.oracle_settings(_args("c1")) == {"k": 0}

@@ -231,26 +231,71 @@ def test_energy_grad_mixed_polish_arithmetic(orc):
     assert np.all(err <= 1e-6 * _contrib_scale(orc, xy, n, R) + 1e-12)
 
 
+def _mixed_bounds(e_ref, n, R):
+    """Bounds of the polish arithmetic against the oracle at the same binary64 coordinates.  Each
+    depth carries 3e-7 relative from its binary32 part, and an absolute delta from binary64
+    rounding that neither side can avoid: the squared distance (rounded once with FMA on the GPU,
+    twice in the oracle: ulp64(4)) and the oracle's wall depth (|c| + 1) - R (two roundings of
+    size ulp64(R + 1)); delta = 4 ulp64(max(4, R + 1)).  With at most 4 n terms, sum d <=
+    sqrt(4 n E) (Cauchy-Schwarz), so |dE| <= 1e-6 E + 2 delta sqrt(4 n E) + 4 n delta^2; each
+    circle's gradient (at most 7 terms of 2 d) gains at most 16 delta."""
+    delta = 4 * float(np.spacing(max(4.0, R + 1.0)))
+    e_bound = 1e-6 * e_ref + 2 * delta * math.sqrt(4 * n * e_ref) + 4 * n * delta ** 2
+    return e_bound, 16 * delta
+
+
 def test_energy_near_contact_mixed_vs_fp64(orc):
-    """Near contact (overlaps ~1e-9) the mixed arithmetic keeps relative accuracy where plain
-    FP32 cannot resolve the depth at all."""
+    """Near contact the mixed arithmetic keeps relative accuracy: 4 - l^2 (and |c|^2 - (R-1)^2) are
+    formed in binary64, where they cancel exactly (Sterbenz), and only the depths derived from them
+    are binary32, each within about 5 ulp32 = 3e-7 relative (one rounding of 4 - s, the reciprocal
+    square root, l, 2 + l and the division).  A squared depth then carries 6e-7, so E is within
+    1e-6 relative of the oracle's and each circle's gradient within 1e-6 times the sum of its
+    terms' norms; the same coordinates in a binary64 context give 1e-12.
+    Two layouts: (1) a square lattice of 8 x 8 circles at spacing 2 - 2^-20, whose coordinates are
+    binary32 values (so an FP32_POLISH64 context keeps them), E = 2 k (k - 1) 2^-40 by hand; (2) the
+    binary64 layouts the polish itself reached, with contact depths down to 1e-10 and below."""
     torch, pecc = need_gpu()
-    xy = synth.hex_patch(6, 2.0 - 2e-9)
-    n = np.array([xy.shape[0]], dtype=np.int32)
+    k, s_ = 8, 2.0 - 2.0 ** -20
+    g1, g2 = np.meshgrid(np.arange(k), np.arange(k), indexing="ij")
+    lat = np.stack([g1.ravel() * s_, g2.ravel() * s_], axis=1) - (k - 1) * s_ / 2
+    assert np.array_equal(lat.astype(np.float32).astype(np.float64), lat)
+    n = np.array([k * k], dtype=np.int32)
     R = np.array([100.0])
     with _ctx(pecc, n, R, precision=2) as c:
-        c.set_positions(torch.from_numpy(xy))
-        xy64 = c.get_positions().cpu().numpy()  # FP32-rounded coordinates
-    # FP32 rounding of the coordinates changes the overlaps; compare on the rounded layout
+        c.set_positions(torch.from_numpy(lat))
+        c.rebuild_neighbors(eval=2)
+        E, g = [t.cpu().numpy().astype(np.float64) for t in c.energy_grad(eval=2)]
+    assert E[0] == pytest.approx(2 * k * (k - 1) * 2.0 ** -40, rel=1e-6)
+    Er, gr = _oracle_eg(orc, lat, n, R)
+    err = np.linalg.norm(g - gr, axis=1)
+    assert np.all(err <= 1e-6 * _contrib_scale(orc, lat, n, R) + _mixed_bounds(Er[0], int(n[0]), 100.0)[1])
+    # the polish's own binary64 layouts: converged (u = 0.80) and jammed (u = 0.87) instances
+    n = np.array([300, 300, 300, 300, 420, 420], dtype=np.int32)
+    R = np.concatenate([_radii(n[:4], 0.80), _radii(n[4:], 0.87)])
+    with _ctx(pecc, n, R, precision=2, polish_gate=1.0) as c:
+        c.init_random(57)
+        c.descend()
+        pol = c.get_stats().cpu().numpy()[:, 7]
+        xy = c.get_positions().cpu().numpy()
+        c.rebuild_neighbors(eval=2)
+        E, g = [t.cpu().numpy().astype(np.float64) for t in c.energy_grad(eval=2)]
+    assert pol.sum() >= 4
+    Er, gr = _oracle_eg(orc, xy, n, R)
+    assert np.any(Er < 1e-18) and np.any(Er > 1e-10)
+    floors = []
+    for q in range(len(n)):
+        eb, gf = _mixed_bounds(Er[q], int(n[q]), float(R[q]))
+        assert abs(E[q] - Er[q]) <= eb, (q, E[q], Er[q])
+        floors.append(np.full(n[q], gf))
+    err = np.linalg.norm(g - gr, axis=1)
+    assert np.all(err <= 1e-6 * _contrib_scale(orc, xy, n, R) + np.concatenate(floors))
     with _ctx(pecc, n, R, precision=0) as c64:
         c64.set_positions(torch.from_numpy(xy))
         c64.rebuild_neighbors()
-        E64, _ = c64.energy_grad()
-    rp, col = orc.neighbors_brute(xy, 2.5)
-    Eref, _, _ = orc.energy_grad_csr(xy, 100.0, rp, col)
-    assert float(E64.cpu()[0]) == pytest.approx(Eref, rel=1e-9)
-    assert Eref == pytest.approx((9 * 36 + 18) * (2e-9) ** 2, rel=1e-5)
-    del xy64
+        E64, g64 = [t.cpu().numpy() for t in c64.energy_grad()]
+    np.testing.assert_allclose(E64, Er, rtol=1e-12, atol=1e-300)
+    gn = np.linalg.norm(gr, axis=1)
+    assert np.all(np.linalg.norm(g64 - gr, axis=1) <= 1e-12 * np.maximum(gn, 1e-300) + 1e-13)
 
 
 # ------------------------------------------------------------------ feasibility
@@ -354,7 +399,8 @@ def _solve(pecc, torch, n, R, seed, **kw):
         xy = c.get_positions().cpu().numpy()
         E = c.get_energy().cpu().numpy()
         return dict(iters=iters.cpu().numpy(), status=status.cpu().numpy(), feasible=feas.cpu().numpy(),
-                    max_overlap=mo.cpu().numpy(), xy=xy, E=E)
+                    max_overlap=mo.cpu().numpy(), xy=xy, E=E, polished=c.get_stats().cpu().numpy()[:, 7],
+                    precision=c.precision)
 
 
 @pytest.mark.parametrize("prec", [0, 2])
@@ -380,14 +426,27 @@ def test_descend_statistics_vs_oracle(orc, prec):
 
 def _check_outcomes(orc, out, n, R):
     """Per instance: the max overlap equals the oracle's on the GPU's own final layout, the energy
-    the GPU reports is the oracle's energy of that layout (to 1e-2 relative: an instance left
-    unpolished reports its binary32 energy, whose overlap depths 2 - l lose up to about 2^-22 / d
-    of their value to cancellation), and converged means feasible."""
+    the GPU reports is the oracle's energy of that layout, and converged means feasible.  The
+    energy bound follows the arithmetic that produced it:
+    - binary64 (plain FP64 context): 1e-12 relative;
+    - a polished instance reports its energy in the polish arithmetic (binary64 4 - l^2, binary32
+      depths within 3e-7 relative, squared and summed in binary64): 1e-6 relative plus the binary64
+      rounding floor of _mixed_bounds;
+    - an instance left unpolished reports its binary32 energy: each depth 2 - l carries up to
+      4 ulp32(2) absolute, so 1e-5 relative plus 4 ulp32(2) times the sum of 2 d over the pairs,
+      which Cauchy-Schwarz bounds by 2 sqrt(3 n E)."""
+    u2 = float(np.spacing(np.float32(2.0)))
     for q, x in enumerate(split(out["xy"], n)):
         mo = orc.max_overlap(x, float(R[q]))[0]
         assert out["max_overlap"][q] == mo, q
         e_ref = orc.energy_allpairs(x, float(R[q]))
-        assert abs(out["E"][q] - e_ref) <= 1e-2 * e_ref + 1e-18, q
+        if out.get("precision", 2) == 0:
+            bound = 1e-12 * e_ref + 1e-300
+        elif out["polished"][q]:
+            bound = _mixed_bounds(e_ref, int(n[q]), float(R[q]))[0]
+        else:
+            bound = 1e-5 * e_ref + 4 * u2 * 2 * math.sqrt(3 * n[q] * e_ref) + 1e-30
+        assert abs(out["E"][q] - e_ref) <= bound, (q, out["E"][q], e_ref, out["polished"][q])
         if out["status"][q] == 0:
             assert out["E"][q] <= 1e-20 and mo <= 1e-9, q
 
@@ -466,7 +525,8 @@ def test_autotune_restores_coordinates_and_descends(orc):
         assert c.launch_shape()[0] == b
         feas, mo = c.check_feasible()
         out = dict(status=status.cpu().numpy(), feasible=feas.cpu().numpy(), max_overlap=mo.cpu().numpy(),
-                   xy=c.get_positions().cpu().numpy(), E=c.get_energy().cpu().numpy())
+                   xy=c.get_positions().cpu().numpy(), E=c.get_energy().cpu().numpy(),
+                   polished=c.get_stats().cpu().numpy()[:, 7], precision=c.precision)
     _check_outcomes(orc, out, n, R)
     assert out["feasible"].sum() >= len(n) - 6
 

@@ -278,7 +278,8 @@ def _armijo_layout(eps):
     return np.array([[1.0, 0.0], [-0.5, 0.0]]), 3.0 - w
 
 
-ARMIJO_KW = dict(k=2, step_max=2.0, max_iter=1, m=5)
+# a cutoff of 6 (Verlet half-skin 2) lets the step cap of 2 keep alpha = 1 as the first trial
+ARMIJO_KW = dict(k=2, step_max=2.0, l_cut=6.0, rebuild_disp=2.0, max_iter=1, m=5)
 
 
 @pytest.mark.parametrize("eps,c1,trials,xm", [
