@@ -291,7 +291,8 @@ pecc_status pecc_get_launch(pecc_ctx *ctx, int32_t *block_threads, int32_t *bloc
 
 /* ---------------------------------------------------------------------------------------------
  * Learned warm start.  Not in the paper: a per-circle MLP (25 -> 128 -> 128 -> 128 -> 2, ReLU,
- * BF16 weights on the tensor cores, FP32 accumulation and FP32 master weights) maps the local
+ * BF16 weights on the fifth-generation tensor cores (tcgen05.mma, accumulators in TMEM, tiles of
+ * 128 rows), FP32 accumulation and FP32 master weights) maps the local
  * neighborhood of a circle to a displacement; it is trained on displacements the descent itself
  * makes, and the plain descent stays its fallback and the test of its moves (a warm-start move of
  * an instance is kept only if it does not raise that instance's energy).
@@ -326,6 +327,16 @@ pecc_status pecc_mlp_forward(pecc_mlp *mlp, const float *feat_dev, int64_t rows,
 pecc_status pecc_mlp_grad(pecc_mlp *mlp, const float *feat_dev, const float *target_dev, int64_t rows,
                           float *grad_dev, float *loss_dev);
 
+/* The same two calls writing what the tensor cores computed, for tests against a CPU restatement:
+ * forward: trace_dev float[rows][3][128], the bf16 activations of the three hidden layers (as
+ * floats); grad: fwd_trace_dev the same for the forward pass of the gradient, bwd_trace_dev
+ * float[rows][4][128], the bf16 back-propagated dZ3, dZ2, dZ1 (ReLU-masked, as floats), then in the
+ * fourth row the bf16 output gradient dO (2 values) and the outputs (2 values). */
+pecc_status pecc_mlp_forward_trace(pecc_mlp *mlp, const float *feat_dev, int64_t rows, float *out_dev,
+                                   float *trace_dev);
+pecc_status pecc_mlp_grad_trace(pecc_mlp *mlp, const float *feat_dev, const float *target_dev, int64_t rows,
+                                float *grad_dev, float *loss_dev, float *fwd_trace_dev, float *bwd_trace_dev);
+
 /* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on L with learning rate lr. */
 pecc_status pecc_mlp_train_step(pecc_mlp *mlp, const float *feat_dev, const float *target_dev, int64_t rows,
                                 float lr, float *loss_dev);
@@ -342,6 +353,12 @@ pecc_status pecc_targets(pecc_ctx *ctx, const double *xbefore_dev, float *target
  * its neighbor-list energy (Eq. 5) does not rise, else the instance is put back.  accepted_dev
  * (int32[num_instances], may be NULL) is increased by the number of rounds kept. */
 pecc_status pecc_warm_start(pecc_ctx *ctx, pecc_mlp *mlp, int32_t rounds, int32_t *accepted_dev);
+
+/* The same with the largest move of a circle per round as a parameter (max_move > 0; the call
+ * above uses 0.25).  The moves need no bound for the check that follows them (the energy after a
+ * round is evaluated over lists rebuilt at the moved layout); the bound limits the damage of a
+ * poor proposal. */
+pecc_status pecc_warm_start_ex(pecc_ctx *ctx, pecc_mlp *mlp, int32_t rounds, double max_move, int32_t *accepted_dev);
 
 /* Largest instance pecc_check_feasible_noalloc accepts. */
 #define PECC_NOALLOC_MAX_N 4096

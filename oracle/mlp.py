@@ -111,3 +111,37 @@ def loss_grad(params, feat, target, round_bf16=True):
             mask = acts[layer] > 0
             dZ = rnd((dH * mask).astype(np.float32) if round_bf16 else dH * mask)
     return L, pack(g)
+
+
+# ------------------------------------------------------------------ layer-by-layer restatement
+# For element-wise parity of the tensor-core network: each layer recomputed in binary64 from the
+# device's own bf16 inputs of that layer (its traced activations), so that an element can differ
+# from the device's only by the device's binary32 accumulation of that one layer.
+
+def weights_bf16(params):
+    """The bf16 values of W1..W4 (binary64 arrays, [out][in]) and the binary32 biases."""
+    p = unpack(params)
+    return [bf16(p["W1"]), bf16(p["W2"]), bf16(p["W3"]), bf16(p["W4"])], [p["b1"], p["b2"], p["b3"], p["b4"]]
+
+
+def pre_activation(params, layer, h_in):
+    """z = h_in W_layer^T + b_layer in binary64 (layer 0..3; h_in holds bf16 values), and the sum of
+    the magnitudes of its terms |h_in| |W|^T + |b| (the scale of a rounding bound)."""
+    Ws, bs = weights_bf16(params)
+    h = np.asarray(h_in, dtype=np.float64)
+    return h @ Ws[layer].T + bs[layer], np.abs(h) @ np.abs(Ws[layer]).T + np.abs(bs[layer])
+
+
+def output_gradient(out, target, rows):
+    """dO = bf16((out - target) * (2 / rows)), every operation in binary32: the output layer's gradient of the
+    mean squared loss as the device forms it from its binary32 outputs."""
+    d = np.asarray(out, dtype=np.float32) - np.asarray(target, dtype=np.float32)
+    return bf16((d * (np.float32(2.0) / np.float32(rows))).astype(np.float32))
+
+
+def back_pre(params, layer, dz):
+    """dZ_layer W_layer (binary64; dz holds bf16 values) and |dZ| |W| (the scale of its rounding bound):
+    the gradient with respect to the input of layer `layer` before the ReLU mask of that input."""
+    Ws, _ = weights_bf16(params)
+    d = np.asarray(dz, dtype=np.float64)
+    return d @ Ws[layer], np.abs(d) @ np.abs(Ws[layer])

@@ -1054,6 +1054,23 @@ pecc_status pecc_mlp_grad(pecc_mlp *mlp, const float *feat_dev, const float *tar
   return PECC_OK;
 }
 
+pecc_status pecc_mlp_forward_trace(pecc_mlp *mlp, const float *feat_dev, int64_t rows, float *out_dev,
+                                   float *trace_dev) {
+  if (!mlp || rows < 0 || (rows > 0 && (!feat_dev || !out_dev || !trace_dev)))
+    return mfail(mlp, PECC_ERR_ARG, "bad arguments");
+  MCK(mlp_forward(mlp->wb, mlp->params, feat_dev, rows, out_dev, mlp->sms, mlp->stream, trace_dev));
+  return PECC_OK;
+}
+
+pecc_status pecc_mlp_grad_trace(pecc_mlp *mlp, const float *feat_dev, const float *target_dev, int64_t rows,
+                                float *grad_dev, float *loss_dev, float *fwd_trace_dev, float *bwd_trace_dev) {
+  if (!mlp || rows <= 0 || !feat_dev || !target_dev || !grad_dev || !fwd_trace_dev || !bwd_trace_dev)
+    return mfail(mlp, PECC_ERR_ARG, "bad arguments");
+  MCK(mlp_grad(mlp->wb, mlp->params, feat_dev, target_dev, rows, mlp->part, mlp->lpart, grad_dev, loss_dev,
+               mlp->sms, mlp->stream, fwd_trace_dev, bwd_trace_dev));
+  return PECC_OK;
+}
+
 pecc_status pecc_mlp_train_step(pecc_mlp *mlp, const float *feat_dev, const float *target_dev, int64_t rows,
                                 float lr, float *loss_dev) {
   if (!mlp || rows <= 0 || !feat_dev || !target_dev || !(lr > 0.f)) return mfail(mlp, PECC_ERR_ARG, "bad arguments");
@@ -1103,9 +1120,14 @@ pecc_status pecc_targets(pecc_ctx *ctx, const double *xbefore_dev, float *target
 }
 
 pecc_status pecc_warm_start(pecc_ctx *ctx, pecc_mlp *mlp, int32_t rounds, int32_t *accepted_dev) {
+  return pecc_warm_start_ex(ctx, mlp, rounds, 0.25, accepted_dev);
+}
+
+pecc_status pecc_warm_start_ex(pecc_ctx *ctx, pecc_mlp *mlp, int32_t rounds, double max_move, int32_t *accepted_dev) {
   pecc_status s = need_fp32(ctx);
   if (s) return s;
-  if (!mlp || rounds < 0) return fail(ctx, PECC_ERR_ARG, "bad arguments");
+  if (!mlp || rounds < 0 || !(max_move > 0.0) || !(max_move <= 1e6))
+    return fail(ctx, PECC_ERR_ARG, "bad arguments");
   if ((s = mlp_scratch(ctx))) return s;
   StandaloneParams sp = sparams(ctx);
   for (int r = 0; r < rounds; ++r) {
@@ -1113,7 +1135,7 @@ pecc_status pecc_warm_start(pecc_ctx *ctx, pecc_mlp *mlp, int32_t rounds, int32_
     CK(energy_grad_launch(ctx, sp, 1, ctx->Eb, ctx->g));
     CK(mlp_features(sp, ctx->feat, ctx->stream));
     CK(mlp_forward(mlp->wb, mlp->params, ctx->feat, ctx->total, ctx->dout, mlp->sms, ctx->stream));
-    CK(mlp_apply(sp, ctx->dout, ctx->backup, ctx->stream));
+    CK(mlp_apply(sp, ctx->dout, ctx->backup, (float)max_move, ctx->stream));
     CK(launch_build(sp, 1, 1, nullptr, nullptr, ctx->block_build, ctx->stream));
     CK(energy_grad_launch(ctx, sp, 1, ctx->Ea, ctx->g));
     CK(mlp_revert(sp, ctx->backup, ctx->Eb, ctx->Ea, accepted_dev, ctx->stream));

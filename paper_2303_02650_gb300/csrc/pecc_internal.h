@@ -234,12 +234,13 @@ cudaError_t mlp_sync_bf16(const float *params, __nv_bfloat16 *wb, cudaStream_t s
 cudaError_t mlp_features(const StandaloneParams &p, float *feat, cudaStream_t s);
 cudaError_t mlp_targets(const StandaloneParams &p, const double *xbefore, float *target, cudaStream_t s);
 cudaError_t mlp_forward(const __nv_bfloat16 *wb, const float *params, const float *feat, int64_t rows, float *out,
-                        int sms, cudaStream_t s);
+                        int sms, cudaStream_t s, float *trace = nullptr);
 cudaError_t mlp_grad(const __nv_bfloat16 *wb, const float *params, const float *feat, const float *target,
-                     int64_t rows, float *part, float *lpart, float *grad, float *loss, int sms, cudaStream_t s);
+                     int64_t rows, float *part, float *lpart, float *grad, float *loss, int sms, cudaStream_t s,
+                     float *fwd_trace = nullptr, float *bwd_trace = nullptr);
 cudaError_t mlp_adam(float *params, float *m, float *v, const float *grad, __nv_bfloat16 *wb, float lr, int step,
                      cudaStream_t s);
-cudaError_t mlp_apply(const StandaloneParams &p, const float *dout, float2 *backup, cudaStream_t s);
+cudaError_t mlp_apply(const StandaloneParams &p, const float *dout, float2 *backup, float max_move, cudaStream_t s);
 cudaError_t mlp_revert(const StandaloneParams &p, const float2 *backup, const double *Eb, const double *Ea,
                        int32_t *accepted, cudaStream_t s);
 

@@ -1,7 +1,8 @@
 // pecc_mlp.cu -- the learned warm start: a per-circle MLP that reads the relative offsets of a
 // circle's 12 nearest neighbours and its distance to the container wall and proposes a
 // displacement; training (forward, backward, Adam) and inference are the kernels below, with the
-// three GEMMs of every layer on the tensor cores (mma.sync m16n8k16, BF16 inputs, FP32 accumulate).
+// 128-wide GEMMs of every layer on the fifth-generation tensor cores (tcgen05.mma, BF16 inputs,
+// FP32 accumulators in TMEM).
 //
 // Features of circle i (binary32, every operation correctly rounded so that a plain CPU
 // restatement reproduces them bit for bit): the frame e_r = c_i / |c_i| (e_r = (1, 0) at the
@@ -12,6 +13,7 @@
 #include <cuda_bf16.h>
 
 #include "pecc_internal.h"
+#include "pecc_tc.cuh"
 
 namespace pecc {
 namespace {
@@ -22,11 +24,8 @@ constexpr int KNN = 12;
 constexpr float kKnnR2 = 4.5f * 4.5f;
 constexpr int H = 128;
 constexpr int F = 25;      // features
-constexpr int FP = 32;     // padded input width
 constexpr int SA = 136;    // padded row stride (bf16) of 128-wide tiles: conflict-free fragments
 constexpr int S1 = 40;     // padded row stride of 32-wide tiles
-constexpr int SO = 24;     // padded row stride of 16-wide tiles
-constexpr int TR = 64;     // rows per block tile
 
 // ---------------------------------------------------------------------------- parameters ----
 // Flat binary32 parameter vector: W1[128][25] b1[128] W2[128][128] b2[128] W3[128][128] b3[128]
@@ -40,43 +39,6 @@ __device__ __forceinline__ uint32_t pack2(bf16 lo, bf16 hi) {
   return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
 }
 
-__device__ __forceinline__ void mma16816(float (&c)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
-                                         uint32_t b0, uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};\n"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-}
-
-// C[16][8 NT] += A[16][K] B[K][8 NT] for one warp; A(m, k) = A[m * am + k * ak], B(k, n) = B[k * bk + n * bn]
-// (shared memory, any strides: transposed operands are read in place).  Fragment layout of
-// m16n8k16: lane = 4 g + t; A regs (g, 2t..), (g+8, 2t..), (g, 8+2t..), (g+8, 8+2t..); B regs
-// (k = 2t.., n = g), (k = 8+2t.., n = g); C (g, 2t..), (g+8, 2t..).
-template <int NT>
-__device__ __forceinline__ void wgemm(float (&c)[NT][4], const bf16 *A, int am, int ak, const bf16 *B, int bk, int bn,
-                                      int K) {
-  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-  for (int k0 = 0; k0 < K; k0 += 16) {
-    const int ka = k0 + 2 * t, kb = ka + 8;
-    const uint32_t a0 = pack2(A[g * am + ka * ak], A[g * am + (ka + 1) * ak]);
-    const uint32_t a1 = pack2(A[(g + 8) * am + ka * ak], A[(g + 8) * am + (ka + 1) * ak]);
-    const uint32_t a2 = pack2(A[g * am + kb * ak], A[g * am + (kb + 1) * ak]);
-    const uint32_t a3 = pack2(A[(g + 8) * am + kb * ak], A[(g + 8) * am + (kb + 1) * ak]);
-#pragma unroll
-    for (int j = 0; j < NT; ++j) {
-      const int nn = 8 * j + g;
-      const uint32_t b0 = pack2(B[ka * bk + nn * bn], B[(ka + 1) * bk + nn * bn]);
-      const uint32_t b1 = pack2(B[kb * bk + nn * bn], B[(kb + 1) * bk + nn * bn]);
-      mma16816(c[j], a0, a1, a2, a3, b0, b1);
-    }
-  }
-}
-
-template <int NT> __device__ __forceinline__ void zero(float (&c)[NT][4]) {
-#pragma unroll
-  for (int j = 0; j < NT; ++j) c[j][0] = c[j][1] = c[j][2] = c[j][3] = 0.f;
-}
 
 // ------------------------------------------------------------------------------- features ----
 __device__ __forceinline__ float2 frame_er(float2 c) {
@@ -165,248 +127,406 @@ __global__ void targets_kernel(StandaloneParams P, const double *__restrict__ xb
   target[2 * gi + 1] = __fsub_rn(__fmul_rn(dy, er.x), __fmul_rn(dx, er.y));
 }
 
-// ------------------------------------------------------------------------- weights in smem ----
-// biases in shared memory: b1[128] b2[128] b3[128] b4[2]
-constexpr int SB1 = 0, SB2 = 128, SB3 = 256, SB4 = 384, NSB = 392;
+// ------------------------------------------------------------------ tensor-core network ----
+// Both kernels below keep every weight and activation tile in shared memory in the core layout of
+// pecc_tc.cuh and run the 128-wide GEMMs as tcgen05 MMAs (M = 128 rows of a tile, K = 16 per
+// instruction) issued by thread 0, with FP32 accumulators in TMEM; thread t of the 128 owns row t
+// of a tile (TMEM lane t) in every epilogue.  The 2-wide output layer and its gradient run on the
+// CUDA cores inside the epilogues.
+constexpr int TM = 128;                  // rows per tile
+constexpr int FPAD = 32;                 // padded input width
+constexpr uint32_t kW1B = TM * FPAD * 2;  // bytes of a [128][32] bf16 core tile
+constexpr uint32_t kHB = TM * H * 2;      // bytes of a [128][128] bf16 core tile
+constexpr long long kWaitNs = 2000000000ll;  // bound of every wait on the MMA barrier
+constexpr uint32_t kColStep = 2 * 128;       // a K step of 16 along the columns: two cores
 
-__device__ void load_weights(const bf16 *__restrict__ wb, const float *__restrict__ params, bf16 *s, float *sb) {
-  const uint4 *src = (const uint4 *)wb;
-  uint4 *dst = (uint4 *)s;
-  for (int u = threadIdx.x; u < NBW * 2 / 16; u += blockDim.x) dst[u] = src[u];
+// weights of the block: W1 [128][32], W2, W3 [128][128] in the core layout, from the padded bf16
+// copies; biases b1 b2 b3 [128], the output layer W4 [2][128] (bf16 values) and b4 [2] as floats
+__device__ void tc_load_weights(const bf16 *__restrict__ wb, const float *__restrict__ params, unsigned char *w1,
+                                unsigned char *w2, unsigned char *w3, float *fb) {
+  for (int u = threadIdx.x; u < TM * (FPAD / 8); u += blockDim.x) {
+    const int o = u / (FPAD / 8), c8 = u % (FPAD / 8);
+    *(uint4 *)(w1 + tc::core_off(o, 8 * c8, FPAD)) = *(const uint4 *)(wb + BW1 + o * S1 + 8 * c8);
+  }
+  for (int u = threadIdx.x; u < TM * (H / 8); u += blockDim.x) {
+    const int o = u / (H / 8), c8 = u % (H / 8);
+    *(uint4 *)(w2 + tc::core_off(o, 8 * c8, H)) = *(const uint4 *)(wb + BW2 + o * SA + 8 * c8);
+    *(uint4 *)(w3 + tc::core_off(o, 8 * c8, H)) = *(const uint4 *)(wb + BW3 + o * SA + 8 * c8);
+  }
   for (int u = threadIdx.x; u < H; u += blockDim.x) {
-    sb[SB1 + u] = params[OB1 + u];
-    sb[SB2 + u] = params[OB2 + u];
-    sb[SB3 + u] = params[OB3 + u];
+    fb[u] = params[OB1 + u];
+    fb[H + u] = params[OB2 + u];
+    fb[2 * H + u] = params[OB3 + u];
+    fb[3 * H + u] = __bfloat162float(wb[BW4 + u]);
+    fb[4 * H + u] = __bfloat162float(wb[BW4 + SA + u]);
   }
-  if (threadIdx.x < 2) sb[SB4 + threadIdx.x] = params[OB4 + threadIdx.x];
+  if (threadIdx.x < 2) fb[5 * H + threadIdx.x] = params[OB4 + threadIdx.x];
 }
 
-// rows row0..row0+15 of the fp32 features [rows][25] into a bf16 [16][S1] tile (zero padded)
-__device__ void load_x(const float *__restrict__ feat, int64_t row0, int64_t rows, bf16 *X) {
-  for (int u = threadIdx.x & 31; u < 16 * FP; u += 32) {
-    const int r = u / FP, c = u % FP;
-    const int64_t gr = row0 + r;
-    const float v = (gr < rows && c < F) ? feat[gr * F + c] : 0.f;
-    X[r * S1 + c] = __float2bfloat16_rn(v);
-  }
-  __syncwarp();
-}
-
-// bias + ReLU on a warp's 16 x 128 accumulator, stored as bf16 into a [16][SA] tile
-__device__ __forceinline__ void act_store(float (&c)[16][4], const float *__restrict__ bias, bf16 *Hs) {
-  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+// row r of the tile's input: the 25 features of global row gr (zero past rows and past column 25)
+__device__ __forceinline__ void tc_load_row(const float *__restrict__ feat, int64_t gr, int64_t rows, int r,
+                                            unsigned char *x) {
 #pragma unroll
-  for (int j = 0; j < 16; ++j) {
-    const int col = 8 * j + 2 * t;
-    const float b0 = bias[col], b1 = bias[col + 1];
-    Hs[g * SA + col] = __float2bfloat16_rn(fmaxf(c[j][0] + b0, 0.f));
-    Hs[g * SA + col + 1] = __float2bfloat16_rn(fmaxf(c[j][1] + b1, 0.f));
-    Hs[(g + 8) * SA + col] = __float2bfloat16_rn(fmaxf(c[j][2] + b0, 0.f));
-    Hs[(g + 8) * SA + col + 1] = __float2bfloat16_rn(fmaxf(c[j][3] + b1, 0.f));
-  }
-  __syncwarp();
-}
-
-// Forward of one warp's 16 rows; out[16][2] (fp32).  X, H1..H3: this warp's tiles.
-__device__ void warp_forward(const bf16 *W, const float *sb, const bf16 *X, bf16 *H1, bf16 *H2, bf16 *H3,
-                             float *out) {
-  float c[16][4];
-  zero(c);
-  wgemm<16>(c, X, S1, 1, W + BW1, 1, S1, FP);
-  act_store(c, sb + SB1, H1);
-  zero(c);
-  wgemm<16>(c, H1, SA, 1, W + BW2, 1, SA, H);
-  act_store(c, sb + SB2, H2);
-  zero(c);
-  wgemm<16>(c, H2, SA, 1, W + BW3, 1, SA, H);
-  act_store(c, sb + SB3, H3);
-  float o[2][4];
-  zero(o);
-  wgemm<2>(o, H3, SA, 1, W + BW4, 1, SA, H);
-  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-  if (t == 0) {  // output columns 0 and 1 sit in n-tile 0 on the lanes with t == 0
-    out[g * 2 + 0] = o[0][0] + sb[SB4];
-    out[g * 2 + 1] = o[0][1] + sb[SB4 + 1];
-    out[(g + 8) * 2 + 0] = o[0][2] + sb[SB4];
-    out[(g + 8) * 2 + 1] = o[0][3] + sb[SB4 + 1];
-  }
-  __syncwarp();
-}
-
-constexpr size_t kWBytes = (size_t)NBW * 2;
-constexpr size_t kHead = kWBytes + (size_t)NSB * 4;
-constexpr size_t kFwdWarpBytes = (size_t)(16 * S1 + 3 * 16 * SA) * 2 + 16 * 2 * 4;
-constexpr size_t kFwdSmem = kHead + 4 * kFwdWarpBytes;
-
-__global__ void __launch_bounds__(128) forward_kernel(const bf16 *__restrict__ wb, const float *__restrict__ params,
-                                                      const float *__restrict__ feat, int64_t rows, float *out) {
-  extern __shared__ __align__(16) unsigned char sm[];
-  bf16 *W = (bf16 *)sm;
-  float *sb = (float *)(sm + kWBytes);
-  load_weights(wb, params, W, sb);
-  __syncthreads();
-  const int w = threadIdx.x >> 5;
-  unsigned char *mine = sm + kHead + (size_t)w * kFwdWarpBytes;
-  bf16 *X = (bf16 *)mine, *H1 = X + 16 * S1, *H2 = H1 + 16 * SA, *H3 = H2 + 16 * SA;
-  float *o = (float *)(H3 + 16 * SA);
-  const int64_t tiles = (rows + 15) / 16;
-  for (int64_t tl = (int64_t)blockIdx.x * 4 + w; tl < tiles; tl += (int64_t)gridDim.x * 4) {
-    const int64_t r0 = tl * 16;
-    load_x(feat, r0, rows, X);
-    warp_forward(W, sb, X, H1, H2, H3, o);
-    const int lane = threadIdx.x & 31;
-    if (lane < 16 && r0 + lane < rows) {
-      out[(r0 + lane) * 2] = o[lane * 2];
-      out[(r0 + lane) * 2 + 1] = o[lane * 2 + 1];
+  for (int c8 = 0; c8 < FPAD / 8; ++c8) {
+    uint32_t w[4];
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+      const int c = 8 * c8 + 2 * h;
+      const float a = (gr < rows && c < F) ? feat[gr * F + c] : 0.f;
+      const float b = (gr < rows && c + 1 < F) ? feat[gr * F + c + 1] : 0.f;
+      w[h] = pack2(__float2bfloat16_rn(a), __float2bfloat16_rn(b));
     }
-    __syncwarp();
+    *(uint4 *)(x + tc::core_off(r, 8 * c8, FPAD)) = make_uint4(w[0], w[1], w[2], w[3]);
+  }
+}
+
+// 32 bf16 values of row r starting at column c0 of a [128][128] core tile
+__device__ __forceinline__ void tc_store32(unsigned char *t, int r, int c0, const float (&v)[32]) {
+#pragma unroll
+  for (int c8 = 0; c8 < 4; ++c8) {
+    uint32_t w[4];
+#pragma unroll
+    for (int h = 0; h < 4; ++h)
+      w[h] = pack2(__float2bfloat16_rn(v[8 * c8 + 2 * h]), __float2bfloat16_rn(v[8 * c8 + 2 * h + 1]));
+    *(uint4 *)(t + tc::core_off(r, c0 + 8 * c8, H)) = make_uint4(w[0], w[1], w[2], w[3]);
+  }
+}
+__device__ __forceinline__ float tc_get(const unsigned char *t, int r, int c, int C) {
+  return __bfloat162float(*(const bf16 *)(t + tc::core_off(r, c, C)));
+}
+
+// Thread 0 issues D = A B^T over K (K / 16 MMAs) and commits them to the barrier.  The operand
+// descriptors advance by `astep` / `bstep` bytes per K step of 16.
+__device__ __forceinline__ void tc_gemm(uint32_t d, uint32_t a_addr, bool a_krows, int a_cols, uint32_t astep,
+                                        uint32_t b_addr, bool b_krows, int b_cols, uint32_t bstep, int N, int K,
+                                        bool accumulate) {
+  const uint32_t id = tc::idesc_bf16(TM, N, a_krows ? 1 : 0, b_krows ? 1 : 0);
+  for (int ks = 0; ks < K / 16; ++ks) {
+    const uint32_t aa = a_addr + ks * astep, ba = b_addr + ks * bstep;
+    const uint64_t ad = a_krows ? tc::desc_k_rows(aa, a_cols) : tc::desc_k_cols(aa, a_cols);
+    const uint64_t bd = b_krows ? tc::desc_k_rows(ba, b_cols) : tc::desc_k_cols(ba, b_cols);
+    tc::mma(d, ad, bd, id, (accumulate || ks > 0) ? 1 : 0);
+  }
+}
+
+// Make this block's shared-memory writes visible to the tensor cores and order TMEM accesses around
+// a block barrier.
+__device__ __forceinline__ void tc_sync() {
+  tc::fence_smem_to_async();
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+}
+
+// Thread 0 commits the MMAs issued so far and waits for them; every thread learns whether the wait
+// ended in time (block-uniform).
+__device__ __forceinline__ bool tc_commit_wait(uint64_t *mbar, uint32_t &phase, int *flag) {
+  if (threadIdx.x == 0) {
+    tc::commit(mbar);
+    *flag = tc::mbar_wait(mbar, phase, kWaitNs) ? 0 : 1;
+  }
+  phase ^= 1u;
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  return *flag == 0;
+}
+
+// Epilogue of a hidden layer: this thread's row of the accumulator plus bias, ReLU, rounded to bf16
+// into tile `t` (and, if set, the rounded values to trace[0..128)); with w4, also the output layer
+// o0 / o1 += h W4^T from the rounded values.
+__device__ __forceinline__ void tc_hidden_epilogue(uint32_t tacc, const float *bias, unsigned char *t, float *trace,
+                                                   const float *w4, float &o0, float &o1) {
+  const int r = threadIdx.x;
+  for (int c0 = 0; c0 < H; c0 += 32) {
+    float v[32];
+    tc::ld32(tacc + ((uint32_t)(r & ~31) << 16) + (uint32_t)c0, v);
+#pragma unroll
+    for (int j = 0; j < 32; ++j) v[j] = __bfloat162float(__float2bfloat16_rn(fmaxf(v[j] + bias[c0 + j], 0.f)));
+    if (t) tc_store32(t, r, c0, v);
+    if (trace)
+#pragma unroll
+      for (int j = 0; j < 32; ++j) trace[c0 + j] = v[j];
+    if (w4)
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        o0 = fmaf(v[j], w4[c0 + j], o0);
+        o1 = fmaf(v[j], w4[H + c0 + j], o1);
+      }
+  }
+}
+
+constexpr uint32_t kFwdW1 = 0, kFwdW2 = kFwdW1 + kW1B, kFwdW3 = kFwdW2 + kHB, kFwdX = kFwdW3 + kHB,
+                   kFwdH = kFwdX + kW1B, kFwdF = kFwdH + kHB, kFwdBar = kFwdF + (5 * H + 2) * 4 + 8;
+constexpr size_t kFwdSmem = (size_t)kFwdBar + 16 + 1024;  // + the barrier, TMEM address, flag; + alignment slack
+
+// Forward: out[rows][2] for rows of feat[rows][25]; trace (may be null): float[rows][3][128], the
+// bf16 activations of the three hidden layers.  Persistent over tiles of 128 rows.
+__global__ void __launch_bounds__(128, 1) forward_tc_kernel(const bf16 *__restrict__ wb, const float *__restrict__ params,
+                                                             const float *__restrict__ feat, int64_t rows, float *out,
+                                                             float *trace) {
+  extern __shared__ unsigned char sm_raw[];
+  unsigned char *sm = (unsigned char *)(((uintptr_t)sm_raw + 1023) & ~(uintptr_t)1023);
+  unsigned char *w1 = sm + kFwdW1, *w2 = sm + kFwdW2, *w3 = sm + kFwdW3, *x = sm + kFwdX, *h = sm + kFwdH;
+  float *fb = (float *)(sm + kFwdF);
+  uint64_t *mbar = (uint64_t *)(sm + kFwdBar);
+  uint32_t *tslot = (uint32_t *)(mbar + 1);
+  int *flag = (int *)(tslot + 1);
+  const int r = threadIdx.x;
+  tc_load_weights(wb, params, w1, w2, w3, fb);
+  if (r == 0) { tc::mbar_init(mbar); *flag = 0; }
+  if (r < 32) tc::tmem_alloc<128>(tslot);
+  tc_sync();
+  const uint32_t tacc = *tslot;
+  const uint32_t sw1 = tc::smem_u32(w1), sw2 = tc::smem_u32(w2), sw3 = tc::smem_u32(w3), sx = tc::smem_u32(x),
+                 sh = tc::smem_u32(h);
+  uint32_t phase = 0;
+  bool ok = true;
+  const int64_t tiles = (rows + TM - 1) / TM;
+  for (int64_t tl = blockIdx.x; tl < tiles && ok; tl += gridDim.x) {
+    const int64_t gr = tl * TM + r;
+    float *tr = (trace && gr < rows) ? trace + gr * 3 * H : nullptr;
+    tc_load_row(feat, gr, rows, r, x);
+    tc_sync();
+    if (r == 0) tc_gemm(tacc, sx, false, FPAD, kColStep, sw1, false, FPAD, kColStep, H, FPAD, false);
+    if (!(ok = tc_commit_wait(mbar, phase, flag))) break;
+    float o0 = 0.f, o1 = 0.f;
+    tc_hidden_epilogue(tacc, fb, h, tr, nullptr, o0, o1);
+    tc_sync();
+    if (r == 0) tc_gemm(tacc, sh, false, H, kColStep, sw2, false, H, kColStep, H, H, false);
+    if (!(ok = tc_commit_wait(mbar, phase, flag))) break;
+    tc_hidden_epilogue(tacc, fb + H, h, tr ? tr + H : nullptr, nullptr, o0, o1);
+    tc_sync();
+    if (r == 0) tc_gemm(tacc, sh, false, H, kColStep, sw3, false, H, kColStep, H, H, false);
+    if (!(ok = tc_commit_wait(mbar, phase, flag))) break;
+    tc_hidden_epilogue(tacc, fb + 2 * H, nullptr, tr ? tr + 2 * H : nullptr, fb + 3 * H, o0, o1);
+    if (gr < rows) {
+      out[gr * 2] = o0 + fb[5 * H];
+      out[gr * 2 + 1] = o1 + fb[5 * H + 1];
+    }
+    tc::fence_before();
+    __syncthreads();  // every row's TMEM reads precede the next tile's MMAs
+    tc::fence_after();
+  }
+  if (!ok)  // the tensor cores did not answer in time: NaN outputs, nothing left waiting
+    for (int64_t gr = (int64_t)blockIdx.x * TM + r; gr < rows; gr += (int64_t)gridDim.x * TM) {
+      out[gr * 2] = out[gr * 2 + 1] = __int_as_float(0x7fc00000);
+    }
+  tc::fence_before();
+  __syncthreads();
+  if (r < 32) {
+    tc::fence_after();
+    tc::tmem_free<128>(tacc);
   }
 }
 
 // ------------------------------------------------------------------------------- training ----
-// One block: 4 warps, tiles of 64 rows; forward (keeping X, H1..H3), then backward:
-//   dO = 2 (out - target) / rows;  dW4 += dO' H3;  dZ3 = (dO W4) o [H3 > 0];  dW3 += dZ3' H2;
-//   dZ2 = (dZ3 W3) o [H2 > 0];  dW2 += dZ2' H1;  dZ1 = (dZ2 W2) o [H1 > 0];  dW1 += dZ1' X;
-//   db_l += column sums of dZ_l (db4 of dO).  GEMM inputs are bf16 (dZ rounded like the activations).
-// Each block adds its tiles' gradients into its own binary32 slice part[block][NPAR].
-constexpr size_t kTrainTile = (size_t)(TR * S1 + 3 * TR * SA + TR * SO + 2 * TR * SA) * 2 + TR * 2 * 4;
-constexpr size_t kTrainSmem = kHead + kTrainTile;
+// One block per SM, persistent over tiles of 128 rows: forward (keeping X, H1, H2, H3), then
+//   dO = 2 (out - target) / rows (rounded to bf16);  dW4 += dO' H3, db4 += sum dO   (CUDA cores)
+//   dZ3 = (dO W4) o [H3 > 0]                                                         (CUDA cores)
+//   dW3 += dZ3' H2 (TMEM, across tiles);  dH2 = dZ3 W3;  dZ2 = dH2 o [H2 > 0]        (tensor cores)
+//   dW2 += dZ2' H1;  dH1 = dZ2 W2;  dZ1 = dH1 o [H1 > 0];  dW1 += dZ1' X             (tensor cores)
+//   db_l += column sums of dZ_l.  Every GEMM input is bf16 (dZ rounded like the activations).
+// The gradient accumulators dW3, dW2, dW1 stay in TMEM until the block's last tile; the block then
+// writes its partial gradient to part[block][NPAR] and its loss to loss_part[block].
+// bwd_trace (may be null): float[rows][4][128], the bf16 dZ3, dZ2, dZ1 of every row, then its bf16
+// dO (2 values) and its outputs (2 values).
+constexpr uint32_t kTrW1 = 0, kTrW2 = kTrW1 + kW1B, kTrW3 = kTrW2 + kHB, kTrX = kTrW3 + kHB, kTrH1 = kTrX + kW1B,
+                   kTrH2 = kTrH1 + kHB, kTrH3 = kTrH2 + kHB, kTrZ = kTrH3 + kHB, kTrF = kTrZ + kHB;
+// floats after kTrF: biases and W4 (5 H + 2), dO [128][2], dW4 accumulator [2][128], bias gradient
+// accumulators db1 db2 db3 [128] and db4 [2], the loss of each warp [4]
+constexpr int kTrFdO = 5 * H + 2, kTrFdW4 = kTrFdO + 2 * TM, kTrFdb = kTrFdW4 + 2 * H, kTrFls = kTrFdb + 3 * H + 2,
+              kTrFn = kTrFls + 4;
+constexpr uint32_t kTrBar = kTrF + ((kTrFn * 4 + 15) & ~15);
+constexpr size_t kTrainSmem = (size_t)kTrBar + 16 + 1024;
 
-// gp[base + (m0 + row) * ld + col] += accumulator of output rows m0.. (rows < mrows, cols < ncols)
-template <int NT>
-__device__ __forceinline__ void add_acc(float *gp, int base, int ld, const float (&c)[NT][4], int m0, int mrows,
-                                        int ncols) {
-  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-#pragma unroll
-  for (int j = 0; j < NT; ++j) {
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int col = 8 * j + 2 * t + h;
-      if (col >= ncols) continue;
-      if (m0 + g < mrows) gp[base + (m0 + g) * ld + col] += c[j][h];
-      if (m0 + g + 8 < mrows) gp[base + (m0 + g + 8) * ld + col] += c[j][2 + h];
-    }
-  }
-}
-
-// dZ = (Zin Wl) o [Hmask > 0] for a warp's 16 rows (Zin: K columns), stored bf16 into Zout
-__device__ __forceinline__ void back_layer(const bf16 *Zin, int zs, int K, const bf16 *Wl, const bf16 *Hmask, bf16 *Zout) {
-  float c[16][4];
-  zero(c);
-  wgemm<16>(c, Zin, zs, 1, Wl, SA, 1, K);
-  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-#pragma unroll
-  for (int j = 0; j < 16; ++j) {
-    const int col = 8 * j + 2 * t;
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const bool m0 = __bfloat162float(Hmask[g * SA + col + h]) > 0.f;
-      const bool m1 = __bfloat162float(Hmask[(g + 8) * SA + col + h]) > 0.f;
-      Zout[g * SA + col + h] = __float2bfloat16_rn(m0 ? c[j][h] : 0.f);
-      Zout[(g + 8) * SA + col + h] = __float2bfloat16_rn(m1 ? c[j][2 + h] : 0.f);
-    }
-  }
-  __syncwarp();
-}
-
-// dW[o][i] += sum_r Z[r][o] Hin[r][i] over the tile's 64 rows; warp w takes output rows 32w..32w+31
-template <int NT>
-__device__ __forceinline__ void weight_grad(float *gp, int base, int ld, const bf16 *Z, const bf16 *Hin, int hs,
-                                            int ncols) {
-  const int w = threadIdx.x >> 5;
-  for (int mt = 2 * w; mt < 2 * w + 2; ++mt) {
-    float c[NT][4];
-    zero(c);
-    wgemm<NT>(c, Z + 16 * mt, 1, SA, Hin, hs, 1, TR);
-    add_acc<NT>(gp, base, ld, c, 16 * mt, H, ncols);
-  }
-}
-
-__device__ __forceinline__ void bias_grad(float *gp, int base, const bf16 *Z) {
-  for (int o = threadIdx.x; o < H; o += blockDim.x) {
-    float s = 0.f;
-    for (int r = 0; r < TR; ++r) s += __bfloat162float(Z[r * SA + o]);
-    gp[base + o] += s;
-  }
-}
-
-__global__ void __launch_bounds__(128, 1) train_kernel(const bf16 *__restrict__ wb, const float *__restrict__ params,
-                                                       const float *__restrict__ feat,
-                                                       const float *__restrict__ target, int64_t rows, float *part,
-                                                       float *loss_part) {
-  extern __shared__ __align__(16) unsigned char sm[];
-  bf16 *W = (bf16 *)sm;
-  float *sb = (float *)(sm + kWBytes);
-  unsigned char *tile = sm + kHead;
-  bf16 *X = (bf16 *)tile;                  // [64][S1]
-  bf16 *H1 = X + TR * S1;                  // [64][SA]
-  bf16 *H2 = H1 + TR * SA;
-  bf16 *H3 = H2 + TR * SA;
-  bf16 *dO = H3 + TR * SA;                 // [64][SO]
-  bf16 *Za = dO + TR * SO;                 // [64][SA]
-  bf16 *Zb = Za + TR * SA;
-  float *out = (float *)(Zb + TR * SA);    // [64][2]
-  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
-  load_weights(wb, params, W, sb);
-  float *gp = part + (size_t)blockIdx.x * NPAR;
-  for (int u = tid; u < NPAR; u += blockDim.x) gp[u] = 0.f;
-  for (int u = tid; u < TR * SO; u += blockDim.x) dO[u] = __float2bfloat16_rn(0.f);
-  float lsum = 0.f;
-  __syncthreads();
+__global__ void __launch_bounds__(128, 1) train_tc_kernel(const bf16 *__restrict__ wb, const float *__restrict__ params,
+                                                           const float *__restrict__ feat, const float *__restrict__ target,
+                                                           int64_t rows, float *part, float *loss_part,
+                                                           float *fwd_trace, float *bwd_trace) {
+  extern __shared__ unsigned char sm_raw[];
+  unsigned char *sm = (unsigned char *)(((uintptr_t)sm_raw + 1023) & ~(uintptr_t)1023);
+  unsigned char *w1 = sm + kTrW1, *w2 = sm + kTrW2, *w3 = sm + kTrW3, *x = sm + kTrX;
+  unsigned char *h1 = sm + kTrH1, *h2 = sm + kTrH2, *h3 = sm + kTrH3, *z = sm + kTrZ;
+  float *fb = (float *)(sm + kTrF);
+  float *dO = fb + kTrFdO, *adW4 = fb + kTrFdW4, *adb = fb + kTrFdb, *lsw = fb + kTrFls;
+  uint64_t *mbar = (uint64_t *)(sm + kTrBar);
+  uint32_t *tslot = (uint32_t *)(mbar + 1);
+  int *flag = (int *)(tslot + 1);
+  const int r = threadIdx.x, lane = r & 31, w = r >> 5;
+  tc_load_weights(wb, params, w1, w2, w3, fb);
+  for (int u = r; u < 2 * H + 3 * H + 2; u += blockDim.x) adW4[u] = 0.f;  // adW4 and adb are adjacent
+  if (r == 0) { tc::mbar_init(mbar); *flag = 0; }
+  if (r < 32) tc::tmem_alloc<512>(tslot);
+  tc_sync();
+  // TMEM columns: [0, 128) the layer accumulator, [128, 256) dW3, [256, 384) dW2, [384, 416) dW1
+  const uint32_t tacc = *tslot, tdw3 = tacc + 128, tdw2 = tacc + 256, tdw1 = tacc + 384;
+  const uint32_t lanes = (uint32_t)(r & ~31) << 16;
+  const uint32_t sw1 = tc::smem_u32(w1), sw2 = tc::smem_u32(w2), sw3 = tc::smem_u32(w3), sx = tc::smem_u32(x);
+  const uint32_t sh1 = tc::smem_u32(h1), sh2 = tc::smem_u32(h2), sz = tc::smem_u32(z);
+  const uint32_t kRowStep = 2 * (H / 8) * 128;     // two 8-row core groups of a [128][128] tile
+  const uint32_t kRowStepX = 2 * (FPAD / 8) * 128;  // of a [128][32] tile
   const float scale = 2.f / (float)rows;
-  const int64_t tiles = (rows + TR - 1) / TR;
-  for (int64_t tl = blockIdx.x; tl < tiles; tl += gridDim.x) {
-    const int64_t r0 = tl * TR;
-    load_x(feat, r0 + 16 * w, rows, X + 16 * w * S1);
-    warp_forward(W, sb, X + 16 * w * S1, H1 + 16 * w * SA, H2 + 16 * w * SA, H3 + 16 * w * SA, out + 16 * w * 2);
-    if (lane < 16) {
-      const int r = 16 * w + lane;
-      const int64_t gr = r0 + r;
-      float d0 = 0.f, d1 = 0.f;
-      if (gr < rows) {
-        d0 = out[r * 2] - target[gr * 2];
-        d1 = out[r * 2 + 1] - target[gr * 2 + 1];
+  float lsum = 0.f;
+  uint32_t phase = 0;
+  bool ok = true, first = true;
+  const int64_t tiles = (rows + TM - 1) / TM;
+  for (int64_t tl = blockIdx.x; tl < tiles && ok; tl += gridDim.x) {
+    const int64_t gr = tl * TM + r;
+    float *ft = (fwd_trace && gr < rows) ? fwd_trace + gr * 3 * H : nullptr;
+    float *bt = (bwd_trace && gr < rows) ? bwd_trace + gr * 4 * H : nullptr;
+    // ---- forward
+    tc_load_row(feat, gr, rows, r, x);
+    tc_sync();
+    if (r == 0) tc_gemm(tacc, sx, false, FPAD, kColStep, sw1, false, FPAD, kColStep, H, FPAD, false);
+    if (!(ok = tc_commit_wait(mbar, phase, flag))) break;
+    float o0 = 0.f, o1 = 0.f;
+    tc_hidden_epilogue(tacc, fb, h1, ft, nullptr, o0, o1);
+    tc_sync();
+    if (r == 0) tc_gemm(tacc, sh1, false, H, kColStep, sw2, false, H, kColStep, H, H, false);
+    if (!(ok = tc_commit_wait(mbar, phase, flag))) break;
+    tc_hidden_epilogue(tacc, fb + H, h2, ft ? ft + H : nullptr, nullptr, o0, o1);
+    tc_sync();
+    if (r == 0) tc_gemm(tacc, sh2, false, H, kColStep, sw3, false, H, kColStep, H, H, false);
+    if (!(ok = tc_commit_wait(mbar, phase, flag))) break;
+    tc_hidden_epilogue(tacc, fb + 2 * H, h3, ft ? ft + 2 * H : nullptr, fb + 3 * H, o0, o1);
+    // ---- output layer: dO of this row, rounded to bf16
+    float d0 = 0.f, d1 = 0.f;
+    if (gr < rows) {
+      d0 = (o0 + fb[5 * H]) - target[gr * 2];
+      d1 = (o1 + fb[5 * H + 1]) - target[gr * 2 + 1];
+    }
+    lsum += d0 * d0 + d1 * d1;
+    const float g0 = __bfloat162float(__float2bfloat16_rn(d0 * scale));
+    const float g1 = __bfloat162float(__float2bfloat16_rn(d1 * scale));
+    dO[2 * r] = g0;
+    dO[2 * r + 1] = g1;
+    if (bt) {
+      bt[3 * H] = g0;
+      bt[3 * H + 1] = g1;
+      bt[3 * H + 2] = o0 + fb[5 * H];
+      bt[3 * H + 3] = o1 + fb[5 * H + 1];
+    }
+    // dZ3 of this row from dO and W4, masked by H3
+    for (int c0 = 0; c0 < H; c0 += 32) {
+      float v[32];
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const int c = c0 + j;
+        const float dz = fmaf(g1, fb[4 * H + c], g0 * fb[3 * H + c]);
+        v[j] = tc_get(h3, r, c, H) > 0.f ? __bfloat162float(__float2bfloat16_rn(dz)) : 0.f;
       }
-      lsum += d0 * d0 + d1 * d1;
-      dO[r * SO + 0] = __float2bfloat16_rn(d0 * scale);
-      dO[r * SO + 1] = __float2bfloat16_rn(d1 * scale);
+      tc_store32(z, r, c0, v);
+      if (bt)
+#pragma unroll
+        for (int j = 0; j < 32; ++j) bt[c0 + j] = v[j];
     }
-    __syncthreads();
-    // layer 4: dW4 (2 x 128, warp 0), db4, dZ3
-    if (w == 0) {
-      float c[16][4];
-      zero(c);
-      wgemm<16>(c, dO, 1, SO, H3, SA, 1, TR);
-      add_acc<16>(gp, OW4, H, c, 0, 2, H);
+    tc_sync();
+    // dW3 += dZ3' H2 and dH2 = dZ3 W3 on the tensor cores; meanwhile dW4, db4 and db3 on the CUDA cores
+    if (r == 0) {
+      tc_gemm(tdw3, sz, true, H, kRowStep, sh2, true, H, kRowStep, H, TM, !first);
+      tc_gemm(tacc, sz, false, H, kColStep, sw3, true, H, kRowStep, H, H, false);
     }
-    if (tid < 2) {
-      float s = 0.f;
-      for (int r = 0; r < TR; ++r) s += __bfloat162float(dO[r * SO + tid]);
-      gp[OB4 + tid] += s;
+    {
+      float s0 = 0.f, s1 = 0.f, sb3 = 0.f;
+      for (int q = 0; q < TM; ++q) {
+        const float hq = tc_get(h3, q, r, H);
+        s0 = fmaf(dO[2 * q], hq, s0);
+        s1 = fmaf(dO[2 * q + 1], hq, s1);
+        sb3 += tc_get(z, q, r, H);
+      }
+      adW4[r] += s0;
+      adW4[H + r] += s1;
+      adb[2 * H + r] += sb3;
+      if (r < 2) {
+        float sb4 = 0.f;
+        for (int q = 0; q < TM; ++q) sb4 += dO[2 * q + r];
+        adb[3 * H + r] += sb4;
+      }
     }
-    back_layer(dO + 16 * w * SO, SO, 16, W + BW4, H3 + 16 * w * SA, Za + 16 * w * SA);
-    __syncthreads();
-    // layer 3: dW3 += Za' H2, db3, dZ2 -> Zb
-    weight_grad<16>(gp, OW3, H, Za, H2, SA, H);
-    bias_grad(gp, OB3, Za);
-    back_layer(Za + 16 * w * SA, SA, H, W + BW3, H2 + 16 * w * SA, Zb + 16 * w * SA);
-    __syncthreads();
-    // layer 2: dW2 += Zb' H1, db2, dZ1 -> Za
-    weight_grad<16>(gp, OW2, H, Zb, H1, SA, H);
-    bias_grad(gp, OB2, Zb);
-    __syncthreads();
-    back_layer(Zb + 16 * w * SA, SA, H, W + BW2, H1 + 16 * w * SA, Za + 16 * w * SA);
-    __syncthreads();
-    // layer 1: dW1 += Za' X (25 input columns), db1
-    weight_grad<4>(gp, OW1, F, Za, X, S1, F);
-    bias_grad(gp, OB1, Za);
-    __syncthreads();
+    if (!(ok = tc_commit_wait(mbar, phase, flag))) break;
+    // dZ2 = dH2 o [H2 > 0]
+    for (int c0 = 0; c0 < H; c0 += 32) {
+      float v[32];
+      tc::ld32(tacc + lanes + (uint32_t)c0, v);
+#pragma unroll
+      for (int j = 0; j < 32; ++j)
+        v[j] = tc_get(h2, r, c0 + j, H) > 0.f ? __bfloat162float(__float2bfloat16_rn(v[j])) : 0.f;
+      tc_store32(z, r, c0, v);
+      if (bt)
+#pragma unroll
+        for (int j = 0; j < 32; ++j) bt[H + c0 + j] = v[j];
+    }
+    tc_sync();
+    if (r == 0) {
+      tc_gemm(tdw2, sz, true, H, kRowStep, sh1, true, H, kRowStep, H, TM, !first);
+      tc_gemm(tacc, sz, false, H, kColStep, sw2, true, H, kRowStep, H, H, false);
+    }
+    {
+      float sb2 = 0.f;
+      for (int q = 0; q < TM; ++q) sb2 += tc_get(z, q, r, H);
+      adb[H + r] += sb2;
+    }
+    if (!(ok = tc_commit_wait(mbar, phase, flag))) break;
+    // dZ1 = dH1 o [H1 > 0]
+    for (int c0 = 0; c0 < H; c0 += 32) {
+      float v[32];
+      tc::ld32(tacc + lanes + (uint32_t)c0, v);
+#pragma unroll
+      for (int j = 0; j < 32; ++j)
+        v[j] = tc_get(h1, r, c0 + j, H) > 0.f ? __bfloat162float(__float2bfloat16_rn(v[j])) : 0.f;
+      tc_store32(z, r, c0, v);
+      if (bt)
+#pragma unroll
+        for (int j = 0; j < 32; ++j) bt[2 * H + c0 + j] = v[j];
+    }
+    tc_sync();
+    if (r == 0) tc_gemm(tdw1, sz, true, H, kRowStep, sx, true, FPAD, kRowStepX, FPAD, TM, !first);
+    {
+      float sb1 = 0.f;
+      for (int q = 0; q < TM; ++q) sb1 += tc_get(z, q, r, H);
+      adb[r] += sb1;
+    }
+    if (!(ok = tc_commit_wait(mbar, phase, flag))) break;
+    first = false;
   }
-  lsum = warp_sum(lsum);
-  __shared__ float ls[4];
-  if (lane == 0) ls[w] = lsum;
+  // ---- the block's partial gradient
+  float *gp = part + (size_t)blockIdx.x * NPAR;
+  const float nanv = __int_as_float(0x7fc00000);
+  if (ok && !first) {
+    for (int c0 = 0; c0 < H; c0 += 32) {
+      float v[32];
+      tc::ld32(tdw3 + lanes + (uint32_t)c0, v);
+      for (int j = 0; j < 32; ++j) gp[OW3 + r * H + c0 + j] = v[j];
+      tc::ld32(tdw2 + lanes + (uint32_t)c0, v);
+      for (int j = 0; j < 32; ++j) gp[OW2 + r * H + c0 + j] = v[j];
+    }
+    float v[32];
+    tc::ld32(tdw1 + lanes, v);
+    for (int j = 0; j < F; ++j) gp[OW1 + r * F + j] = v[j];
+  } else {
+    const float fill = ok ? 0.f : nanv;  // a block without tiles adds nothing
+    for (int u = r; u < H * H; u += blockDim.x) { gp[OW3 + u] = fill; gp[OW2 + u] = fill; }
+    for (int u = r; u < H * F; u += blockDim.x) gp[OW1 + u] = fill;
+  }
   __syncthreads();
-  if (tid == 0) loss_part[blockIdx.x] = ls[0] + ls[1] + ls[2] + ls[3];
+  for (int u = r; u < H; u += blockDim.x) {
+    gp[OB1 + u] = ok ? adb[u] : nanv;
+    gp[OB2 + u] = ok ? adb[H + u] : nanv;
+    gp[OB3 + u] = ok ? adb[2 * H + u] : nanv;
+    gp[OW4 + u] = ok ? adW4[u] : nanv;
+    gp[OW4 + H + u] = ok ? adW4[H + u] : nanv;
+  }
+  if (r < 2) gp[OB4 + r] = ok ? adb[3 * H + r] : nanv;
+  lsum = warp_sum(lsum);
+  if (lane == 0) lsw[w] = lsum;
+  tc::fence_before();
+  __syncthreads();
+  if (r == 0) loss_part[blockIdx.x] = ok ? lsw[0] + lsw[1] + lsw[2] + lsw[3] : nanv;
+  if (r < 32) {
+    tc::fence_after();
+    tc::tmem_free<512>(tacc);
+  }
 }
 
 // grad[p] = sum over blocks of part[b][p]; loss = sum of the blocks' losses / rows
@@ -476,8 +596,8 @@ __global__ void init_params_kernel(float *params, uint64_t seed) {
 }
 
 // ------------------------------------------------------------------------------ warm start ----
-// x += clip(du e_r + dv e_t, 0.25) per circle; the old coordinates go to backup
-__global__ void apply_kernel(StandaloneParams P, const float *__restrict__ dout, float2 *backup) {
+// x += clip(du e_r + dv e_t, max_move) per circle; the old coordinates go to backup
+__global__ void apply_kernel(StandaloneParams P, const float *__restrict__ dout, float2 *backup, float max_move) {
   const int64_t gi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (gi >= P.total) return;
   const float2 x = P.x32[gi];
@@ -486,7 +606,7 @@ __global__ void apply_kernel(StandaloneParams P, const float *__restrict__ dout,
   const float du = dout[2 * gi], dv = dout[2 * gi + 1];
   float dx = du * er.x - dv * er.y, dy = du * er.y + dv * er.x;
   const float nrm = sqrtf(dx * dx + dy * dy);
-  if (nrm > 0.25f) { dx *= 0.25f / nrm; dy *= 0.25f / nrm; }
+  if (nrm > max_move) { dx *= max_move / nrm; dy *= max_move / nrm; }
   if (!isfinite(dx) || !isfinite(dy)) { dx = 0.f; dy = 0.f; }
   const float2 nx = make_float2(x.x + dx, x.y + dy);
   P.x32[gi] = nx;
@@ -539,32 +659,33 @@ cudaError_t mlp_targets(const StandaloneParams &p, const double *xbefore, float 
 }
 
 cudaError_t mlp_forward(const bf16 *wb, const float *params, const float *feat, int64_t rows, float *out, int sms,
-                        cudaStream_t s) {
+                        cudaStream_t s, float *trace) {
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFwdSmem);
+    cudaError_t e = cudaFuncSetAttribute(forward_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFwdSmem);
     if (e) return e;
     attr = true;
   }
   if (rows <= 0) return cudaSuccess;
-  const int64_t tiles = (rows + 15) / 16;
-  const int grid = (int)std::min<int64_t>((tiles + 3) / 4, (int64_t)sms * 2);
-  forward_kernel<<<grid, 128, kFwdSmem, s>>>(wb, params, feat, rows, out);
+  const int64_t tiles = (rows + TM - 1) / TM;
+  const int grid = (int)std::min<int64_t>(tiles, (int64_t)sms);
+  forward_tc_kernel<<<grid, TM, kFwdSmem, s>>>(wb, params, feat, rows, out, trace);
   return cudaGetLastError();
 }
 
 int mlp_train_blocks(int sms) { return sms; }
 
 cudaError_t mlp_grad(const bf16 *wb, const float *params, const float *feat, const float *target, int64_t rows,
-                     float *part, float *lpart, float *grad, float *loss, int sms, cudaStream_t s) {
+                     float *part, float *lpart, float *grad, float *loss, int sms, cudaStream_t s, float *fwd_trace,
+                     float *bwd_trace) {
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(train_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTrainSmem);
+    cudaError_t e = cudaFuncSetAttribute(train_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTrainSmem);
     if (e) return e;
     attr = true;
   }
   const int nb = mlp_train_blocks(sms);
-  train_kernel<<<nb, 128, kTrainSmem, s>>>(wb, params, feat, target, rows, part, lpart);
+  train_tc_kernel<<<nb, TM, kTrainSmem, s>>>(wb, params, feat, target, rows, part, lpart, fwd_trace, bwd_trace);
   grad_reduce_kernel<<<nblk(NPAR, 256), 256, 0, s>>>(part, nb, grad, lpart, rows, loss);
   return cudaGetLastError();
 }
@@ -576,8 +697,8 @@ cudaError_t mlp_adam(float *params, float *m, float *v, const float *grad, bf16 
   return cudaGetLastError();
 }
 
-cudaError_t mlp_apply(const StandaloneParams &p, const float *dout, float2 *backup, cudaStream_t s) {
-  if (p.total > 0) apply_kernel<<<nblk(p.total, 256), 256, 0, s>>>(p, dout, backup);
+cudaError_t mlp_apply(const StandaloneParams &p, const float *dout, float2 *backup, float max_move, cudaStream_t s) {
+  if (p.total > 0) apply_kernel<<<nblk(p.total, 256), 256, 0, s>>>(p, dout, backup, max_move);
   return cudaGetLastError();
 }
 

@@ -58,7 +58,8 @@ _EXPORTS = ["pecc_config_default", "pecc_create", "pecc_destroy", "pecc_set_radi
             "pecc_adjust_container", "pecc_sed_config_default", "pecc_sed_create", "pecc_sed_destroy",
             "pecc_sed_last_error", "pecc_sed_set_radius", "pecc_sed_start", "pecc_sed_set_state", "pecc_sed_iterate",
             "pecc_sed_prepare", "pecc_sed_descend", "pecc_sed_select", "pecc_sed_get", "pecc_sed_context",
-            "pecc_frame_run", "pecc_set_list_dump"]
+            "pecc_frame_run", "pecc_set_list_dump", "pecc_warm_start_ex", "pecc_mlp_forward_trace",
+            "pecc_mlp_grad_trace"]
 NOALLOC_MAX_N = 4096
 ENERGY_STAGE_BYTES = 96 * 1024  # PECC_ENERGY_STAGE_BYTES
 
@@ -135,6 +136,9 @@ def load(build_if_missing: bool = True):
         "pecc_frame_run": (st, [vp, vp, vp, C.c_uint64, C.c_int32, C.c_int32, C.c_double, C.c_int32, vp, vp, vp,
                                 vp]),
         "pecc_set_list_dump": (st, [vp, C.c_int32, vp, vp, vp]),
+        "pecc_warm_start_ex": (st, [vp, vp, C.c_int32, C.c_double, vp]),
+        "pecc_mlp_forward_trace": (st, [vp, vp, C.c_int64, vp, vp]),
+        "pecc_mlp_grad_trace": (st, [vp, vp, vp, C.c_int64, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -236,6 +240,27 @@ class MLP:
         self._check(self._L.pecc_mlp_grad(self.h, _ptr(feat.contiguous()), _ptr(target.contiguous()), feat.shape[0],
                                           _ptr(g), _ptr(loss)), "pecc_mlp_grad")
         return g, loss
+
+    def forward_trace(self, feat):
+        """pecc_mlp_forward_trace: (out [rows, 2], trace [rows, 3, 128] of the bf16 hidden activations)."""
+        feat = feat.contiguous()
+        out = torch.empty((feat.shape[0], 2), dtype=torch.float32, device=feat.device)
+        tr = torch.empty((feat.shape[0], 3, 128), dtype=torch.float32, device=feat.device)
+        self._check(self._L.pecc_mlp_forward_trace(self.h, _ptr(feat), feat.shape[0], _ptr(out), _ptr(tr)),
+                    "pecc_mlp_forward_trace")
+        return out, tr
+
+    def grad_trace(self, feat, target):
+        """pecc_mlp_grad_trace: (grad, loss, forward trace [rows, 3, 128], backward trace [rows, 4, 128]:
+        dZ3, dZ2, dZ1, then dO (2) and the outputs (2))."""
+        g = torch.empty(self.num_params, dtype=torch.float32, device=feat.device)
+        loss = torch.empty(1, dtype=torch.float32, device=feat.device)
+        ft = torch.empty((feat.shape[0], 3, 128), dtype=torch.float32, device=feat.device)
+        bt = torch.empty((feat.shape[0], 4, 128), dtype=torch.float32, device=feat.device)
+        self._check(self._L.pecc_mlp_grad_trace(self.h, _ptr(feat.contiguous()), _ptr(target.contiguous()),
+                                                feat.shape[0], _ptr(g), _ptr(loss), _ptr(ft), _ptr(bt)),
+                    "pecc_mlp_grad_trace")
+        return g, loss, ft, bt
 
     def train_step(self, feat, target, lr):
         loss = torch.empty(1, dtype=torch.float32, device=feat.device)
@@ -422,9 +447,10 @@ class Context:
         self._check(self._L.pecc_targets(self.h, _ptr(xbefore.contiguous()), _ptr(t)), "pecc_targets")
         return t
 
-    def warm_start(self, mlp, rounds=1):
+    def warm_start(self, mlp, rounds=1, max_move=0.25):
         acc = torch.zeros(self.num, dtype=torch.int32, device=self.dev)
-        self._check(self._L.pecc_warm_start(self.h, mlp.h, int(rounds), _ptr(acc)), "pecc_warm_start")
+        self._check(self._L.pecc_warm_start_ex(self.h, mlp.h, int(rounds), float(max_move), _ptr(acc)),
+                    "pecc_warm_start_ex")
         return acc
 
     def adjust_container(self, R, lambda0=1e-4, rounds=35, out=None, stats=None):
