@@ -578,7 +578,7 @@ static pecc_status plan_launch(pecc_ctx *ctx, int arith, int block = 0, int bps_
     for (int a = (arith == 3 ? 1 : arith); a <= (arith == 3 ? 2 : arith); ++a) {  // fused: both phases
       int k = D.k;
       if (a == 2 && ctx->cfg.polish_k > 0) k = std::min(ctx->cfg.polish_k, D.k);
-      need = std::max(need, descend_smem_need(a, D.n, k, a == 1 ? D.ncx_f : D.ncx, blk));
+      need = std::max(need, descend_smem_need(a, D.n, k, a == 1 ? D.ncx_f : D.ncx, blk, ctx->cfg.lbfgs_m));
       mand = std::max(mand, descend_smem_mandatory(a, k, blk));
     }
   }
@@ -850,7 +850,9 @@ pecc_status pecc_autotune(pecc_ctx *ctx, int32_t sweeps, uint64_t seed, int32_t 
   pecc_status err = PECC_OK;
   for (int bi = 0; bi < 3 && !err; ++bi) {
     for (int ti = 0; ti < 5 && !err; ++ti) {
-      if (blocks[bi] > descend_max_block(plan_arith)) continue;  // shapes the planned kernel can run
+      // shapes the planned kernel can run; the fused kernel's 512-thread instance serves launches of
+      // a few instances (its default plan), not the many-instance shapes searched here
+      if (blocks[bi] > (plan_arith == 3 ? 256 : descend_max_block(plan_arith))) continue;
       if ((err = plan_launch(ctx, arith, blocks[bi], targets[ti]))) break;
       if (ctx->lc[arith].bps < targets[ti]) continue;  // that many blocks do not fit an SM
       ctx->lc_ready = true;

@@ -33,7 +33,7 @@ cudaError_t launch_descend(const DescendVariant &v, const DescendParams &p, int 
   return cudaLaunchKernel(v.fn, dim3(grid), dim3(block), args, p.smem_bytes, s);
 }
 
-int descend_max_block(int arith) { return arith == 1 ? 512 : 256; }
+int descend_max_block(int arith) { return (arith == 1 || arith == 3) ? 512 : 256; }
 
 // Shared-memory bytes without a global fallback: the per-warp partials of the first reduction of
 // a batch step and the k batch rings.
@@ -43,15 +43,15 @@ size_t descend_smem_mandatory(int arith, int k, int block) {
   return al(sc * (size_t)(block / 32) * kPA) + al(4 * (size_t)k * kRingInts);
 }
 
-// Shared-memory bytes the working set of an instance of n circles (k batches) asks for, in the
-// order the kernel carves it.
-size_t descend_smem_need(int arith, int n, int k, int ncx, int block) {
+// Shared-memory bytes the working set of an instance of n circles (k batches, m secant pairs)
+// asks for, in the order the kernel carves it.
+size_t descend_smem_need(int arith, int n, int k, int ncx, int block, int m) {
   const size_t pos = arith == 1 ? 8 : 16, vec = arith == 0 ? 16 : 8, sc = arith == 0 ? 8 : 4;
   auto al = [](size_t b) { return (b + 15) & ~size_t(15); };
   const size_t cells = 4 * (2 * (size_t)ncx * ncx + 2);
   size_t b = descend_smem_mandatory(arith, k, block) + al(sc * (size_t)k * kBasis * kBasis) + al(pos * n) +
              al(4 * (size_t)(n + 1)) + al(2 * (size_t)(8 * n + 64)) + 3 * al(vec * n) + 2 * al(pos * n) +
-             (cells <= pos * (size_t)n ? 0 : al(cells));
+             (cells <= pos * (size_t)n ? 0 : al(cells)) + 2 * al(vec * (size_t)(m + 1) * n);
   return b;
 }
 

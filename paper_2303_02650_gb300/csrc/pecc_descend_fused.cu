@@ -4,8 +4,10 @@
 
 namespace pecc {
 
-// 128 registers (two 256-thread or four 128-thread blocks per SM) and 96 (five 128-thread blocks).
-static const DescendVariant kVarFused[] = {descend_fused_variant<256, 2>(), descend_fused_variant<128, 5>()};
+// 128 registers (two 256-thread or four 128-thread blocks per SM), 96 (five 128-thread blocks), and
+// one 512-thread block per SM (a few large instances, each block alone on its SM).
+static const DescendVariant kVarFused[] = {descend_fused_variant<256, 2>(), descend_fused_variant<128, 5>(),
+                                           descend_fused_variant<512, 1>()};
 
 int descend_variants_fused(const DescendVariant **v) {
   *v = kVarFused;

@@ -19,9 +19,10 @@
 //     pair push when the curvature condition holds.
 //
 // The instance's working set (coordinates, gradients, direction, neighbor lists,
-// cell scratch, Gram matrices) is carved out of dynamic shared memory as far as it
-// fits, the rest falls back to global memory; the secant pairs stay in global
-// memory (read coalesced, L2-resident for the instances in flight).
+// cell scratch, Gram matrices, and last the secant pairs) is carved out of dynamic shared
+// memory as far as it fits, the rest falls back to global memory; with thousands of instances
+// in flight the secant pairs stay in global memory (read coalesced, L2-resident), a block alone
+// on its SM holds them on chip.
 //
 // The direction is computed in "vector-free" form (Chen, Wang, Zhou, Burges,
 // "Large-scale L-BFGS using MapReduce", NIPS 2014): the two-loop recursion is
@@ -208,8 +209,10 @@ __device__ __forceinline__ void descend_instance(const DescendParams &P, Smem<A,
   const size_t ncells = 2 * (size_t)G.nc * G.nc + 2;
   int32_t *cells = (ncells * sizeof(int32_t) <= (size_t)n * sizeof(PP)) ? (int32_t *)xb
                                                                        : cv.take<int32_t>(ncells, P.cells + D.cell_off);
-  VV *Sv = (VV *)P.S + (int64_t)mm * D.off;
-  VV *Yv = (VV *)P.Y + (int64_t)mm * D.off;
+  // the secant pairs last: on chip when the block's share holds them (few instances per launch, a
+  // block alone on its SM), else in global memory; they carry nothing between descent calls
+  VV *Sv = cv.take<VV>((size_t)mm * n, (VV *)P.S + (int64_t)mm * D.off);
+  VV *Yv = cv.take<VV>((size_t)mm * n, (VV *)P.Y + (int64_t)mm * D.off);
   int32_t *perm = P.perm + D.off;
   // the partition keys borrow the list storage (8 n bytes) before the first build
   uint64_t *skey = (col_s && (size_t)cap_s * 2 >= (size_t)n * 8) ? (uint64_t *)col_s : P.skey + D.off;

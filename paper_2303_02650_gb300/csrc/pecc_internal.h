@@ -106,7 +106,7 @@ cudaError_t launch_descend_fused(const DescendVariant &v, const DescendParams &p
                                  int block, cudaStream_t s);
 cudaError_t launch_descend(const DescendVariant &v, const DescendParams &p, int grid, int block, cudaStream_t s);
 int descend_max_block(int arith);
-size_t descend_smem_need(int arith, int n, int k, int ncx, int block);
+size_t descend_smem_need(int arith, int n, int k, int ncx, int block, int m);
 size_t descend_smem_mandatory(int arith, int k, int block);
 
 // Standalone kernels (pecc_kernels.cu).
