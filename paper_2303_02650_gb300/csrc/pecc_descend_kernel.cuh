@@ -97,7 +97,11 @@ __device__ __forceinline__ void reduce_sm(Smem<A, W> &S, int &buf, typename A::a
   __syncthreads();
   acc_t sa = S.rs[buf][0];
   vec_t sm = S.rm[buf][0];
-  for (int u = 1; u < nw; ++u) { sa += S.rs[buf][u]; sm = max(sm, S.rm[buf][u]); }
+  // the loads of every warp's partial are independent: unrolled to the block's warp bound so that
+  // they are all in flight, the additions keep the warp order
+#pragma unroll
+  for (int u = 1; u < W; ++u)
+    if (u < nw) { sa += S.rs[buf][u]; sm = max(sm, S.rm[buf][u]); }
   a = sa;
   m = sm;
   buf ^= 1;
@@ -425,12 +429,16 @@ __device__ __forceinline__ void descend_instance(const DescendParams &P, Smem<A,
       if (warp == 0) {
         for (int qv = lane; qv < nch * 32; qv += 32) {
           vec_t t = 0;
-          for (int u = 0; u < nw; ++u) t += pa[u * kPA + qv];
+#pragma unroll
+          for (int u = 0; u < W; ++u)
+            if (u < nw) t += pa[u * kPA + qv];
           S.ob[qv] = t;
         }
         if (lane == 0) {
           acc_t t = 0;
-          for (int u = 0; u < nw; ++u) t += S.rs[rbuf][u];
+#pragma unroll
+          for (int u = 0; u < W; ++u)
+            if (u < nw) t += S.rs[rbuf][u];
           S.eA = t;
         }
         __syncwarp();
@@ -453,28 +461,26 @@ __device__ __forceinline__ void descend_instance(const DescendParams &P, Smem<A,
             }
           }
           __syncwarp();
-          if (lane == 0) {
-            if (push) {
-              int c = ring[0];
-              if (c < P.m) {
+          if (push) {
+            const int c = ring[0];
+            if (c < P.m) {
+              // the new stage slot: the lowest physical slot not in the ring once st joins it
+              const unsigned inring =
+                  __reduce_or_sync(0xffffffffu, lane < c ? (1u << ring[2 + lane]) : 0u) | (1u << st);
+              __syncwarp();
+              if (lane == 0) {
                 ring[2 + c] = st;
                 ring[0] = c + 1;
-                int fr = 0;  // first slot not in the ring
-                for (; fr < mm; ++fr) {
-                  bool used = false;
-                  for (int u = 0; u <= c; ++u) used |= (ring[2 + u] == fr);
-                  if (!used) break;
-                }
-                ring[1] = fr;
-              } else {
-                int ev = ring[2];
-                for (int u = 0; u + 1 < c; ++u) ring[2 + u] = ring[3 + u];
-                ring[2 + c - 1] = st;
-                ring[1] = ev;
+                ring[1] = __ffs(~inring) - 1;
               }
+            } else if (lane == 0) {
+              int ev = ring[2];
+              for (int u = 0; u + 1 < c; ++u) ring[2 + u] = ring[3 + u];
+              ring[2 + c - 1] = st;
+              ring[1] = ev;
             }
-            ring[2 + kMaxSlots] = 0;
           }
+          if (lane == 0) ring[2 + kMaxSlots] = 0;
           __syncwarp();
         }
         const int count = ring[0];
