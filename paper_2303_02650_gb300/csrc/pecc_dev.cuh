@@ -153,8 +153,9 @@ __device__ __forceinline__ void warp_reduce_scatter(T (&v)[NV]) {
   }
 }
 
-// Inclusive prefix sum of a[0..len) in place (int32), whole block.
-__device__ inline void block_scan_inplace(int32_t *a, int len, int32_t *sh /*>=33 ints*/) {
+// Inclusive prefix sum of a[0..len) in place (int32), whole block; copy (may be null) receives the
+// same sums.
+__device__ inline void block_scan_inplace(int32_t *a, int len, int32_t *sh /*>=33 ints*/, int32_t *copy = nullptr) {
   const int T = blockDim.x, t = threadIdx.x, lane = t & 31, w = t >> 5, nw = T >> 5;
   int ch = (len + T - 1) / T;
   int lo = min(len, t * ch), hi = min(len, lo + ch);
@@ -179,7 +180,10 @@ __device__ inline void block_scan_inplace(int32_t *a, int len, int32_t *sh /*>=3
   }
   __syncthreads();
   int32_t run = incl - s + (w > 0 ? sh[w - 1] : 0);
-  for (int i = lo; i < hi; ++i) { run += a[i]; a[i] = run; }
+  if (copy)
+    for (int i = lo; i < hi; ++i) { run += a[i]; a[i] = run; copy[i] = run; }
+  else
+    for (int i = lo; i < hi; ++i) { run += a[i]; a[i] = run; }
   __syncthreads();
 }
 
@@ -243,15 +247,16 @@ __device__ void cta_cell_sort(const v2<T> *__restrict__ x, int n, const CellGrid
     atomicAdd(&cstart[key + 1], 1);
   }
   __syncthreads();
-  block_scan_inplace(cstart + 1, ncell, sh);
-  for (int c = t; c < ncell; c += T_) cfill[c] = cstart[c];
-  __syncthreads();
+  // the scan leaves the cell starts in cstart[1..] and, shifted by one, the fill cursors in cfill
+  // (cfill[c] = cstart[c]: cell 0 starts at 0)
+  if (t == 0) cfill[0] = 0;
+  block_scan_inplace(cstart + 1, ncell, sh, cfill + 1);
   for (int i = t; i < n; i += T_) {
     int p = atomicAdd(&cfill[ckey[i]], 1);
     corder[p] = i;
   }
   __syncthreads();
-  // stable order: sort every cell's members by index
+  // stable order: sort every cell's members by index, then their coordinates in that order
   for (int c = t; c < ncell; c += T_) {
     int lo = cstart[c], hi = cstart[c + 1];
     for (int a = lo + 1; a < hi; ++a) {
@@ -259,9 +264,8 @@ __device__ void cta_cell_sort(const v2<T> *__restrict__ x, int n, const CellGrid
       while (b >= lo && corder[b] > v) { corder[b + 1] = corder[b]; --b; }
       corder[b + 1] = v;
     }
+    for (int a = lo; a < hi; ++a) xs[a] = x[corder[a]];
   }
-  __syncthreads();
-  for (int q = t; q < n; q += T_) xs[q] = x[corder[q]];
   __syncthreads();
 }
 
