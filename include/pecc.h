@@ -25,7 +25,7 @@
  *    example a torch CUDA tensor's data_ptr()); *_host are host pointers.
  *  - Every call is ordered on the context's CUDA stream and returns after
  *    enqueueing, except those that read something back and so synchronise the
- *    stream: pecc_set_radius (the radii size the cell grids), pecc_neighbor_count,
+ *    stream: pecc_neighbor_count,
  *    pecc_export_neighbors, pecc_autotune, pecc_phase_times, pecc_solve_host,
  *    pecc_destroy; pecc_sed_create, pecc_sed_set_radius, pecc_sed_iterate (every
  *    check_every iterations), pecc_sed_destroy, pecc_frame_run, pecc_mlp_destroy.
@@ -154,10 +154,12 @@ pecc_status pecc_destroy(pecc_ctx *ctx);
 
 /* Container radii R of the problem statement (Sec. 3.1; the container constraint of Eq. 2 and the
  * wall depth of Eq. 3 use them): R_dev = device double[num_instances], each R finite and > 0.
- * Synchronises, unlike the stream-ordered calls of the descent: the radii are read back to the
- * host, where they size each instance's cell grid (cells per side, which bound the shared-memory
- * plan of the descent kernels and the cell-table allocation) and are checked (PECC_ERR_ARG for a
- * bad radius).  Call it once per set of radii, before the descents. */
+ * Stream-ordered and asynchronous: a kernel copies the radii and sizes each instance's cell grid
+ * on the device (the cell tables were allocated at pecc_create for the largest grid an instance
+ * can get, max(16, ceil(2 sqrt(n))) cells per side), so R_dev must stay valid until the stream
+ * has run the call.  A radius that is not finite and > 0 is not an argument error (it is not read
+ * on the host): its instance gets R = NaN, and its energies, descents (status
+ * PECC_DESC_NONFINITE) and feasibility checks (max_overlap NaN) say so. */
 pecc_status pecc_set_radius(pecc_ctx *ctx, const double *R_dev);
 
 /* Coordinates: xy_dev = device double[2 * sum n].  FP32 contexts round them to binary32. */

@@ -44,8 +44,9 @@ struct pecc_ctx {
   int32_t *corder = nullptr, *corder_s = nullptr, *cells = nullptr;
   int64_t *nnz = nullptr;
   char *stage = nullptr;  // per-instance staging of pecc_solve_host (R, outputs)
-  size_t cells_cap = 0;
   bool radius_set = false;
+  bool radius_host_known = false;  // radius_host holds the radii of the last pecc_solve_host
+  std::vector<double> radius_host;
   int lists_prec = -1;  // precision of the standalone lists: 0 FP64, 1 FP32
   int block = 0, bps = 0, grid = 0, block_build = 256;
   // per arithmetic (0 FP64, 1 FP32, 2 polish) and 3 = FP32 descent + polish fused in one kernel
@@ -225,7 +226,7 @@ pecc_status pecc_create(const pecc_config *cfg, void *stream, pecc_ctx **out) {
   const size_t vecs = fp64 ? sizeof(double) : sizeof(float);
   ctx->desc_h.resize(ctx->num);
   ctx->k.resize(ctx->num);
-  int64_t off = 0, rp_off = 0, col_off = 0, col_s_off = 0, gram_off = 0, meta_off = 0;
+  int64_t off = 0, rp_off = 0, col_off = 0, col_s_off = 0, gram_off = 0, meta_off = 0, cell_off = 0;
   for (int q = 0; q < ctx->num; ++q) {
     InstDesc &D = ctx->desc_h[q];
     std::memset(&D, 0, sizeof D);
@@ -244,13 +245,19 @@ pecc_status pecc_create(const pecc_config *cfg, void *stream, pecc_ctx **out) {
     D.col_s_off = col_s_off;
     D.gram_off = gram_off;
     D.meta_off = meta_off;
+    D.cell_off = cell_off;
     D.R = 0.0;
+    D.ncx = D.ncx_f = 1;  // until pecc_set_radius
+    D.inv_cs = 1.0;
+    D.inv_f = 1.f;
     off += n;
     rp_off += 2 * (int64_t)(n + 1);
     col_off += 2 * (int64_t)D.cap;
     col_s_off += D.cap;
     gram_off += (int64_t)k * kBasis * kBasis;
     meta_off += (int64_t)k * kMetaInts;
+    const int cap_c = cell_grid_cap(n);  // the cell table of the largest grid the instance can get
+    cell_off += 2 * (int64_t)cap_c * cap_c + 2;
   }
   pecc_status s;
 #define ALC(ptr, T, count)                                   \
@@ -291,6 +298,7 @@ pecc_status pecc_create(const pecc_config *cfg, void *stream, pecc_ctx **out) {
   ALC(ctx->corder, int32_t, total);
   ALC(ctx->corder_s, int32_t, total);
   ALC(ctx->nnz, int64_t, ctx->num + 1);
+  ALC(ctx->cells, int32_t, cell_off);
   ALC(ctx->stage, char, (size_t)ctx->num * 32);
   if (!ctx->big.empty()) {
     int occ = 0, nmax_big = 0, kmax = 1;
@@ -324,6 +332,9 @@ pecc_status pecc_create(const pecc_config *cfg, void *stream, pecc_ctx **out) {
     return bail(fail(ctx, PECC_ERR_CUDA, "upload inst_of"));
   if (ctx->num > 0 && cudaMemcpy(ctx->order, order.data(), sizeof(int32_t) * ctx->num, cudaMemcpyHostToDevice))
     return bail(fail(ctx, PECC_ERR_CUDA, "upload order"));
+  if (ctx->num > 0 &&
+      cudaMemcpy(ctx->desc, ctx->desc_h.data(), sizeof(InstDesc) * ctx->num, cudaMemcpyHostToDevice))
+    return bail(fail(ctx, PECC_ERR_CUDA, "upload instance descriptors"));
   if (cudaMemset(ctx->out, 0, sizeof(InstOut) * std::max(ctx->num, 1)) ||
       cudaMemset(ctx->rp_s, 0, sizeof(int32_t) * (total + ctx->num)) ||
       cudaMemset(ctx->x64, 0, sizeof(double2) * std::max<int64_t>(total, 1)))
@@ -355,7 +366,6 @@ pecc_status pecc_destroy(pecc_ctx *ctx) {
   for (int i = 0; i < 4; ++i)
     if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
   for (void *p : ctx->allocs) cudaFree(p);
-  if (ctx->cells) cudaFree(ctx->cells);
   delete ctx;
   return PECC_OK;
 }
@@ -374,49 +384,16 @@ pecc_status pecc_selftest_grid_barrier(int64_t timeout_ns, int32_t *failed_host,
 
 const char *pecc_last_error(pecc_ctx *ctx) { return ctx ? ctx->err.c_str() : g_create_err.c_str(); }
 
-static void cell_grid(double R, double l_cut, int n, double *inv, int *nc, double margin = 1.0 / 1048576.0) {
-  host_cell_grid(R, l_cut, n, inv, nc, margin);
-}
-
 pecc_status pecc_set_radius(pecc_ctx *ctx, const double *R_dev) {
   if (!ctx) return PECC_ERR_ARG;
   if (ctx->num == 0) return PECC_OK;
   if (!R_dev) return fail(ctx, PECC_ERR_ARG, "R_dev is NULL");
-  std::vector<double> R(ctx->num);
-  CK(cudaMemcpyAsync(R.data(), R_dev, sizeof(double) * ctx->num, cudaMemcpyDeviceToHost, ctx->stream));
-  CK(cudaStreamSynchronize(ctx->stream));
-  size_t cells = 0;
-  for (int q = 0; q < ctx->num; ++q) {
-    if (!(R[q] > 0.0) || !std::isfinite(R[q])) return fail(ctx, PECC_ERR_ARG, "R[%d] must be finite and > 0", q);
-    InstDesc &D = ctx->desc_h[q];
-    D.R = R[q];
-    cell_grid(R[q], ctx->cfg.l_cut, D.n, &D.inv_cs, &D.ncx);
-    {
-      double invf;
-      int ncf;
-      cell_grid(R[q], ctx->cfg.l_cut, D.n, &invf, &ncf, 1.0 / 1024.0);
-      // round the binary32 inverse side down so the side only grows
-      float f = (float)invf;
-      if ((double)f > invf) f = nextafterf(f, 0.0f);
-      D.inv_f = f;
-      D.ncx_f = std::min(ncf, D.ncx);
-    }
-    D.cell_off = (int64_t)cells;
-    cells += 2 * (size_t)D.ncx * D.ncx + 2;
-  }
-  if (cells > ctx->cells_cap) {
-    if (ctx->cells) cudaFree(ctx->cells);
-    ctx->cells = nullptr;
-    CK(cudaMalloc(&ctx->cells, cells * sizeof(int32_t)));
-    ctx->cells_cap = cells;
-  }
-  CK(cudaMemcpyAsync(ctx->desc, ctx->desc_h.data(), sizeof(InstDesc) * ctx->num, cudaMemcpyHostToDevice,
-                     ctx->stream));
-  CK(cudaStreamSynchronize(ctx->stream));
+  // the radii and each instance's cell grids are written on the device, in stream order; the cell
+  // tables were sized at create for the largest grid an instance can get
+  CK(launch_set_radius(ctx->desc, R_dev, ctx->num, ctx->cfg.l_cut, ctx->stream));
   ctx->radius_set = true;
+  ctx->radius_host_known = false;
   ctx->lists_prec = -1;
-  ctx->lc_ready = false;
-  if (ctx->graph) { cudaGraphExecDestroy(ctx->graph); ctx->graph = nullptr; }
   return PECC_OK;
 }
 
@@ -578,7 +555,8 @@ static pecc_status plan_launch(pecc_ctx *ctx, int arith, int block = 0, int bps_
     for (int a = (arith == 3 ? 1 : arith); a <= (arith == 3 ? 2 : arith); ++a) {  // fused: both phases
       int k = D.k;
       if (a == 2 && ctx->cfg.polish_k > 0) k = std::min(ctx->cfg.polish_k, D.k);
-      need = std::max(need, descend_smem_need(a, D.n, k, a == 1 ? D.ncx_f : D.ncx, blk, ctx->cfg.lbfgs_m));
+      // the grid's size is known on the device only: plan for the largest it can be
+      need = std::max(need, descend_smem_need(a, D.n, k, cell_grid_cap(D.n), blk, ctx->cfg.lbfgs_m));
       mand = std::max(mand, descend_smem_mandatory(a, k, blk));
     }
   }
@@ -1166,15 +1144,13 @@ pecc_status pecc_solve_host(pecc_ctx *ctx, const double *R_host, uint64_t seed, 
   int32_t *dit = (int32_t *)(ctx->stage + 24 * (size_t)ctx->num);    // [num]
   int32_t *dst = dit + ctx->num;                                      // [num]
   CK(cudaMemcpyAsync(dR, R_host, sizeof(double) * ctx->num, cudaMemcpyHostToDevice, ctx->stream));
-  bool same = ctx->radius_set;
-  if (same) {
-    std::vector<double> cur(ctx->num);
-    for (int q = 0; q < ctx->num; ++q) cur[q] = ctx->desc_h[q].R;
-    same = std::memcmp(cur.data(), R_host, sizeof(double) * ctx->num) == 0;
-  }
+  const bool same = ctx->radius_set && ctx->radius_host_known &&
+                    std::memcmp(ctx->radius_host.data(), R_host, sizeof(double) * ctx->num) == 0;
   pecc_status s;
   if (!same) {
     if ((s = pecc_set_radius(ctx, dR))) return s;
+    ctx->radius_host.assign(R_host, R_host + ctx->num);
+    ctx->radius_host_known = true;
   }
   if ((s = pecc_init_random(ctx, seed))) return s;
   if ((s = pecc_descend(ctx, nullptr, nullptr))) return s;

@@ -250,6 +250,7 @@ __device__ __forceinline__ void descend_instance(const DescendParams &P, Smem<A,
     bad |= !(isfinite((float)v.x) && isfinite((float)v.y));
     xw[p] = v;
   }
+  bad |= !(D.R > 0.0 && isfinite(D.R));  // a radius pecc_set_radius could not accept
   bad = __syncthreads_or(bad);
 
   int status = 3;  // max_iter unless something else ends the run

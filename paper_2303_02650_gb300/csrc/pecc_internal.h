@@ -12,14 +12,21 @@
 
 namespace pecc {
 
-// Cell grid of one instance (host side): side l_cut (1 + margin), ncx = ceil(2R / side), capped at
-// max(16, ceil(2 sqrt(n))) cells per side (the side then grows to 2R / ncx).
-inline void host_cell_grid(double R, double l_cut, int n, double *inv, int *nc, double margin = 1.0 / 1048576.0) {
+// Cells per side the grid of an instance of n circles has at most: max(16, ceil(2 sqrt(n))).
+__host__ __device__ inline int cell_grid_cap(int n) {
+  const int cap = (int)ceil(2.0 * sqrt((double)n));
+  return cap < 16 ? 16 : cap;
+}
+
+// Cell grid of one instance (the same arithmetic on the host and on the device, every operation
+// correctly rounded): side l_cut (1 + margin), ncx = ceil(2R / side), capped at cell_grid_cap(n)
+// cells per side (the side then grows to 2R / ncx).
+__host__ __device__ inline void host_cell_grid(double R, double l_cut, int n, double *inv, int *nc,
+                                               double margin = 1.0 / 1048576.0) {
   double cs = l_cut * (1.0 + margin);
   double iv = 1.0 / cs;
   double w = ceil((2.0 * R) * iv);
-  int cap = (int)ceil(2.0 * sqrt((double)n));
-  if (cap < 16) cap = 16;
+  const int cap = cell_grid_cap(n);
   int c = (w >= 1.0) ? (int)(w > 65535.0 ? 65535.0 : w) : 1;
   if (c > cap) {
     c = cap;
@@ -27,6 +34,19 @@ inline void host_cell_grid(double R, double l_cut, int n, double *inv, int *nc, 
   }
   *inv = iv;
   *nc = c;
+}
+
+// The binary32 grid of the FP32 descent for an instance whose binary64 grid has ncx cells per side:
+// side l_cut (1 + 2^-10), its inverse rounded down to binary32 (so the side only grows), at most
+// ncx cells per side.
+__host__ __device__ inline void f32_cell_grid(double R, double l_cut, int n, int ncx, float *inv_f, int *ncx_f) {
+  double invf;
+  int ncf;
+  host_cell_grid(R, l_cut, n, &invf, &ncf, 1.0 / 1024.0);
+  float f = (float)invf;
+  if ((double)f > invf) f = nextafterf(f, 0.0f);
+  *inv_f = f;
+  *ncx_f = ncf < ncx ? ncf : ncx;
 }
 
 // Message of the last failed call that has no context (read by pecc_last_error(NULL)).
@@ -210,7 +230,9 @@ struct StandaloneParams {
 cudaError_t launch_init(const StandaloneParams &p, uint64_t seed, int mode, int prec, cudaStream_t s);
 cudaError_t launch_set_positions(const StandaloneParams &p, const double *xy, int prec, cudaStream_t s);
 cudaError_t launch_get_positions(const StandaloneParams &p, double *xy, int from32, cudaStream_t s);
-cudaError_t launch_set_radius(InstDesc *desc, const double *R, int num, cudaStream_t s);
+// Radii and cell grids of every instance from device radii (stream-ordered); a radius that is not
+// finite and > 0 leaves R = NaN and a one-cell grid.
+cudaError_t launch_set_radius(InstDesc *desc, const double *R, int num, double l_cut, cudaStream_t s);
 cudaError_t launch_build(const StandaloneParams &p, int prec, int force, int32_t *rebuilt, int32_t *status,
                          int block, cudaStream_t s);
 cudaError_t launch_energy_grad(const StandaloneParams &p, int eval, double *E, void *grad, void *ecirc,

@@ -63,9 +63,29 @@ __global__ void get_pos_kernel(StandaloneParams P, double *__restrict__ xy, int 
   xy[2 * gi + 1] = v.y;
 }
 
-__global__ void set_radius_kernel(InstDesc *desc, const double *__restrict__ R, int num) {
-  int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q < num) desc[q].R = R[q];
+__global__ void set_radius_kernel(InstDesc *desc, const double *__restrict__ R, int num, double l_cut) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= num) return;
+  InstDesc &D = desc[q];
+  const double r = R[q];
+  double inv;
+  int nc;
+  float invf;
+  int ncf;
+  if (r > 0.0 && isfinite(r)) {
+    host_cell_grid(r, l_cut, D.n, &inv, &nc);
+    f32_cell_grid(r, l_cut, D.n, nc, &invf, &ncf);
+    D.R = r;
+  } else {  // the instance's energies, descents and checks come out NaN (status PECC_DESC_NONFINITE)
+    host_cell_grid(1.0, l_cut, D.n, &inv, &nc);
+    f32_cell_grid(1.0, l_cut, D.n, nc, &invf, &ncf);
+    nc = ncf = 1;
+    D.R = __longlong_as_double(0x7ff8000000000000ll);
+  }
+  D.inv_cs = inv;
+  D.ncx = nc;
+  D.inv_f = invf;
+  D.ncx_f = ncf;
 }
 
 // ----------------------------------------------------------------- build ----
@@ -368,8 +388,8 @@ cudaError_t launch_get_positions(const StandaloneParams &p, double *xy, int from
   return cudaGetLastError();
 }
 
-cudaError_t launch_set_radius(InstDesc *desc, const double *R, int num, cudaStream_t s) {
-  if (num > 0) set_radius_kernel<<<blocks_for(num, 128), 128, 0, s>>>(desc, R, num);
+cudaError_t launch_set_radius(InstDesc *desc, const double *R, int num, double l_cut, cudaStream_t s) {
+  if (num > 0) set_radius_kernel<<<blocks_for(num, 128), 128, 0, s>>>(desc, R, num, l_cut);
   return cudaGetLastError();
 }
 

@@ -31,6 +31,7 @@ def test_asynchronous_and_synchronising_calls():
             c.descend()  # first use: graph capture
             s.synchronize()
             xy = c.get_positions()
+            R_dev = torch.as_tensor(R, dtype=torch.float64, device="cuda")
             asynchronous = {
                 "pecc_init_random": lambda: c.init_random(5),
                 "pecc_set_positions": lambda: c.set_positions(xy),
@@ -41,6 +42,7 @@ def test_asynchronous_and_synchronising_calls():
                 "pecc_get_stats": c.get_stats,
                 "pecc_rebuild_neighbors": lambda: c.rebuild_neighbors(force=True),
                 "pecc_check_feasible": c.check_feasible,
+                "pecc_set_radius": lambda: c.set_radius(R_dev),
             }
             for call in asynchronous.values():  # first use of every output size in the allocator's cache
                 call()
@@ -53,7 +55,6 @@ def test_asynchronous_and_synchronising_calls():
             c.rebuild_neighbors(force=True)
             c.energy_grad()  # the standalone lists are current: energy + gradient is asynchronous too
             synchronising = {
-                "pecc_set_radius": lambda: c.set_radius(R),
                 "pecc_neighbor_count": c.neighbor_count,
                 "pecc_solve_host": lambda: c.solve_host(R, 9, want_xy=False),
             }
@@ -64,3 +65,25 @@ def test_asynchronous_and_synchronising_calls():
                 call()
                 assert s.query(), f"{name} returned with work pending"
         s.synchronize()
+
+
+def test_bad_radius_marks_its_instance(orc):
+    """A radius that is not finite and > 0 is not read on the host: its instance's descent ends
+    with status 5 (non-finite) and its feasibility check gives NaN, the other instances are
+    unaffected and match the oracle's check."""
+    torch, pecc = need_gpu()
+    n = np.array([300, 200, 120], dtype=np.int32)
+    R = np.array([synth.radius(300, 0.8), float("nan"), synth.radius(120, 0.8)])
+    with pecc.Context(n, precision=pecc.FP32_POLISH64) as c:
+        c.set_radius(np.where(np.isnan(R), -1.0, R))
+        c.set_radius(R)
+        c.init_random(3)
+        iters, status = c.descend()
+        feas, mo = c.check_feasible()
+        xy = c.get_positions().cpu().numpy()
+    status, feas, mo = status.cpu().numpy(), feas.cpu().numpy(), mo.cpu().numpy()
+    assert status[1] == 5 and np.isnan(mo[1]) and feas[1] == 0
+    off = np.concatenate([[0], np.cumsum(n)])
+    for q in (0, 2):
+        assert status[q] in (0, 1, 2, 3)
+        assert mo[q] == orc.max_overlap(xy[off[q]:off[q + 1]], float(R[q]))[0]
