@@ -83,6 +83,25 @@ def cfg_fields(cfg):
     return out
 
 
+# The paper's own runtimes for this path (context: other hardware and settings).  Average GBO
+# convergence time of one descent from a random layout, 1000 runs per n: the table of Sec. 6.5
+# comparing the non-batch descent (k = 1) with the best batch number; dense per-batch BFGS, l_cut 4,
+# square initial layout at the best-known radius; C++ (g++ 5.4.0) on an Intel Xeon E5-2650 v3.
+PAPER_DESCENT_S = {100: (0.09, 1, 0.09), 200: (0.49, 1, 0.49), 300: (1.23, 3, 1.09), 400: (2.43, 3, 1.89),
+                   500: (4.04, 5, 2.72), 600: (7.17, 7, 4.74), 700: (9.90, 5, 5.48), 800: (13.35, 6, 7.19), 900: (17.35, 5, 8.73), 1000: (24.97, 6, 11.46)}
+
+
+def paper_context(n, ms_per_step):
+    """The paper's per-descent times for the workload's sizes beside this run's device time per
+    descent (the step's time over its instances, so for a batch the amortised time)."""
+    lo, hi = int(np.min(n)), int(np.max(n))
+    rows = {str(k): {"T_k1_s": v[0], "best_k": v[1], "T_best_k_s": v[2]} for k, v in PAPER_DESCENT_S.items()
+            if lo - 50 <= k <= hi + 50}
+    return {"source": "paper, Sec. 6.5 table of GBO convergence times (average of 1000 descents per n)",
+            "hardware": "Intel Xeon E5-2650 v3, C++ (g++ 5.4.0); dense BFGS, l_cut 4, best-known radius",
+            "per_n": rows, "this_run_ms_per_descent": round(ms_per_step / max(1, len(n)), 4)}
+
+
 def oracle_settings(args):
     """The descent settings of the workload that the FP64 oracle also has (k, m, step cap), so that
     the CPU baseline and the reference arm run the same algorithm as the GPU arm."""
@@ -1259,6 +1278,7 @@ def run_ours(args, rank, world, local):
         "energy_grad_roofline": eg,
         "plain_fp64": plain,
         "error_vs_oracle": err_orc,
+        "paper_context": paper_context(n, ms_total / args.steps),
         "e2e": {"value": round(e2e_feas / (e2e_ms / 1e3), 3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": (4 if prec == 0 else 5) * args.steps + (2 if prec == 2 else 1) * args.steps * int(big),

@@ -91,3 +91,11 @@ def test_oracle_runs_the_workload_settings():
     assert bench.oracle_settings(_args("c3")) == {"k": 2, "m": 5, "step_max": 0.3}
     assert bench.oracle_settings(_args("c3", cfg=["lbfgs_m=10"])) == {"k": 2, "m": 10, "step_max": 0.3}
     assert bench.oracle_settings(_args("c1")) == {"k": 0}
+
+
+def test_paper_runtimes_match_the_golden_table():
+    """The paper's per-descent times quoted beside the bench line are the printed table's values."""
+    path = os.path.join(ROOT, "tests", "golden", "gbo_batch_numbers.txt")
+    rows = [ln.split() for ln in open(path) if ln.strip() and not ln.startswith("#")]
+    table = {int(r[0]): (float(r[1]), int(r[2]), float(r[3])) for r in rows}
+    assert bench.PAPER_DESCENT_S == table
