@@ -136,6 +136,15 @@ typedef struct {
                                pairs.  Needs PECC_FP64 and instances below 16384 circles; the
                                first pecc_descend allocates sum over batches of (2 |B_p|)^2
                                doubles (32 MB for n = 1000, k = 1).  lbfgs_m is then unused; 0 */
+    double list_outer;      /* the descent (instances below 16384 circles) keeps an outer list of
+                               the pairs closer than l_cut + list_outer, built from the cell grid,
+                               and makes every list of Sec. 4.3 (each ANM and Verlet rebuild) by
+                               filtering it, as long as twice the largest displacement since the
+                               outer list's build stays below list_outer (else the outer list is
+                               rebuilt first).  The filter applies the same predicate to the same
+                               coordinates, so the lists are the same set as a build from the cell
+                               grid; only their order within a row can differ.  0 = every rebuild
+                               from the cell grid, else in [2^-9, 64]; 0.5 */
 } pecc_config;
 
 /* Fill *cfg with the defaults listed above (num_instances = 0, n = NULL). */

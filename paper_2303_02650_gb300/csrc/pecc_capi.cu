@@ -163,6 +163,7 @@ void pecc_config_default(pecc_config *c) {
   c->polish_stall_rel = 1e-2;
   c->polish_stall_window = 100;
   c->fuse_phases = 1;
+  c->list_outer = 0.5;
 }
 
 static int default_k(int n) { return n < 300 ? 1 : (n < 500 ? 3 : 5); }
@@ -192,6 +193,8 @@ pecc_status pecc_create(const pecc_config *cfg, void *stream, pecc_ctx **out) {
   if (cfg->polish_k < 0 || cfg->polish_k > kMaxK) return fail(nullptr, PECC_ERR_ARG, "polish_k must be in 0..64");
   if (cfg->smem_per_block < 0) return fail(nullptr, PECC_ERR_ARG, "smem_per_block must be >= 0");
   if (cfg->qn_dense != 0 && cfg->qn_dense != 1) return fail(nullptr, PECC_ERR_ARG, "qn_dense must be 0 or 1");
+  if (!(cfg->list_outer == 0.0 || (cfg->list_outer >= 1.0 / 512.0 && cfg->list_outer <= 64.0)))
+    return fail(nullptr, PECC_ERR_ARG, "list_outer must be 0 or in [2^-9, 64]");
   if (cfg->qn_dense && cfg->precision != PECC_FP64)
     return fail(nullptr, PECC_ERR_ARG, "qn_dense needs precision PECC_FP64");
   if (cfg->block_threads != 0 && (cfg->block_threads < 32 || cfg->block_threads % 32 ||
@@ -556,7 +559,8 @@ static pecc_status plan_launch(pecc_ctx *ctx, int arith, int block = 0, int bps_
       int k = D.k;
       if (a == 2 && ctx->cfg.polish_k > 0) k = std::min(ctx->cfg.polish_k, D.k);
       // the grid's size is known on the device only: plan for the largest it can be
-      need = std::max(need, descend_smem_need(a, D.n, k, cell_grid_cap(D.n), blk, ctx->cfg.lbfgs_m));
+      need = std::max(need, descend_smem_need(a, D.n, k, cell_grid_cap(D.n), blk, ctx->cfg.lbfgs_m,
+                                                   ctx->cfg.list_outer > 0.0));
       mand = std::max(mand, descend_smem_mandatory(a, k, blk));
     }
   }
@@ -626,6 +630,7 @@ static DescendParams dparams(pecc_ctx *c, int phase) {
   p.e_tol = f.e_tol; p.gsum_tol = f.gsum_tol; p.c1 = f.c1; p.curv_eps = f.curv_eps; p.polish_gate = f.polish_gate;
   p.m = f.lbfgs_m; p.max_iter = f.max_iter; p.max_trials = f.max_trials; p.anm = f.anm; p.partition = f.partition;
   p.part_seed = f.partition_seed;
+  p.list_outer = f.list_outer;
   p.stall_rel = (phase == 2) ? f.polish_stall_rel : f.stall_rel;
   p.stall_window = (phase == 2) ? f.polish_stall_window : f.stall_window;
   p.t0 = c->t0;

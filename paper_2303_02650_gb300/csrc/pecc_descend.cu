@@ -45,13 +45,14 @@ size_t descend_smem_mandatory(int arith, int k, int block) {
 
 // Shared-memory bytes the working set of an instance of n circles (k batches, m secant pairs)
 // asks for, in the order the kernel carves it.
-size_t descend_smem_need(int arith, int n, int k, int ncx, int block, int m) {
+size_t descend_smem_need(int arith, int n, int k, int ncx, int block, int m, bool outer) {
   const size_t pos = arith == 1 ? 8 : 16, vec = arith == 0 ? 16 : 8, sc = arith == 0 ? 8 : 4;
   auto al = [](size_t b) { return (b + 15) & ~size_t(15); };
   const size_t cells = 4 * (2 * (size_t)ncx * ncx + 2);
   size_t b = descend_smem_mandatory(arith, k, block) + al(sc * (size_t)k * kBasis * kBasis) + al(pos * n) +
-             al(4 * (size_t)(n + 1)) + al(2 * (size_t)(8 * n + 64)) + 3 * al(vec * n) + 2 * al(pos * n) +
-             (cells <= pos * (size_t)n ? 0 : al(cells)) + 2 * al(vec * (size_t)(m + 1) * n);
+             al(4 * (size_t)(n + 1)) + (outer ? al(4 * (size_t)n) : 0) + al(2 * (size_t)(8 * n + 64)) +
+             3 * al(vec * n) + 2 * al(pos * n) + (cells <= pos * (size_t)n ? 0 : al(cells)) +
+             2 * al(vec * (size_t)(m + 1) * n) + (outer ? al(2 * (size_t)(kOuterPerCircle * n + 64)) : 0);
   return b;
 }
 

@@ -190,6 +190,10 @@ __device__ __forceinline__ void descend_instance(const DescendParams &P, Smem<A,
   vec_t *gram = cv.take<vec_t>((size_t)k * kBasis * kBasis, (vec_t *)P.gram + D.gram_off);
   PP *xw = cv.take<PP>(n, (PP *)((double2 *)P.xw + D.off));
   int32_t *rp = cv.take<int32_t>(n + 1, P.rp + D.rp_off);
+  // two-level lists: the rows of the filtered lists start where the outer list's rows start and
+  // end at re[p]; with one level re = rp + 1 (CSR)
+  bool two = P.list_outer > 0.0;
+  int32_t *re = two ? cv.take<int32_t>(n, P.rp + D.rp_off + n + 1) : rp + 1;
   // neighbor indices are 16-bit inside the descent (instances of at most 65535 circles)
   const int cap_s = min(D.cap, 8 * n + 64);  // about 5 neighbors per circle in practice
   uint16_t *col_s = cv.take<uint16_t>(cap_s, (uint16_t *)nullptr);
@@ -217,6 +221,32 @@ __device__ __forceinline__ void descend_instance(const DescendParams &P, Smem<A,
   // block alone on its SM), else in global memory; they carry nothing between descent calls
   VV *Sv = cv.take<VV>((size_t)mm * n, (VV *)P.S + (int64_t)mm * D.off);
   VV *Yv = cv.take<VV>((size_t)mm * n, (VV *)P.Y + (int64_t)mm * D.off);
+  // the outer list last: its rows are read once per filtered rebuild
+  uint16_t *const colL_g = col_g + 2 * (size_t)D.cap;
+  uint16_t *colL_s = nullptr, *colL = nullptr;
+  int capL = 0;
+  CellGrid GL = G;
+  pos_t lc2L = 0;
+  if (two) {
+    const int capL_s = min(D.cap, kOuterPerCircle * n + 64);
+    colL_s = cv.take<uint16_t>(capL_s, (uint16_t *)nullptr);
+    colL = colL_s ? colL_s : colL_g;
+    capL = colL_s ? capL_s : D.cap;
+    const double lb = P.l_cut + P.list_outer;
+    double inv;
+    int nc;
+    host_cell_grid(D.R, lb, n, &inv, &nc);
+    if (A::kId == 1) {
+      float invf;
+      int ncf;
+      f32_cell_grid(D.R, lb, n, nc, &invf, &ncf);
+      GL = CellGrid{D.R, inv, (float)D.R, invf, ncf, true};
+    } else {
+      GL = CellGrid{D.R, inv, 0.f, 0.f, nc, false};
+    }
+    lc2L = (pos_t)(lb * lb);
+    if (GL.nc > G.nc) { two = false; re = rp + 1; }  // its cell table must fit the scratch
+  }
   int32_t *perm = P.perm + D.off;
   // the partition keys borrow the list storage (8 n bytes) before the first build
   uint64_t *skey = (col_s && (size_t)cap_s * 2 >= (size_t)n * 8) ? (uint64_t *)col_s : P.skey + D.off;
@@ -262,9 +292,73 @@ __device__ __forceinline__ void descend_instance(const DescendParams &P, Smem<A,
   acc_t E = 0;
   int rbuf = 0;  // buffer of the next single-barrier reduction (block-uniform)
 
-  // one neighbor build into the block's list storage; moves the lists to global memory when
-  // they outgrow their shared-memory share; false when even the global capacity is exceeded
+  // the outer list at the current layout (rows rp, entries colL); the filtered lists take the
+  // same room, so they move to global memory with it when it outgrows their share
+  auto build_outer = [&]() -> bool {
+    int tot = cta_build_neighbors<pos_t, uint16_t>(xw, n, GL, lc2L, ckey, corder, cells, xo, rp, colL, capL, S.sh,
+                                                   nullptr, false);
+    if (tot > capL && colL_s && colL == colL_s) {
+      colL = colL_g;
+      capL = D.cap;
+      tot = cta_build_neighbors<pos_t, uint16_t>(xw, n, GL, lc2L, ckey, corder, cells, xo, rp, colL, capL, S.sh,
+                                                 nullptr, false);
+    }
+    if (tot > capL) return false;
+    if (tot > cap && col_s && col == col_s) {
+      col = col_g;
+      cap = D.cap;
+    }
+    return tot <= cap;
+  };
+  // the lists of Sec. 4.3 from the outer list: the predicate of a cell-grid build on the same
+  // coordinates, so the same set (rows in the outer list's order), and the same digest
+  auto filter = [&]() {
+    if (tid == 0) S.hash = 0ull;
+    __syncthreads();
+    unsigned long long h = 0ull;
+    for (int p = tid; p < n; p += T) {
+      const PP xi = xw[p];
+      const int t1 = rp[p + 1];
+      int w = rp[p];
+      for (int t = w; t < t1; t += 8) {
+        int jj[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) jj[u] = (t + u < t1) ? (int)colL[t + u] : -1;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int j = jj[u];
+          if (j >= 0 && nbr_pred(xi, xw[j], lc2)) {
+            col[w++] = (uint16_t)j;
+            h += mix32((uint32_t)p * 0x9E3779B1u ^ (uint32_t)j);
+          }
+        }
+      }
+      re[p] = w;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) h += __shfl_xor_sync(0xffffffffu, h, o);
+    if (lane == 0) atomicAdd(&S.hash, h);
+    __syncthreads();
+  };
+  // bound on the largest displacement since the outer list's build: the sum of the largest
+  // displacements between the list builds since then
+  sc_t DL = 0;
+  bool outer_ok = false;
+  const sc_t outer_room = (sc_t)(P.list_outer - 1.0 / 1024.0);
+  // one list build into the block's list storage; moves the lists to global memory when they
+  // outgrow their shared-memory share; false when even the global capacity is exceeded
   auto build = [&]() -> bool {
+    if (two) {
+      const sc_t Dnow = DL + Dmax;
+      if (outer_ok && sc_t(2) * Dnow < outer_room) {
+        DL = Dnow;
+      } else {
+        outer_ok = build_outer();
+        DL = 0;
+        if (!outer_ok) { two = false; re = rp + 1; }  // one level from here on
+      }
+      if (two) { filter(); return true; }
+    }
     int tot = cta_build_neighbors<pos_t, uint16_t>(xw, n, G, lc2, ckey, corder, cells, xo, rp, col, cap, S.sh,
                                                    &S.hash, false);
     if (tot > cap && col_s && col == col_s) {
@@ -295,7 +389,7 @@ __device__ __forceinline__ void descend_instance(const DescendParams &P, Smem<A,
     for (int p = tid; p < n; p += T) {
       PP xi = xw[p];
       acc_t e = 0;
-      for (int t = rp[p]; t < rp[p + 1]; ++t) {
+      for (int t = rp[p]; t < re[p]; ++t) {
         int j = col[t];
         if (j >= p) continue;
         vec_t fx, fy;
@@ -364,7 +458,7 @@ __device__ __forceinline__ void descend_instance(const DescendParams &P, Smem<A,
         if (!fresh) {
           vec_t gx = 0, gy = 0;
           acc_t ei = 0;
-          for (int t = rp[pos]; t < rp[pos + 1]; ++t) {
+          for (int t = rp[pos]; t < re[pos]; ++t) {
             int j = col[t];
             vec_t fx, fy;
             acc_t d = A::pair(xi, xw[j], fx, fy);
@@ -608,7 +702,7 @@ __device__ __forceinline__ void descend_instance(const DescendParams &P, Smem<A,
             PP xi = xw[pos];
             vec_t gx = 0, gy = 0;
             acc_t ei = 0;
-            for (int t = rp[pos]; t < rp[pos + 1]; ++t) {
+            for (int t = rp[pos]; t < re[pos]; ++t) {
               int j = col[t];
               vec_t fx, fy;
               acc_t d = A::pair(xi, xw[j], fx, fy);
@@ -701,7 +795,7 @@ __device__ __forceinline__ void descend_instance(const DescendParams &P, Smem<A,
     const int64_t stride = P.dump_stride;
     for (int pos = tid; pos < n; pos += T) {
       const int i = perm[pos];
-      const int b0 = lists_ok ? rp[pos] : 0, len_ = lists_ok ? rp[pos + 1] - b0 : 0;
+      const int b0 = lists_ok ? rp[pos] : 0, len_ = lists_ok ? re[pos] - b0 : 0;
       const bool ok = lists_ok && len_ <= P.dump_stride;
       P.dump_cnt[D.off + i] = ok ? len_ : -1;
       if (ok)

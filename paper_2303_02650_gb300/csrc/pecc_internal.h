@@ -49,6 +49,10 @@ __host__ __device__ inline void f32_cell_grid(double R, double l_cut, int n, int
   *ncx_f = ncf < ncx ? ncf : ncx;
 }
 
+// Shared-memory share of a descent's outer neighbor list (list_outer > 0), in entries per circle;
+// an outer list that outgrows it lives in global memory.
+constexpr int kOuterPerCircle = 12;
+
 // Message of the last failed call that has no context (read by pecc_last_error(NULL)).
 void set_global_error(const char *msg);
 
@@ -75,6 +79,7 @@ struct DescendParams {
   double l_cut, rebuild_disp, step_max, e_tol, gsum_tol, c1, curv_eps, polish_gate;
   int m, max_iter, max_trials, anm, partition;
   uint64_t part_seed;     // random partition (3): Philox key
+  double list_outer;     // > 0: reach of the outer list beyond l_cut (two-level lists)
   double stall_rel;       // FP32 phase: stop when E fell by less than this over stall_window sweeps
   int stall_window;
   const long long *t0;    // %globaltimer at the start of the call (written by stamp_kernel)
@@ -126,7 +131,7 @@ cudaError_t launch_descend_fused(const DescendVariant &v, const DescendParams &p
                                  int block, cudaStream_t s);
 cudaError_t launch_descend(const DescendVariant &v, const DescendParams &p, int grid, int block, cudaStream_t s);
 int descend_max_block(int arith);
-size_t descend_smem_need(int arith, int n, int k, int ncx, int block, int m);
+size_t descend_smem_need(int arith, int n, int k, int ncx, int block, int m, bool outer);
 size_t descend_smem_mandatory(int arith, int k, int block);
 
 // Standalone kernels (pecc_kernels.cu).

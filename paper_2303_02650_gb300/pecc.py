@@ -38,7 +38,7 @@ class Config(C.Structure):
                 ("stall_window", C.c_int32), ("polish_k", C.c_int32),
                 ("smem_per_block", C.c_int32), ("polish_stall_rel", C.c_double),
                 ("polish_stall_window", C.c_int32), ("fuse_phases", C.c_int32), ("partition_seed", C.c_uint64),
-                ("qn_dense", C.c_int32)]
+                ("qn_dense", C.c_int32), ("list_outer", C.c_double)]
 
 
 class SedConfig(C.Structure):
