@@ -6,6 +6,8 @@
   layout whose lists no longer change.
 - Eq. 9's line search (Armijo with c1 and halving) and the stationary stop of Algorithm GBO: the
   hand-computed cases of the oracle's pins run on the GPU too.
+- Two-level lists: lists filtered from an outer list keep every count of the oracle, and an outer
+  list that overflows its capacity falls back to cell-grid builds.
 - The binary32 descent: the neighbor lists it builds itself (binary32 grid, binary32 predicate,
   16-bit indices in partition order) equal the oracle's brute force on the coordinates of that
   build, and a few binary32 sweeps follow the oracle's binary64 sweeps from the same binary32
@@ -56,6 +58,45 @@ def test_anm_and_trial_counters_match_oracle(orc, k, m, step_max, sweeps):
         assert out["iters"][q] == r.iters, q
         assert (out["builds"][q], out["changes"][q], out["trials"][q]) == (r.builds, r.changes, r.trials), q
         np.testing.assert_allclose(b, r.x, rtol=0, atol=1e-9 * float(R[q]))
+
+
+@pytest.mark.parametrize("outer", [0.0, 2.0 ** -9, 0.5, 1.5])
+def test_two_level_lists_keep_the_counts(orc, outer):
+    """The lists of Sec. 4.3 filtered from an outer list (cutoff l_cut + list_outer) are the sets a
+    cell-grid build gives: builds, changes and trials equal the oracle's for an outer reach that is
+    rebuilt at almost every list build (2^-9), the default (0.5), and one whose list can outgrow its
+    shared-memory share (1.5, about 12 entries per circle), and positions agree to 1e-9 R."""
+    torch, pecc = need_gpu()
+    n = np.array([300, 257, 640, 1000], dtype=np.int32)
+    R = _radii(n, 0.82)
+    out = _run(pecc, torch, n, R, seed=93, precision=0, k_batches=2, lbfgs_m=5, step_max=0.3, max_iter=8,
+               list_outer=outer)
+    for q, (a, b) in enumerate(zip(split(out["x0"], n), split(out["x"], n))):
+        r = orc.gbo(a, float(R[q]), k=2, m=5, step_max=0.3, max_iter=8)
+        assert out["iters"][q] == r.iters, q
+        assert (out["builds"][q], out["changes"][q], out["trials"][q]) == (r.builds, r.changes, r.trials), q
+        np.testing.assert_allclose(b, r.x, rtol=0, atol=1e-9 * float(R[q]))
+
+
+def test_two_level_lists_fall_back_when_the_outer_list_overflows():
+    """With room for 6 entries per circle the lists (about 5 per circle at density 0.82) fit but an
+    outer list of cutoff 3 (about 7) does not: the descent falls back to cell-grid builds from the
+    start, bit for bit the run with list_outer = 0; with the default room the two-level run orders
+    its rows differently, so its coordinates differ in the last bits (the fallback is what makes
+    the first pair equal)."""
+    torch, pecc = need_gpu()
+    n = np.array([1000, 640], dtype=np.int32)
+    R = _radii(n, 0.82)
+    kw = dict(seed=95, precision=0, k_batches=2, lbfgs_m=5, step_max=0.3, max_iter=6)
+    a = _run(pecc, torch, n, R, list_outer=0.5, nbr_capacity=6.0, **kw)
+    b = _run(pecc, torch, n, R, list_outer=0.0, nbr_capacity=6.0, **kw)
+    assert np.all(a["status"] == 3) and np.all(b["status"] == 3)
+    assert np.array_equal(a["x"], b["x"]) and np.array_equal(a["builds"], b["builds"])
+    c = _run(pecc, torch, n, R, list_outer=0.5, **kw)
+    d = _run(pecc, torch, n, R, list_outer=0.0, **kw)
+    assert np.array_equal(c["builds"], d["builds"]) and np.array_equal(c["changes"], d["changes"])
+    assert not np.array_equal(c["x"], d["x"])
+    np.testing.assert_allclose(c["x"], d["x"], rtol=0, atol=1e-9 * float(R.max()))
 
 
 def test_anm_deferral_doubles_on_stable_layout_gpu(orc):
@@ -163,7 +204,10 @@ def _rows(cnt, col, lo, hi):
 
 
 @pytest.mark.parametrize("cfg", [dict(max_iter=1), dict(max_iter=3, k_batches=2, lbfgs_m=5, step_max=0.3),
-                                 dict(max_iter=60, k_batches=2, lbfgs_m=5, step_max=0.3)])
+                                 dict(max_iter=60, k_batches=2, lbfgs_m=5, step_max=0.3),
+                                 dict(max_iter=60, k_batches=2, lbfgs_m=5, step_max=0.3, list_outer=0.0),
+                                 dict(max_iter=20, k_batches=2, lbfgs_m=5, step_max=0.3, list_outer=2.0 ** -9),
+                                 dict(max_iter=20, k_batches=2, lbfgs_m=5, step_max=0.3, list_outer=1.5)])
 def test_fp32_descent_lists_bit_exact(orc, cfg):
     """The lists the binary32 descent builds for itself (cell grid of side l_cut (1 + 2^-10) in
     binary32, the predicate s = dx dx + dy dy < l_cut^2 in binary32 without FMA, 16-bit indices in
