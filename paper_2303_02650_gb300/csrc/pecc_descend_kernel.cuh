@@ -107,6 +107,33 @@ __device__ __forceinline__ void reduce_sm(Smem<A, W> &S, int &buf, typename A::a
   buf ^= 1;
 }
 
+// Forces on circle pos from the entries col[t0 .. t1) of its row, added to (gx, gy), and its share
+// of the batch energy added to ei: the pairs with a circle outside the batch [b, e) or inside it
+// with a smaller index.  Two entries per step, so that the loads of both are in flight together;
+// the sums take the entries in row order, the values of one entry per step.
+template <class A, typename PP>
+__device__ __forceinline__ void row_terms(const PP xi, const uint16_t *__restrict__ col, int t0, int t1,
+                                          const PP *__restrict__ xw, int b, int e, int pos,
+                                          typename A::vec_t &gx, typename A::vec_t &gy, typename A::acc_t &ei) {
+  using vec_t = typename A::vec_t;
+  using acc_t = typename A::acc_t;
+  for (int t = t0; t < t1; t += 2) {
+    const bool two = t + 1 < t1;
+    const int j1 = col[t];
+    const int j2 = two ? (int)col[t + 1] : j1;
+    const PP x1 = xw[j1], x2 = xw[j2];
+    vec_t fx, fy;
+    acc_t d = A::pair(xi, x1, fx, fy);
+    gx += fx; gy += fy;
+    if (j1 < b || j1 >= e || j1 < pos) ei += d * d;
+    if (two) {
+      d = A::pair(xi, x2, fx, fy);
+      gx += fx; gy += fy;
+      if (j2 < b || j2 >= e || j2 < pos) ei += d * d;
+    }
+  }
+}
+
 // Bump allocator over dynamic shared memory; returns the fallback when the request does not fit.
 struct Carve {
   unsigned char *base;
@@ -389,13 +416,8 @@ __device__ __forceinline__ void descend_instance(const DescendParams &P, Smem<A,
     for (int p = tid; p < n; p += T) {
       PP xi = xw[p];
       acc_t e = 0;
-      for (int t = rp[p]; t < re[p]; ++t) {
-        int j = col[t];
-        if (j >= p) continue;
-        vec_t fx, fy;
-        acc_t d = A::pair(xi, xw[j], fx, fy);
-        e += d * d;
-      }
+      vec_t ux = 0, uy = 0;  // unused
+      row_terms<A, PP>(xi, col, rp[p], re[p], xw, 0, n, p, ux, uy, e);
       vec_t fx, fy;
       acc_t d0 = A::wall(xi, R, Rm1sq, fx, fy);
       a += e + d0 * d0;
@@ -458,13 +480,7 @@ __device__ __forceinline__ void descend_instance(const DescendParams &P, Smem<A,
         if (!fresh) {
           vec_t gx = 0, gy = 0;
           acc_t ei = 0;
-          for (int t = rp[pos]; t < re[pos]; ++t) {
-            int j = col[t];
-            vec_t fx, fy;
-            acc_t d = A::pair(xi, xw[j], fx, fy);
-            gx += fx; gy += fy;
-            if (j < b || j >= e || j < pos) ei += d * d;
-          }
+          row_terms<A, PP>(xi, col, rp[pos], re[pos], xw, b, e, pos, gx, gy, ei);
           vec_t fx, fy;
           acc_t d0 = A::wall(xi, R, Rm1sq, fx, fy);
           gx += fx; gy += fy;
@@ -702,13 +718,7 @@ __device__ __forceinline__ void descend_instance(const DescendParams &P, Smem<A,
             PP xi = xw[pos];
             vec_t gx = 0, gy = 0;
             acc_t ei = 0;
-            for (int t = rp[pos]; t < re[pos]; ++t) {
-              int j = col[t];
-              vec_t fx, fy;
-              acc_t d = A::pair(xi, xw[j], fx, fy);
-              gx += fx; gy += fy;
-              if (j < b || j >= e || j < pos) ei += d * d;
-            }
+            row_terms<A, PP>(xi, col, rp[pos], re[pos], xw, b, e, pos, gx, gy, ei);
             vec_t fx, fy;
             acc_t d0 = A::wall(xi, R, Rm1sq, fx, fy);
             gx += fx; gy += fy;
