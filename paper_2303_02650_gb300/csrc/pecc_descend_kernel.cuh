@@ -123,13 +123,13 @@ __device__ __forceinline__ void row_terms(const PP xi, const uint16_t *__restric
     const int j2 = two ? (int)col[t + 1] : j1;
     const PP x1 = xw[j1], x2 = xw[j2];
     vec_t fx, fy;
-    acc_t d = A::pair(xi, x1, fx, fy);
+    const auto d1 = A::pair(xi, x1, fx, fy);
     gx += fx; gy += fy;
-    if (j1 < b || j1 >= e || j1 < pos) ei += d * d;
+    if (j1 < b || j1 >= e || j1 < pos) ei += (acc_t)d1 * (acc_t)d1;
     if (two) {
-      d = A::pair(xi, x2, fx, fy);
+      const auto d2 = A::pair(xi, x2, fx, fy);
       gx += fx; gy += fy;
-      if (j2 < b || j2 >= e || j2 < pos) ei += d * d;
+      if (j2 < b || j2 >= e || j2 < pos) ei += (acc_t)d2 * (acc_t)d2;
     }
   }
 }

@@ -5,10 +5,11 @@
 //   Arith32  binary32 coordinates, pair math, gradient, energy accumulation
 //   Arith64  binary64 everywhere (the plain FP64 form)
 //   ArithMix binary64 coordinates, pair differences and the near-contact
-//            quantities 4 - l^2 and r^2 - (R-1)^2 (exact by Sterbenz' lemma
-//            where they cancel); binary32 for everything that only needs
-//            relative accuracy (the overlap depth from them, unit vectors,
-//            gradient, quasi-Newton vectors), binary64 energy sums.
+//            quantities 4 - l^2 (two fused multiply-adds) and r^2 - (R-1)^2
+//            (exact by Sterbenz' lemma where it cancels); binary32 for
+//            everything that only needs relative accuracy (the overlap depth
+//            from them, unit vectors, gradient, quasi-Newton vectors), binary64
+//            energy sums.
 #pragma once
 
 #include <cstdint>
@@ -452,21 +453,25 @@ struct ArithMix {
   using vec_t = float;
   using acc_t = double;
   static constexpr int kId = 2;
-  __device__ static __forceinline__ acc_t pair(double2 a, double2 b, float &fx, float &fy) {
-    double dx = a.x - b.x, dy = a.y - b.y;
-    double s = fma(dx, dx, dy * dy);
+  // 4 - l^2 = 4 - dy^2 - dx^2 by two fused multiply-adds (one rounding of size ulp64(4) / 2 at
+  // most, then the exact cancellation near contact and one rounding of the small result); its
+  // sign is the contact test, and everything after it is binary32.
+  __device__ static __forceinline__ float pair(double2 a, double2 b, float &fx, float &fy) {
+    const double dx = a.x - b.x, dy = a.y - b.y;
+    const float e = (float)fma(-dx, dx, fma(-dy, dy, 4.0));
     fx = 0.f; fy = 0.f;
-    if (!(s < 4.0)) return 0.0;
-    if (s > 1e-30) {
-      float e = (float)(4.0 - s);       // exact cancellation near contact
-      float rl = rsqrtf((float)s);
-      float l = (float)s * rl;
-      float d = e / (2.f + l);          // 2 - l = (4 - l^2) / (2 + l)
-      float c = -2.f * d * rl;
-      fx = c * (float)dx; fy = c * (float)dy;
-      return (double)d;
+    if (!(e > 0.f)) return 0.f;
+    const float dxf = (float)dx, dyf = (float)dy;
+    const float s = fmaf(dxf, dxf, dyf * dyf);
+    if (s > 1e-30f) {
+      const float rl = rsqrtf(s);
+      const float l = s * rl;
+      const float d = e / (2.f + l);    // 2 - l = (4 - l^2) / (2 + l)
+      const float c = -2.f * d * rl;
+      fx = c * dxf; fy = c * dyf;
+      return d;
     }
-    return 2.0;
+    return 2.f;
   }
   __device__ static __forceinline__ acc_t wall(double2 a, double R, double Rm1sq, float &fx, float &fy) {
     double r2 = fma(a.x, a.x, a.y * a.y);
