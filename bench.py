@@ -308,14 +308,14 @@ class Clocks:
 
 # DRAM traffic of the fused descent kernel per algorithmic byte, from one ncu capture on 1216
 # instances of the batch at the batch settings (profiles/descend_fused_kernel_1216inst_128x4.md:
-# dram__bytes_read.sum + dram__bytes_write.sum = 85.5 MB + 510.1 MB over the launch's 131.94 GB of
+# dram__bytes_read.sum + dram__bytes_write.sum = 94.7 MB + 877.9 MB over the launch's 131.22 GB of
 # algorithmic bytes, the byte model charging the context's m).  A full launch's traffic is that
 # ratio times its algorithmic bytes.  The figure holds for the kernel sources it was measured on:
 # once their hash changes the bench reports traffic as null.
 FUSED_TRAFFIC = {"sources": ["pecc_descend_kernel.cuh", "pecc_dev.cuh", "pecc_descend_fused.cu"], "k": 2,
                  "cfg": ["step_max=0.3", "polish_gate=0.00001", "stall_window=5", "polish_stall_window=50",
                          "lbfgs_m=5"],
-                 "sha256_16": "086b1e5454e79991", "dram_per_algorithmic_byte": (85499392 + 510110464) / 131942264784.0}
+                 "sha256_16": "d54cfc9f696c8573", "dram_per_algorithmic_byte": (94726144 + 877912320) / 131215464960.0}
 
 
 def fused_traffic(alg_bytes):
