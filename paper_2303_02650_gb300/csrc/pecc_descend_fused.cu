@@ -1,13 +1,13 @@
 // pecc_descend_fused.cu -- the fused instances of the descent kernel: the FP32 descent and the FP64
-// polish of each instance back to back in one block (own translation unit, compiled in parallel).
-#include "pecc_descend_kernel.cuh"
+// polish of each instance back to back in one block.  Each instance is compiled in a translation
+// unit of its own (pecc_descend_fused_*.cu), so that they compile in parallel.
+#include "pecc_internal.h"
 
 namespace pecc {
 
 // 128 registers (two 256-thread or four 128-thread blocks per SM), 96 (five 128-thread blocks), and
 // one 512-thread block per SM (a few large instances, each block alone on its SM).
-static const DescendVariant kVarFused[] = {descend_fused_variant<256, 2>(), descend_fused_variant<128, 5>(),
-                                           descend_fused_variant<512, 1>()};
+static const DescendVariant kVarFused[] = {descend_fused_256x2(), descend_fused_128x5(), descend_fused_512x1()};
 
 int descend_variants_fused(const DescendVariant **v) {
   *v = kVarFused;

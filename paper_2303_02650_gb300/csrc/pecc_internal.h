@@ -127,6 +127,10 @@ struct DescendVariant {
 int descend_variants(int arith, const DescendVariant **v);  // largest register budget first
 int descend_variants32(const DescendVariant **v);
 int descend_variants_fused(const DescendVariant **v);  // arith 3: FP32 descent + polish in one block
+// the compiled instances of the fused kernel, one translation unit each (they compile in parallel)
+DescendVariant descend_fused_256x2();
+DescendVariant descend_fused_128x5();
+DescendVariant descend_fused_512x1();
 cudaError_t launch_descend_fused(const DescendVariant &v, const DescendParams &p32, const DescendParams &p64, int grid,
                                  int block, cudaStream_t s);
 cudaError_t launch_descend(const DescendVariant &v, const DescendParams &p, int grid, int block, cudaStream_t s);
