@@ -27,6 +27,7 @@ struct pecc_ctx {
   InstDesc *desc = nullptr;
   InstOut *out = nullptr;
   int32_t *order = nullptr, *queue = nullptr, *inst_of = nullptr;
+  int32_t *eorder = nullptr;  // largest instance first, never rewritten (the standalone kernels' block order)
   long long *t0 = nullptr;
   float2 *x32 = nullptr;
   double2 *x64 = nullptr;
@@ -128,6 +129,7 @@ static StandaloneParams sparams(pecc_ctx *c) {
   p.xtmp2 = c->xo;
   p.l_cut = c->cfg.l_cut;
   p.rebuild_disp = c->cfg.rebuild_disp;
+  p.eorder = c->eorder;
   return p;
 }
 
@@ -272,6 +274,7 @@ pecc_status pecc_create(const pecc_config *cfg, void *stream, pecc_ctx **out) {
   ALC(ctx->desc, InstDesc, ctx->num);
   ALC(ctx->out, InstOut, ctx->num);
   ALC(ctx->order, int32_t, ctx->num);
+  ALC(ctx->eorder, int32_t, ctx->num);
   ALC(ctx->queue, int32_t, 5);  // descent phases 0..3, container adjustment 4
   ALC(ctx->t0, long long, 1);
   ALC(ctx->inst_of, int32_t, total);
@@ -333,7 +336,8 @@ pecc_status pecc_create(const pecc_config *cfg, void *stream, pecc_ctx **out) {
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return ctx->n[a] > ctx->n[b]; });
   if (total > 0 && cudaMemcpy(ctx->inst_of, inst_of.data(), sizeof(int32_t) * total, cudaMemcpyHostToDevice))
     return bail(fail(ctx, PECC_ERR_CUDA, "upload inst_of"));
-  if (ctx->num > 0 && cudaMemcpy(ctx->order, order.data(), sizeof(int32_t) * ctx->num, cudaMemcpyHostToDevice))
+  if (ctx->num > 0 && (cudaMemcpy(ctx->order, order.data(), sizeof(int32_t) * ctx->num, cudaMemcpyHostToDevice) ||
+                       cudaMemcpy(ctx->eorder, order.data(), sizeof(int32_t) * ctx->num, cudaMemcpyHostToDevice)))
     return bail(fail(ctx, PECC_ERR_CUDA, "upload order"));
   if (ctx->num > 0 &&
       cudaMemcpy(ctx->desc, ctx->desc_h.data(), sizeof(InstDesc) * ctx->num, cudaMemcpyHostToDevice))

@@ -372,19 +372,18 @@ struct Arith32 {
   using vec_t = float;
   using acc_t = float;
   static constexpr int kId = 1;
+  // Without branches: every lane of a warp takes the same instructions whether its pair is in
+  // contact or not (a list row holds both kinds), and the selects give the values of the case split.
   __device__ static __forceinline__ acc_t pair(float2 a, float2 b, float &fx, float &fy) {
     float dx = a.x - b.x, dy = a.y - b.y;
     float s = dx * dx + dy * dy;
-    fx = 0.f; fy = 0.f;
-    if (!(s < 4.f)) return 0.f;
-    if (s > 0.f) {
-      float rl = rsqrtf(s);
-      float d = 2.f - s * rl;
-      float c = -2.f * d * rl;
-      fx = c * dx; fy = c * dy;
-      return d > 0.f ? d : 0.f;
-    }
-    return 2.f;
+    const bool act = s < 4.f, pos = s > 0.f, ap = act && pos;
+    float rl = rsqrtf(pos ? s : 1.f);
+    float d = 2.f - s * rl;
+    float c = -2.f * d * rl;
+    fx = ap ? c * dx : 0.f;
+    fy = ap ? c * dy : 0.f;
+    return act ? (pos ? fmaxf(d, 0.f) : 2.f) : 0.f;
   }
   // container term: depth d_i0 and gradient 2 d_i0 c_i / |c_i|
   __device__ static __forceinline__ acc_t wall(float2 a, float R, float Rm1sq, float &fx, float &fy) {

@@ -234,6 +234,7 @@ struct StandaloneParams {
   void *xtmp;                 // per-circle double2 scratch
   void *xtmp2;                // another per-circle double2 scratch
   double l_cut, rebuild_disp;
+  const int32_t *eorder;      // instances, largest first: block b of a per-instance kernel takes eorder[b]
 };
 
 cudaError_t launch_init(const StandaloneParams &p, uint64_t seed, int mode, int prec, cudaStream_t s);

@@ -6,6 +6,10 @@ namespace pecc {
 
 namespace {
 
+// threads per block of the block-per-instance energy + gradient kernel (measured on the
+// 4096-instance batch's final layouts: 128 threads 41.2 us, 256 threads 43.3 us, 512 threads 49.5 us)
+constexpr int kEgBlock = 128;
+
 // ------------------------------------------------------------------ init ----
 // Circle i of instance q: Philox4x32-10, key (seed lo, seed hi), counter (i, attempt, q, 0);
 // (w0, w1) and (w2, w3) give two 53-bit uniforms u, v; candidate (R-1)(2u-1, 2v-1),
@@ -180,9 +184,11 @@ __global__ void __launch_bounds__(256) energy_grad_kernel(StandaloneParams P, in
 // coordinates are staged in shared memory by one coalesced read, so every neighbor gather is an
 // on-chip load; row pointers and lists stream through once, the gradient is written once, and the
 // energy is reduced in the block in a fixed order (deterministic) and written once.  Larger
-// instances are left to energy_grad_kernel + energy_reduce_kernel.
+// instances are left to energy_grad_kernel + energy_reduce_kernel.  Blocks take the instances
+// largest first (the last blocks to start are the shortest), kEgBlock threads each: sixteen
+// blocks share an SM.
 template <class A>
-__global__ void __launch_bounds__(256) energy_grad_block_kernel(StandaloneParams P, int stage_n,
+__global__ void __launch_bounds__(kEgBlock) energy_grad_block_kernel(StandaloneParams P, int stage_n,
                                                                 void *__restrict__ grad_, double *E) {
   using pos_t = typename A::pos_t;
   using vec_t = typename A::vec_t;
@@ -191,7 +197,7 @@ __global__ void __launch_bounds__(256) energy_grad_block_kernel(StandaloneParams
   using VV = v2<vec_t>;
   extern __shared__ __align__(16) unsigned char stage[];
   __shared__ acc_t red[32];
-  const int q = blockIdx.x;
+  const int q = P.eorder[blockIdx.x];
   const int n = P.desc[q].n;
   if (n > stage_n) return;  // the per-circle kernels' instance (uniform across the block)
   if (n == 0) {
@@ -272,7 +278,7 @@ __global__ void feasible_kernel(StandaloneParams P, int from32, double tol, uint
                                 double *max_overlap) {
   __shared__ int32_t sh[40];
   __shared__ double red[32];
-  const int q = blockIdx.x;
+  const int q = P.eorder[blockIdx.x];  // largest instance first
   const InstDesc D = P.desc[q];
   const int n = D.n;
   double2 *x = (double2 *)P.xtmp + D.off;
@@ -406,7 +412,7 @@ template <class A> static cudaError_t launch_eg_block(const StandaloneParams &p,
   cudaError_t e = cudaFuncSetAttribute(energy_grad_block_kernel<A>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
-  energy_grad_block_kernel<A><<<p.num, 256, smem, s>>>(p, stage_n, grad, E);
+  energy_grad_block_kernel<A><<<p.num, kEgBlock, smem, s>>>(p, stage_n, grad, E);
   return cudaGetLastError();
 }
 
