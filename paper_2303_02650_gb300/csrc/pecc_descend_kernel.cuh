@@ -663,30 +663,45 @@ __device__ __forceinline__ void descend_instance(const DescendParams &P, Smem<A,
           for (int u = tid; u < kBasis; u += T) S.coef[u] = (u == GI) ? vec_t(-1) : vec_t(0);
           __syncthreads();
         }
-        // ---- pass B: direction, g'd and the largest per-circle move
+        // ---- pass B: direction, g'd and the largest per-circle move.  Two positions per thread at a
+        // time, so that the secant-slot loads of both are in flight together; g'd takes the positions
+        // in the same order as one at a time.
         acc_t gdB = 0;
         vec_t dmB = 0;
         for (int round = 0; round < 2; ++round) {
           const unsigned used = S.used;
           gdB = 0;
           dmB = 0;
-          for (int pos = b + tid; pos < e; pos += T) {
-            VV gi = g[pos];
-            vec_t cg = S.coef[GI];
+          for (int pos = b + tid; pos < e; pos += 2 * T) {
+            const int p2 = pos + T;
+            const bool h2 = p2 < e;
+            const int q2 = h2 ? p2 : pos;
+            const VV gi = g[pos], gi2 = g[q2];
+            const vec_t cg = S.coef[GI];
             vec_t dx = cg * gi.x, dy = cg * gi.y;
+            vec_t dx2 = cg * gi2.x, dy2 = cg * gi2.y;
 #pragma unroll
             for (int a = 0; a < kMaxSlots; ++a) {
               if (a < mm && ((used >> a) & 1u)) {
                 const VV s_ = Sv[(int64_t)a * n + pos], y_ = Yv[(int64_t)a * n + pos];
+                const VV s2 = Sv[(int64_t)a * n + q2], y2 = Yv[(int64_t)a * n + q2];
                 const vec_t cs = S.coef[a], cy = S.coef[KS + a];
                 dx += cs * s_.x + cy * y_.x;
                 dy += cs * s_.y + cy * y_.y;
+                dx2 += cs * s2.x + cy * y2.x;
+                dy2 += cs * s2.y + cy * y2.y;
               }
             }
             VV dd; dd.x = dx; dd.y = dy;
             dv[pos] = dd;
             gdB += (acc_t)(gi.x * dx + gi.y * dy);
             dmB = max(dmB, dx * dx + dy * dy);
+            if (h2) {
+              VV d2; d2.x = dx2; d2.y = dy2;
+              dv[p2] = d2;
+              gdB += (acc_t)(gi2.x * dx2 + gi2.y * dy2);
+              dmB = max(dmB, dx2 * dx2 + dy2 * dy2);
+            }
           }
           reduce_sm<A, W>(S, rbuf, gdB, dmB);
           if (gdB < acc_t(0) || round == 1) break;
