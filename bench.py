@@ -32,6 +32,7 @@ from __future__ import annotations
 import argparse
 import datetime
 import json
+import math
 import os
 import subprocess
 import sys
@@ -1294,15 +1295,15 @@ def run_ours(args, rank, world, local):
         dist.destroy_process_group()
 
 
-def energy_grad_roofline(ctx, torch, n, R, copies=4, rounds=8):
+def energy_grad_roofline(ctx, torch, n, R, rounds=8, l2_bytes=129e6):
     """The standalone fused energy + gradient kernel over every circle of the batch, after a
     forced FP32 (or FP64) list build at the final layouts.
 
-    Timed two ways with CUDA events: launches back to back over `copies` contexts holding the same
-    layouts (their inputs together exceed L2, so each launch reads data the launches in between
-    have evicted), the events around all of them (the average launch duration); and one launch
-    after a 1 GB write that flushes L2, the events around it alone (that also counts the gap
-    between the event and the kernel's start)."""
+    Timed two ways with CUDA events: launches back to back over as many contexts holding the same
+    layouts as it takes for their inputs together to exceed L2 (at least four), so that each launch
+    reads data the launches in between have evicted, the events around all of them (the average
+    launch duration); and one launch after a 1 GB write that flushes L2, the events around it alone
+    (that also counts the gap between the event and the kernel's start)."""
     from paper_2303_02650_gb300 import pecc
 
     prec = ctx.precision
@@ -1310,6 +1311,18 @@ def energy_grad_roofline(ctx, torch, n, R, copies=4, rounds=8):
     ctx.rebuild_neighbors(force=True, eval=ev)
     nnz = ctx.neighbor_count()
     N, I = int(n.sum()), int(n.size)
+    pos = 16 if ev == 0 else 8
+    acc = 8 if ev == 0 else 4
+    # algorithmic bytes.  Instances whose coordinates fit the staging limit (one block each): read x
+    # and the row pointers, the column indices, write g, write E.  Larger ones (one thread per
+    # circle): also the instance id per circle, and the per-circle energy written and read back.
+    vec = pos  # the gradient has the coordinates' width (float2 / double2)
+    staged = n.astype(np.int64) * pos <= pecc.ENERGY_STAGE_BYTES
+    Ns, Nl = int(n[staged].sum()), int(n[~staged].sum())
+    nnz_s = nnz * Ns / max(1, N)
+    bytes_ = (Ns * (pos + 4 + vec) + 4 * nnz_s + 12 * int(staged.sum())
+              + Nl * (pos + 4 + 4 + vec + 2 * acc) + 4 * (nnz - nnz_s) + 12 * int((~staged).sum()))
+    copies = int(min(64, max(4, math.ceil(1.25 * l2_bytes / max(bytes_, 1.0)))))
     xy = ctx.get_positions()
     ctxs = [ctx]
     for _ in range(copies - 1):
@@ -1351,17 +1364,6 @@ def energy_grad_roofline(ctx, torch, n, R, copies=4, rounds=8):
         torch.cuda.synchronize()
         times.append(a.elapsed_time(b))
     ms_single = float(np.median(times[1:]))
-    pos = 16 if ev == 0 else 8
-    acc = 8 if ev == 0 else 4
-    # algorithmic bytes.  Instances whose coordinates fit the staging limit (one block each): read x
-    # and the row pointers, the column indices, write g, write E.  Larger ones (one thread per
-    # circle): also the instance id per circle, and the per-circle energy written and read back.
-    vec = pos  # the gradient has the coordinates' width (float2 / double2)
-    staged = n.astype(np.int64) * pos <= pecc.ENERGY_STAGE_BYTES
-    Ns, Nl = int(n[staged].sum()), int(n[~staged].sum())
-    nnz_s = nnz * Ns / max(1, N)
-    bytes_ = (Ns * (pos + 4 + vec) + 4 * nnz_s + 12 * int(staged.sum())
-              + Nl * (pos + 4 + 4 + vec + 2 * acc) + 4 * (nnz - nnz_s) + 12 * int((~staged).sum()))
     hbm, kind = peaks()
     gbs = bytes_ / (ms / 1e3) / 1e9
     kname = ("energy_grad_block_kernel (coordinates staged in shared memory)" if Nl == 0 else
@@ -1369,7 +1371,8 @@ def energy_grad_roofline(ctx, torch, n, R, copies=4, rounds=8):
     return {"kernel": kname, "achieved": round(gbs, 1), "peak": hbm,
             "unit": "GB/s", "frac": round(gbs / hbm, 4), "peak_kind": kind, "avg_launch_ms": round(ms, 4),
             "timing": f"{rounds} rounds of {len(ctxs)} launches back to back over {len(ctxs)} contexts with the same "
-                      f"layouts ({len(ctxs)} x the algorithmic bytes > L2), events around all",
+                      f"layouts ({len(ctxs)} x {bytes_ / 1e6:.1f} MB of algorithmic bytes > {l2_bytes / 1e6:.0f} MB of L2), "
+                      f"events around all",
             "single_launch_after_flush_ms": round(ms_single, 4),
             "single_launch_frac": round(bytes_ / (ms_single / 1e3) / 1e9 / hbm, 4),
             "algorithmic_bytes_per_launch": int(bytes_), "circles": N, "neighbor_entries": int(nnz),

@@ -172,12 +172,22 @@ __global__ void __launch_bounds__(256) energy_grad_kernel(StandaloneParams P, in
     ((acc_t *)ecirc_)[gi] = (acc_t)NAN;
     return;
   }
-  for (int t = lo; t < hi; ++t) {
-    int j = __ldg(cl + t);
+  // two entries per step (their index and coordinate loads in flight together); the sums take the
+  // entries in row order
+  for (int t = lo; t < hi; t += 2) {
+    const bool two = t + 1 < hi;
+    const int j1 = __ldg(cl + t);
+    const int j2 = two ? __ldg(cl + t + 1) : j1;
+    const PP x1 = x[j1], x2 = x[j2];
     vec_t fx, fy;
-    acc_t d = A::pair(xi, x[j], fx, fy);
+    const acc_t d1 = A::pair(xi, x1, fx, fy);
     gx += fx; gy += fy;
-    if (j < i) e += d * d;
+    if (j1 < i) e += d1 * d1;
+    if (two) {
+      const acc_t d2 = A::pair(xi, x2, fx, fy);
+      gx += fx; gy += fy;
+      if (j2 < i) e += d2 * d2;
+    }
   }
   vec_t fx, fy;
   acc_t d0 = A::wall(xi, R, Rm1sq, fx, fy);
@@ -272,15 +282,31 @@ __global__ void __launch_bounds__(kEgBlock) energy_grad_block_kernel(StandaloneP
 }
 
 // Per-instance sum of the per-circle energies (fixed order: deterministic), for the instances the
-// block kernel left (more than stage_n circles).
+// block kernel left (more than stage_n circles).  Each thread keeps kRed partial sums over
+// interleaved circles, so that kRed loads are in flight at a time, and adds them in a fixed order.
+constexpr int kRed = 8;
 template <typename acc_t>
-__global__ void energy_reduce_kernel(StandaloneParams P, int stage_n, const acc_t *__restrict__ ecirc, double *E) {
+__global__ void __launch_bounds__(1024) energy_reduce_kernel(StandaloneParams P, int stage_n,
+                                                             const acc_t *__restrict__ ecirc, double *E) {
   __shared__ acc_t sh[32];
   const int q = blockIdx.x;
   const InstDesc D = P.desc[q];
   if (D.n <= stage_n) return;
-  acc_t s = 0;
-  for (int i = threadIdx.x; i < D.n; i += blockDim.x) s += ecirc[D.off + i];
+  const acc_t *e = ecirc + D.off;
+  const int B = blockDim.x;
+  acc_t part[kRed];
+#pragma unroll
+  for (int u = 0; u < kRed; ++u) part[u] = 0;
+  for (int i0 = threadIdx.x; i0 < D.n; i0 += kRed * B) {
+#pragma unroll
+    for (int u = 0; u < kRed; ++u) {
+      const int i = i0 + u * B;
+      if (i < D.n) part[u] += e[i];
+    }
+  }
+  acc_t s = part[0];
+#pragma unroll
+  for (int u = 1; u < kRed; ++u) s += part[u];
   s = warp_sum(s);
   if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
   __syncthreads();
@@ -455,8 +481,8 @@ cudaError_t launch_energy_grad(const StandaloneParams &p, int eval, double *E, v
     if (eval == 0) energy_grad_kernel<Arith64><<<nb, 256, 0, s>>>(p, stage_n, grad, ecirc);
     else if (eval == 1) energy_grad_kernel<Arith32><<<nb, 256, 0, s>>>(p, stage_n, grad, ecirc);
     else energy_grad_kernel<ArithMix><<<nb, 256, 0, s>>>(p, stage_n, grad, ecirc);
-    if (eval == 1) energy_reduce_kernel<float><<<p.num, 256, 0, s>>>(p, stage_n, (const float *)ecirc, E);
-    else energy_reduce_kernel<double><<<p.num, 256, 0, s>>>(p, stage_n, (const double *)ecirc, E);
+    if (eval == 1) energy_reduce_kernel<float><<<p.num, 1024, 0, s>>>(p, stage_n, (const float *)ecirc, E);
+    else energy_reduce_kernel<double><<<p.num, 1024, 0, s>>>(p, stage_n, (const double *)ecirc, E);
   }
   return cudaGetLastError();
 }
