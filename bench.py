@@ -1423,7 +1423,7 @@ def run_reference(args, rank, world):
         return run_reference_ksweep(args, world)
     if args.workload == "c5":
         # the learned form's evaluation set, descended by the plain method (the oracle has no
-        # network: the plain descent is the learned form's fallback and the judge of its error)
+        # network: the plain descent is the learned form's fallback and decides whether its proposal is kept)
         n, R = synth.batch_manifest(1024, seed=10**6 + 7)
         desc = "learned form's evaluation set: 1024 fresh instances n~U{300..1000}, plain FP64 descent"
     else:
