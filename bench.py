@@ -1429,9 +1429,10 @@ def run_reference(args, rank, world):
     else:
         n, R, prec, desc = workload(args.workload)
     cores = os.cpu_count() or 1
-    # eight instances per thread and step: the threads take instances from one queue, so the
-    # ragged sizes balance out (with two per thread most threads idled behind the largest)
-    per_step = max(1, min(n.size, 8 * cores))
+    # 32 instances per thread and step: the threads take instances from one queue, so the ragged
+    # sizes balance out and few threads idle behind the step's last instance (with eight per thread
+    # a step's tail cost about a fifth of the throughput of one long queue, with two most of it)
+    per_step = max(1, min(n.size, 32 * cores))
     kw = oracle_settings(args) if args.workload != "c5" else {}
     # warm-up: the library and the thread pool, on the smallest instance of the workload, or on 50
     # circles where that is larger than 1000 (one 100000-circle descent takes minutes)
