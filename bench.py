@@ -1392,11 +1392,14 @@ def cpu_baseline(args, n, R, prec, budget_s=15.0):
     per = max(t1, 1e-3)
     count = int(max(1, min(n.size, budget_s * cores / per)))
     if n.size == 1:
+        # one instance: the GPU line solves it one descent at a time, and one oracle descent runs on
+        # one core, so the descents (different seeds) run one after another on one thread
         count = max(1, min(int(budget_s / per), 64))
         nn = np.repeat(n, count)
         RR = np.repeat(R, count)
-        t, out = oracle.solve_batch(nn, RR, args.seed, nthreads=cores, **kw)
-        sample = f"{count} runs of the single instance (different seeds), {cores} threads, settings {kw}"
+        cores = 1
+        t, out = oracle.solve_batch(nn, RR, args.seed, nthreads=1, **kw)
+        sample = f"{count} descents of the single instance (different seeds), one after another on 1 thread, settings {kw}"
     else:
         idx = rng_order[:count]
         t, out = oracle.solve_batch(n[idx], R[idx], args.seed, nthreads=cores, **kw)
