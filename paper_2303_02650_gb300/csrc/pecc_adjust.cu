@@ -127,12 +127,22 @@ __global__ void __launch_bounds__(kAdjT) adjust_kernel(AdjustParams P) {
         const double2 xi = x[i];
         GT gx = 0, gy = 0;
         double e = 0.0;
-        for (int t = rp[i]; t < rp[i + 1]; ++t) {
-          const int j = col[t];
+        // two entries per step (both coordinate loads in flight); the sums take the entries in row order
+        const int t1 = rp[i + 1];
+        for (int t = rp[i]; t < t1; t += 2) {
+          const bool two = t + 1 < t1;
+          const int j1 = col[t];
+          const int j2 = two ? col[t + 1] : j1;
+          const double2 x1 = x[j1], x2 = x[j2];
           GT fx, fy;
-          const double d = A::pair(xi, x[j], fx, fy);
+          const double d1 = A::pair(xi, x1, fx, fy);
           gx += fx; gy += fy;
-          if (j < i) e += d * d;
+          if (j1 < i) e += d1 * d1;
+          if (two) {
+            const double d2 = A::pair(xi, x2, fx, fy);
+            gx += fx; gy += fy;
+            if (j2 < i) e += d2 * d2;
+          }
         }
         GT fx, fy;
         const double d0 = A::wall(xi, Rz, Rm1sq, fx, fy);
