@@ -1295,7 +1295,7 @@ def run_ours(args, rank, world, local):
         dist.destroy_process_group()
 
 
-def energy_grad_roofline(ctx, torch, n, R, rounds=8, l2_bytes=129e6):
+def energy_grad_roofline(ctx, torch, n, R, rounds=8, repeats=5, l2_bytes=129e6):
     """The standalone fused energy + gradient kernel over every circle of the batch, after a
     forced FP32 (or FP64) list build at the final layouts.
 
@@ -1338,15 +1338,18 @@ def energy_grad_roofline(ctx, torch, n, R, rounds=8, l2_bytes=129e6):
     for o in outs[1:]:
         if not (same(o[0], outs[0][0]) and same(o[1], outs[0][1])):
             raise RuntimeError("energy_grad_roofline: a copy of the layouts gave another result")
-    a = torch.cuda.Event(enable_timing=True)
-    b = torch.cuda.Event(enable_timing=True)
-    a.record()
-    for _ in range(rounds):
-        for c, o in zip(ctxs, outs):
-            c.energy_grad(eval=ev, out=o)
-    b.record()
-    torch.cuda.synchronize()
-    ms = a.elapsed_time(b) / (rounds * len(ctxs))
+    per = []
+    for _ in range(repeats):  # the median of several timed sequences
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(rounds):
+            for c, o in zip(ctxs, outs):
+                c.energy_grad(eval=ev, out=o)
+        b.record()
+        torch.cuda.synchronize()
+        per.append(a.elapsed_time(b) / (rounds * len(ctxs)))
+    ms = float(np.median(per))
     for c in ctxs[1:]:
         c.close()
     # a 1 GB flush of L2 before one launch; while the GPU writes it (about 150 us) the host has
@@ -1370,9 +1373,10 @@ def energy_grad_roofline(ctx, torch, n, R, rounds=8, l2_bytes=129e6):
              "energy_grad_block_kernel + energy_grad_kernel + energy_reduce_kernel")
     return {"kernel": kname, "achieved": round(gbs, 1), "peak": hbm,
             "unit": "GB/s", "frac": round(gbs / hbm, 4), "peak_kind": kind, "avg_launch_ms": round(ms, 4),
-            "timing": f"{rounds} rounds of {len(ctxs)} launches back to back over {len(ctxs)} contexts with the same "
+            "timing": f"median of {repeats} sequences of {rounds} rounds of {len(ctxs)} launches back to back over "
+                      f"{len(ctxs)} contexts with the same "
                       f"layouts ({len(ctxs)} x {bytes_ / 1e6:.1f} MB of algorithmic bytes > {l2_bytes / 1e6:.0f} MB of L2), "
-                      f"events around all",
+                      f"events around each sequence",
             "single_launch_after_flush_ms": round(ms_single, 4),
             "single_launch_frac": round(bytes_ / (ms_single / 1e3) / 1e9 / hbm, 4),
             "algorithmic_bytes_per_launch": int(bytes_), "circles": N, "neighbor_entries": int(nnz),

