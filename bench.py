@@ -309,7 +309,7 @@ class Clocks:
 
 # DRAM traffic of the fused descent kernel per algorithmic byte, from one ncu capture on 1216
 # instances of the batch at the batch settings (profiles/descend_fused_kernel_1216inst_128x4.md:
-# dram__bytes_read.sum + dram__bytes_write.sum = 93.3 MB + 854.4 MB over the launch's 131.26 GB of
+# dram__bytes_read.sum + dram__bytes_write.sum = 93.0 MB + 852.1 MB over the launch's 131.26 GB of
 # algorithmic bytes, the byte model charging the context's m).  A full launch's traffic is that
 # ratio times its algorithmic bytes.  The figure holds for the kernel sources it was measured on:
 # once their hash changes the bench reports traffic as null.
@@ -317,7 +317,7 @@ FUSED_TRAFFIC = {"sources": ["pecc_descend_kernel.cuh", "pecc_dev.cuh", "pecc_de
                              "pecc_descend_fused_256x2.cu"], "k": 2,
                  "cfg": ["step_max=0.3", "polish_gate=0.00001", "stall_window=5", "polish_stall_window=50",
                          "lbfgs_m=5"],
-                 "sha256_16": "c656e9af07fde39d", "dram_per_algorithmic_byte": (93301760 + 854396672) / 131256661876.0}
+                 "sha256_16": "500e9057b0c5b0bb", "dram_per_algorithmic_byte": (92966912 + 852149248) / 131256661876.0}
 
 
 def fused_traffic(alg_bytes):
